@@ -1,0 +1,234 @@
+/*
+ * apic.h - C interface of the GB300 per-tile APIC reconstruction library.
+ *
+ * APIC (angular ptychographic imaging with a closed-form solution), as used by
+ * WSI-APIC (arXiv 2407.20469, Sec. 2.3): from a stack of low-resolution
+ * intensity images of one slide tile - NA-matching images first, darkfield
+ * images after - recover the complex high-resolution field and the pupil
+ * aberration. Every tile of a batch is independent; all per-tile arithmetic
+ * runs in this library's CUDA kernels (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named d_* are DEVICE pointers (the current CUDA device at the
+ *   call); h_* are HOST pointers. The caller owns every buffer it passes; the
+ *   library owns only the plan and the plan's workspace.
+ * - Complex arrays are interleaved float pairs (re, im), i.e. complex64.
+ * - Calls that take a stream are asynchronous and stream-ordered: they enqueue
+ *   work on `stream` (a cudaStream_t passed as void*, NULL = legacy default
+ *   stream) and return once it is enqueued. Device-side results are valid
+ *   after the stream reaches that point.
+ * - A host return code other than APIC_OK means nothing was enqueued (argument
+ *   or set-up error) or a launch failed (APIC_ECUDA). Numerical trouble in a
+ *   tile never traps: it is reported per tile in d_tile_status.
+ * - A plan may be used from one host thread at a time; concurrent calls on the
+ *   same plan from several streams race on its workspace.
+ *
+ * Frequencies and layouts
+ * -----------------------
+ * A plan serves one tile-size class h x w (low-resolution pixels of pitch
+ * pixel_um in the sample plane) and upsampling u: the output grid is
+ * (u h) x (u w) with pitch pixel_um / u. The frequency step is 1/(w dx) along
+ * x and 1/(h dx) along y on both grids. Spectra are Fourier-series
+ * coefficients (DFT / number of samples); signed integer frequency k of an
+ * n-point axis lives at index k mod n. Illumination wave-vectors are snapped
+ * to the integer grid at plan creation (apic_plan_query reports the result).
+ */
+#ifndef APIC_H
+#define APIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes of every entry point. */
+typedef enum {
+    APIC_OK = 0,
+    APIC_EINVAL = 1,      /* bad argument (NULL, size, count, layout)            */
+    APIC_ENOMEM = 2,      /* device or host allocation failed                    */
+    APIC_ECUDA = 3,       /* a CUDA call or kernel launch failed                 */
+    APIC_EGEOMETRY = 4,   /* illumination geometry unusable for this tile size  */
+    APIC_EINTERNAL = 5    /* library bug (an invariant did not hold)             */
+} apic_status;
+
+/* Per-tile status words written to d_tile_status (bit flags, 0 = clean). */
+#define APIC_TILE_OK          0
+#define APIC_TILE_BACKGROUND  1   /* below the background-contrast threshold (Sec. 3.2) */
+#define APIC_TILE_NOTCONV     2   /* a darkfield solve stopped above its tolerance      */
+#define APIC_TILE_BADINPUT    4   /* non-finite or negative intensity in the stack      */
+
+/* Plan flags. */
+#define APIC_SKIP_BACKGROUND  1   /* background tiles: outputs zeroed, no reconstruction */
+#define APIC_HOST_ONLY        2   /* build the geometry only: no device memory, no CUDA
+                                     calls; only apic_plan_query / apic_plan_table /
+                                     apic_plan_df_set / apic_plan_destroy accept it */
+
+/* Number of Zernike coefficients per tile (Noll j = 1..15; j = 1..3 always 0). */
+#define APIC_N_ZERNIKE 15
+
+typedef struct {
+    int tile_h, tile_w;          /* low-resolution tile size of this plan (>= 16, powers of 2) */
+    int n_bf, n_df;              /* NA-matching then darkfield image counts                  */
+    const float* h_kx;           /* host [n_bf + n_df] transverse illumination k, cycles/um */
+    const float* h_ky;
+    float na;                    /* objective numerical aperture (0.25)                      */
+    float wavelength_um;         /* 0.52                                                      */
+    float pixel_um;              /* camera pixel in the sample plane (0.345)                  */
+    int upsample;                /* output upsampling factor u (2)                             */
+    int max_tiles;               /* largest n_tiles of one call; larger calls are chunked     */
+    int df_iters;                /* CGLS iterations per darkfield image (<= 0: 40)            */
+    float df_tol;                /* CGLS relative gradient tolerance (<= 0: 1e-6)             */
+    int ab_passes;               /* value passes of the aberration solve (< 0: 2)             */
+    float bg_contrast;           /* background threshold on RMS contrast (Sec. 3.2; 0.02)     */
+    int flags;                   /* APIC_SKIP_BACKGROUND                                       */
+} apic_params;
+
+typedef struct apic_plan apic_plan;
+
+/* Sizes of a plan's fixed index sets (for callers laying out stage buffers). */
+typedef struct {
+    int tile_h, tile_w, out_h, out_w;
+    int n_bf, n_df;
+    int n_pupil;           /* grid points inside the pupil (Circ_NA of Eq. 1)              */
+    int n_aperture;        /* object frequencies of the final synthetic aperture           */
+    int n_rows;            /* rows of the aberration system D phi = beta (Eq. 10)          */
+    int n_df_used;         /* darkfield images the geometry admits (Sec. 4: <= 42% unknown) */
+    int fft_m;             /* grid of the darkfield correlations                            */
+    double pupil_rx, pupil_ry;   /* pupil radius in grid steps along x and y              */
+} apic_plan_info;
+
+/* Human-readable name of a return code. Never NULL. */
+const char* apic_status_string(apic_status s);
+
+/* Message describing the last error returned on the calling host thread. Never NULL. */
+const char* apic_last_error(void);
+
+/*
+ * Build a plan: snap the illumination to the grid (NA-matching LEDs keep the
+ * DC term on the edge of the shifted pupil, Sec. 2.3), enumerate the overlap
+ * sets S_il (Eq. 8), the darkfield sets U, P, Q (Eq. 11-13, images taken by
+ * increasing |k|), upload the index tables and allocate workspace for
+ * max_tiles tiles on the current device. *out receives the plan.
+ * Errors: APIC_EINVAL (NULL or out-of-range field), APIC_EGEOMETRY (an
+ * NA-matching LED has no admissible grid point, or the spectrum leaves the
+ * output grid), APIC_ENOMEM, APIC_ECUDA.
+ */
+apic_status apic_plan_create(const apic_params* params, apic_plan** out);
+
+/* Free a plan and its device memory (synchronises the device first). NULL is a no-op. */
+apic_status apic_plan_destroy(apic_plan* plan);
+
+/* Sizes of the plan's index sets. */
+apic_status apic_plan_query(const apic_plan* plan, apic_plan_info* info);
+
+/*
+ * Copy one of the plan's integer tables to host memory (int32):
+ *   APIC_TABLE_LEDS      [n_bf + n_df][2] snapped (kx, ky) of each LED
+ *   APIC_TABLE_PUPIL     [n_pupil][2]     camera frequencies k inside the pupil
+ *   APIC_TABLE_APERTURE  [n_aperture][2]  object frequencies of the aperture
+ * `count` is the number of int32 the destination holds; APIC_EINVAL if short.
+ */
+#define APIC_TABLE_LEDS      0
+#define APIC_TABLE_PUPIL     1
+#define APIC_TABLE_APERTURE  2
+apic_status apic_plan_table(const apic_plan* plan, int which, int32_t* h_dst, size_t count);
+
+/*
+ * Index sets of darkfield image `index` in processing order (Eq. 11-13), all
+ * images including skipped ones, as int32 pairs in the pupil frame c = K + k_j:
+ *   which 0: U (unknown), 1: P (known), 2: Q (lags), each sorted by (y, x).
+ * h_meta (may be NULL) receives {led index, used (0/1), |U|, |P|, |Q|}.
+ * h_dst may be NULL to query the sizes only; otherwise it holds `count` int32.
+ */
+apic_status apic_plan_df_set(const apic_plan* plan, int index, int which, int32_t* h_dst, size_t count,
+                             int32_t* h_meta);
+
+/*
+ * Whole per-tile reconstruction (Sec. 2.3, Fig. 2), for n_tiles tiles:
+ *   d_intensity  [n_tiles][n_bf + n_df][h][w] float32 intensity stacks
+ *   d_field      [n_tiles][u h][u w] complex64 out: high-resolution field
+ *   d_zernike    [n_tiles][15] float32 out: Noll coefficients (rad) of phi
+ *   d_pupil      [n_tiles][h][w] complex64 out, or NULL: Circ(k) exp(j phi(k)),
+ *                frequency k at index k mod n
+ *   d_tile_status [n_tiles] int32 out, or NULL: APIC_TILE_* bits
+ * Steps: background test (Sec. 3.2), Kramers-Kronig recovery (Eq. 4-7),
+ * aberration solve (Eq. 8-10), correction and stitching, darkfield extension
+ * (Eq. 11-13), inverse transform. The global phase of the field is the
+ * phase gauge of Eq. 5 (mean phase of the recovered fields set to zero).
+ */
+apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* d_intensity,
+                                   float* d_field, float* d_zernike, float* d_pupil,
+                                   int32_t* d_tile_status, void* stream);
+
+/* ---- Stages of apic_reconstruct_batch, for testing and custom pipelines ---- */
+
+/*
+ * Background statistic (Sec. 3.2): per tile, the mean over the NA-matching
+ * images of var(I)/mean(I)^2 (squared RMS contrast), written to d_contrast2
+ * [n_tiles] float32, and d_tile_status [n_tiles] set to APIC_TILE_BACKGROUND
+ * where it is below bg_contrast^2 (else 0), with APIC_TILE_BADINPUT where
+ * the stack holds a negative or non-finite value.
+ */
+apic_status apic_background(apic_plan* plan, int n_tiles, const float* d_intensity,
+                            float* d_contrast2, int32_t* d_tile_status, void* stream);
+
+/*
+ * Kramers-Kronig recovery (Eq. 4-7) of every NA-matching image:
+ *   d_xdisc [n_tiles][n_bf][n_pupil] complex64 out: X_i(K) = S'_i(K) exp(-j theta_i)
+ *   at K = k_p - k_i for the pupil points k_p (APIC_TABLE_PUPIL order).
+ */
+apic_status apic_kk_spectra(apic_plan* plan, int n_tiles, const float* d_intensity,
+                            float* d_xdisc, void* stream);
+
+/*
+ * Aberration solve (Eq. 8-10): phase differences on every overlap S_il,
+ * neighbour-difference fit, then least squares on Eq. 10 (FP64 normal
+ * equations). d_xdisc as written by apic_kk_spectra; d_zernike [n_tiles][15] out.
+ */
+apic_status apic_aberration(apic_plan* plan, int n_tiles, const float* d_xdisc,
+                            float* d_zernike, void* stream);
+
+/*
+ * Correction and stitching: d_spec [n_tiles][n_aperture] complex64 out, the
+ * mean of the aberration-corrected spectra at each brightfield aperture point
+ * (APIC_TABLE_APERTURE order) and zero on the darkfield-only points.
+ */
+apic_status apic_stitch(apic_plan* plan, int n_tiles, const float* d_xdisc,
+                        const float* d_zernike, float* d_spec, void* stream);
+
+/*
+ * Darkfield extension (Eq. 11-13), darkfield images in plan order, each solved
+ * by CGLS on C U = b with FFT correlations (FP32 transforms, FP64 scalars and
+ * solution accumulation). Updates d_spec in place; ORs APIC_TILE_NOTCONV into
+ * d_tile_status (may be NULL) where a solve ended above its tolerance.
+ */
+apic_status apic_darkfield(apic_plan* plan, int n_tiles, const float* d_intensity,
+                           const float* d_zernike, float* d_spec, int32_t* d_tile_status,
+                           void* stream);
+
+/* Inverse transform of d_spec onto the (u h) x (u w) grid: d_field out. */
+apic_status apic_synthesize(apic_plan* plan, int n_tiles, const float* d_spec, float* d_field,
+                            void* stream);
+
+/* Pupil function Circ(k) exp(j phi(k)) (Eq. 1) of each tile: d_pupil [n_tiles][h][w]. */
+apic_status apic_pupil(apic_plan* plan, int n_tiles, const float* d_zernike, float* d_pupil,
+                       void* stream);
+
+/*
+ * Forward model (Eq. 1-2) for synthetic inputs: from objects on the output
+ * grid, d_object [n_tiles][u h][u w] complex64 (transmission), and
+ * d_zernike [n_tiles][15], write d_intensity [n_tiles][n_bf + n_df][h][w].
+ * photons > 0 adds Poisson noise at `photons` per unit intensity from a
+ * counter-based generator keyed by (seed, tile, image, pixel).
+ */
+apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* d_object,
+                          const float* d_zernike, float photons, uint64_t seed,
+                          float* d_intensity, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APIC_H */

@@ -1,0 +1,216 @@
+"""Thin Python binding of the C interface in include/apic.h (ctypes).
+
+Argument marshalling only: every computation runs in libapic.so's kernels.
+Device buffers are passed as torch CUDA tensors (their data_ptr()) or raw
+integer addresses; streams default to torch's current stream. Loading fails
+loudly when the shared object is missing - there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapic.so")
+
+APIC_OK, APIC_EINVAL, APIC_ENOMEM, APIC_ECUDA, APIC_EGEOMETRY, APIC_EINTERNAL = range(6)
+APIC_TILE_OK, APIC_TILE_BACKGROUND, APIC_TILE_NOTCONV, APIC_TILE_BADINPUT = 0, 1, 2, 4
+APIC_SKIP_BACKGROUND = 1
+APIC_HOST_ONLY = 2
+APIC_N_ZERNIKE = 15
+APIC_TABLE_LEDS, APIC_TABLE_PUPIL, APIC_TABLE_APERTURE = 0, 1, 2
+
+# Every symbol include/apic.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "apic_status_string", "apic_last_error", "apic_plan_create", "apic_plan_destroy",
+    "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_reconstruct_batch", "apic_background",
+    "apic_kk_spectra", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
+    "apic_pupil", "apic_simulate",
+]
+
+
+class apic_params(C.Structure):
+    _fields_ = [
+        ("tile_h", C.c_int), ("tile_w", C.c_int), ("n_bf", C.c_int), ("n_df", C.c_int),
+        ("h_kx", C.POINTER(C.c_float)), ("h_ky", C.POINTER(C.c_float)),
+        ("na", C.c_float), ("wavelength_um", C.c_float), ("pixel_um", C.c_float),
+        ("upsample", C.c_int), ("max_tiles", C.c_int), ("df_iters", C.c_int), ("df_tol", C.c_float),
+        ("ab_passes", C.c_int), ("bg_contrast", C.c_float), ("flags", C.c_int),
+    ]
+
+
+class apic_plan_info(C.Structure):
+    _fields_ = [
+        ("tile_h", C.c_int), ("tile_w", C.c_int), ("out_h", C.c_int), ("out_w", C.c_int),
+        ("n_bf", C.c_int), ("n_df", C.c_int), ("n_pupil", C.c_int), ("n_aperture", C.c_int),
+        ("n_rows", C.c_int), ("n_df_used", C.c_int), ("fft_m", C.c_int),
+        ("pupil_rx", C.c_double), ("pupil_ry", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libapic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2407_20469_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i32, f32, sz = C.c_void_p, C.c_int, C.c_float, C.c_size_t
+    sig = {
+        "apic_status_string": (C.c_char_p, [i32]),
+        "apic_last_error": (C.c_char_p, []),
+        "apic_plan_create": (i32, [C.POINTER(apic_params), C.POINTER(vp)]),
+        "apic_plan_destroy": (i32, [vp]),
+        "apic_plan_query": (i32, [vp, C.POINTER(apic_plan_info)]),
+        "apic_plan_table": (i32, [vp, i32, C.POINTER(C.c_int32), sz]),
+        "apic_plan_df_set": (i32, [vp, i32, i32, C.POINTER(C.c_int32), sz, C.POINTER(C.c_int32)]),
+        "apic_reconstruct_batch": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "apic_background": (i32, [vp, i32, vp, vp, vp, vp]),
+        "apic_kk_spectra": (i32, [vp, i32, vp, vp, vp]),
+        "apic_aberration": (i32, [vp, i32, vp, vp, vp]),
+        "apic_stitch": (i32, [vp, i32, vp, vp, vp, vp]),
+        "apic_darkfield": (i32, [vp, i32, vp, vp, vp, vp, vp]),
+        "apic_synthesize": (i32, [vp, i32, vp, vp, vp]),
+        "apic_pupil": (i32, [vp, i32, vp, vp, vp]),
+        "apic_simulate": (i32, [vp, i32, vp, vp, f32, C.c_uint64, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class ApicError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        msg = lib.apic_last_error().decode()
+        super().__init__(f"{where}: {lib.apic_status_string(code).decode()} ({msg})")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != APIC_OK:
+        raise ApicError(code, where)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """An apic_plan: geometry of one tile-size class plus its device workspace."""
+
+    def __init__(self, tile: int, kx, ky, n_bf: int, na=0.25, wavelength_um=0.52, pixel_um=0.345,
+                 upsample: int = 2, max_tiles: int = 64, df_iters: int = 0, df_tol: float = 0.0,
+                 ab_passes: int = -1, bg_contrast: float = 0.02, flags: int = 0):
+        lib = load()
+        self._kx = np.ascontiguousarray(kx, dtype=np.float32)
+        self._ky = np.ascontiguousarray(ky, dtype=np.float32)
+        p = apic_params()
+        p.tile_h = p.tile_w = tile
+        p.n_bf = n_bf
+        p.n_df = len(self._kx) - n_bf
+        p.h_kx = self._kx.ctypes.data_as(C.POINTER(C.c_float))
+        p.h_ky = self._ky.ctypes.data_as(C.POINTER(C.c_float))
+        p.na, p.wavelength_um, p.pixel_um = float(na), float(wavelength_um), float(pixel_um)
+        p.upsample, p.max_tiles, p.df_iters, p.df_tol = upsample, max_tiles, df_iters, df_tol
+        p.ab_passes, p.bg_contrast, p.flags = ab_passes, bg_contrast, flags
+        h = C.c_void_p()
+        _check(lib.apic_plan_create(C.byref(p), C.byref(h)), "apic_plan_create")
+        self.handle = h
+        self.params = p
+        info = apic_plan_info()
+        _check(lib.apic_plan_query(h, C.byref(info)), "apic_plan_query")
+        self.info = info
+
+    @classmethod
+    def from_illumination(cls, tile: int, ill, **kw) -> "Plan":
+        return cls(tile, ill.kx, ill.ky, ill.n_bf, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().apic_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def table(self, which: int) -> np.ndarray:
+        n = {APIC_TABLE_LEDS: self.info.n_bf + self.info.n_df, APIC_TABLE_PUPIL: self.info.n_pupil,
+             APIC_TABLE_APERTURE: self.info.n_aperture}[which]
+        out = np.zeros((n, 2), dtype=np.int32)
+        _check(load().apic_plan_table(self.handle, which, out.ctypes.data_as(C.POINTER(C.c_int32)), out.size),
+               "apic_plan_table")
+        return out
+
+    def df_set(self, index: int, which: int):
+        """(points [k, 2] int32, meta {led, used, nU, nP, nQ}) of darkfield image `index`."""
+        meta = np.zeros(5, dtype=np.int32)
+        lib = load()
+        P32 = C.POINTER(C.c_int32)
+        _check(lib.apic_plan_df_set(self.handle, index, which, None, 0, meta.ctypes.data_as(P32)), "apic_plan_df_set")
+        out = np.zeros((int(meta[2 + which]), 2), dtype=np.int32)
+        _check(lib.apic_plan_df_set(self.handle, index, which, out.ctypes.data_as(P32), out.size,
+                                    meta.ctypes.data_as(P32)), "apic_plan_df_set")
+        return out, meta
+
+    # -- entry points (same names as the C interface, without the prefix)
+    def reconstruct_batch(self, n_tiles, intensity, field, zernike, pupil=None, tile_status=None, stream=None):
+        _check(load().apic_reconstruct_batch(self.handle, n_tiles, _ptr(intensity), _ptr(field), _ptr(zernike),
+                                             _ptr(pupil), _ptr(tile_status), _stream(stream)),
+               "apic_reconstruct_batch")
+
+    def background(self, n_tiles, intensity, contrast2, tile_status, stream=None):
+        _check(load().apic_background(self.handle, n_tiles, _ptr(intensity), _ptr(contrast2), _ptr(tile_status),
+                                      _stream(stream)), "apic_background")
+
+    def kk_spectra(self, n_tiles, intensity, xdisc, stream=None):
+        _check(load().apic_kk_spectra(self.handle, n_tiles, _ptr(intensity), _ptr(xdisc), _stream(stream)),
+               "apic_kk_spectra")
+
+    def aberration(self, n_tiles, xdisc, zernike, stream=None):
+        _check(load().apic_aberration(self.handle, n_tiles, _ptr(xdisc), _ptr(zernike), _stream(stream)),
+               "apic_aberration")
+
+    def stitch(self, n_tiles, xdisc, zernike, spec, stream=None):
+        _check(load().apic_stitch(self.handle, n_tiles, _ptr(xdisc), _ptr(zernike), _ptr(spec), _stream(stream)),
+               "apic_stitch")
+
+    def darkfield(self, n_tiles, intensity, zernike, spec, tile_status=None, stream=None):
+        _check(load().apic_darkfield(self.handle, n_tiles, _ptr(intensity), _ptr(zernike), _ptr(spec),
+                                     _ptr(tile_status), _stream(stream)), "apic_darkfield")
+
+    def synthesize(self, n_tiles, spec, field, stream=None):
+        _check(load().apic_synthesize(self.handle, n_tiles, _ptr(spec), _ptr(field), _stream(stream)),
+               "apic_synthesize")
+
+    def pupil(self, n_tiles, zernike, pupil, stream=None):
+        _check(load().apic_pupil(self.handle, n_tiles, _ptr(zernike), _ptr(pupil), _stream(stream)), "apic_pupil")
+
+    def simulate(self, n_tiles, obj, zernike, photons, seed, intensity, stream=None):
+        _check(load().apic_simulate(self.handle, n_tiles, _ptr(obj), _ptr(zernike), float(photons), int(seed),
+                                    _ptr(intensity), _stream(stream)), "apic_simulate")

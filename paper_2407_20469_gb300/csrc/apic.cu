@@ -1,0 +1,626 @@
+// apic.cu - C interface of the library (include/apic.h): plan creation, table
+// upload, workspace, stage entry points and the batched reconstruction.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/apic.h"
+#include "internal.cuh"
+#include "passes.cuh"
+#include "plan.h"
+
+using namespace apic;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+apic_status fail(apic_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+apic_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(APIC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define APIC_TRY_CUDA(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return cuda_fail(_e, #expr);   \
+    } while (0)
+
+// Packs host vectors into one device allocation.
+struct Arena {
+    std::vector<char> host;
+    template <typename T>
+    size_t add(const T* p, size_t count) {
+        size_t off = (host.size() + 255) & ~(size_t)255;
+        host.resize(off + count * sizeof(T));
+        if (count) std::memcpy(host.data() + off, p, count * sizeof(T));
+        return off;
+    }
+    template <typename T>
+    size_t add(const std::vector<T>& v) {
+        return add(v.data(), v.size());
+    }
+};
+
+std::vector<int> rowptr_of(const std::vector<int>& ys, int y0, int y1) {
+    std::vector<int> rp(std::max(0, y1 - y0 + 1) + 1, 0);
+    for (int y : ys) rp[y - y0 + 1]++;
+    for (size_t i = 1; i < rp.size(); ++i) rp[i] += rp[i - 1];
+    return rp;
+}
+
+std::vector<float2> twiddles(int N) {
+    std::vector<float2> t(N);
+    for (int k = 0; k < N; ++k) {
+        const double a = -2.0 * M_PI * (double)k / (double)N;
+        t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    return t;
+}
+
+bool pow2(int n) { return n >= 16 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+struct apic_plan {
+    apic_params params;
+    HostPlan host;
+    DevPlan dev;
+    Launch L;
+    int device = 0, sms = 0;
+    int max_tiles = 0, df_iters = 40, ab_passes = 2;
+    float df_tol = 1e-5f, bg_thresh2 = 4e-4f, bg_c2 = 4e-4f;
+    void* d_tables = nullptr;
+    // workspace
+    float2* xdisc = nullptr;
+    float* zern = nullptr;
+    float* phi = nullptr;
+    float2* spec = nullptr;
+    int32_t* status = nullptr;
+    float* c2 = nullptr;
+    float2* kk_scratch = nullptr;
+    float* beta_scratch = nullptr;
+    void* df_scratch = nullptr;
+    size_t df_per_block = 0;
+    float2* sim_scratch = nullptr;
+    size_t sim_bytes = 0;
+    std::vector<void*> allocs;
+    bool host_only = false;
+};
+
+namespace {
+
+apic_status dmalloc(apic_plan* p, void** ptr, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(APIC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+    }
+    p->allocs.push_back(*ptr);
+    return APIC_OK;
+}
+
+apic_status upload(apic_plan* plan) {
+    const HostPlan& H = plan->host;
+    DevPlan& D = plan->dev;
+    Arena A;
+    D = DevPlan();
+    D.h = H.h;
+    D.w = H.w;
+    D.H = H.H;
+    D.W = H.W;
+    D.n_bf = H.n_bf;
+    D.n_df = H.n_df;
+    D.n_img = H.n_bf + H.n_df;
+    D.npup = (int)H.pup_x.size();
+    D.nap = (int)H.ap_x.size();
+    D.nrows = (int)H.row_i.size();
+    D.m = H.m;
+    D.Rx = (float)H.Rx;
+    D.Ry = (float)H.Ry;
+    D.pup_ax = H.pup_ax;
+    D.pup_ay = H.pup_ay;
+
+    const size_t o_pupx = A.add(H.pup_x), o_pupy = A.add(H.pup_y), o_lut = A.add(H.pup_lut);
+    const size_t o_puprp = A.add(rowptr_of(H.pup_y, -H.pup_ay, H.pup_ay));
+    const size_t o_ledx = A.add(H.led_x), o_ledy = A.add(H.led_y), o_ledp = A.add(H.led_pup);
+    std::vector<int> il(H.row_i.size());
+    for (size_t r = 0; r < il.size(); ++r) il[r] = H.row_i[r] | (H.row_l[r] << 16);
+    const size_t o_il = A.add(il), o_pi = A.add(H.row_pi), o_pl = A.add(H.row_pl);
+    const size_t o_nx = A.add(H.row_nx), o_ny = A.add(H.row_ny), o_A = A.add(H.row_A);
+    const size_t o_Lv = A.add(H.Lval, 144), o_Lg = A.add(H.Lgrad, 144);
+    const size_t o_apx = A.add(H.ap_x), o_apy = A.add(H.ap_y), o_apbf = A.add(H.ap_bf);
+    const size_t o_stp = A.add(H.st_ptr), o_sti = A.add(H.st_img), o_stq = A.add(H.st_pup);
+    int ay0 = 0, ay1 = -1;
+    if (!H.ap_y.empty()) {
+        ay0 = H.ap_y.front();
+        ay1 = H.ap_y.back();
+    }
+    D.ap_y0 = ay0;
+    D.ap_y1 = ay1;
+    const size_t o_aprp = A.add(rowptr_of(H.ap_y, ay0, ay1));
+
+    // darkfield tables
+    std::vector<DevDF> dfs;
+    std::vector<int> ux, uy, up, ua, px, py, pp, pa, qx, qy, rp;
+    int maxN = 1, maxM = 1;
+    for (const auto& d : H.df) {
+        if (!d.used) continue;
+        DevDF e{};
+        e.led = d.led;
+        e.kx = d.kx;
+        e.ky = d.ky;
+        e.N = (int)d.U_x.size();
+        e.M = (int)d.Q_x.size();
+        e.NP = (int)d.P_x.size();
+        e.u_off = (int)ux.size();
+        e.p_off = (int)px.size();
+        e.q_off = (int)qx.size();
+        ux.insert(ux.end(), d.U_x.begin(), d.U_x.end());
+        uy.insert(uy.end(), d.U_y.begin(), d.U_y.end());
+        up.insert(up.end(), d.U_pup.begin(), d.U_pup.end());
+        ua.insert(ua.end(), d.U_ap.begin(), d.U_ap.end());
+        px.insert(px.end(), d.P_x.begin(), d.P_x.end());
+        py.insert(py.end(), d.P_y.begin(), d.P_y.end());
+        pp.insert(pp.end(), d.P_pup.begin(), d.P_pup.end());
+        pa.insert(pa.end(), d.P_ap.begin(), d.P_ap.end());
+        qx.insert(qx.end(), d.Q_x.begin(), d.Q_x.end());
+        qy.insert(qy.end(), d.Q_y.begin(), d.Q_y.end());
+        auto band = [](const std::vector<int>& ys, int& y0, int& y1) {
+            y0 = *std::min_element(ys.begin(), ys.end());
+            y1 = *std::max_element(ys.begin(), ys.end());
+        };
+        band(d.U_y, e.uy0, e.uy1);
+        band(d.Q_y, e.qy0, e.qy1);
+        if (d.P_y.empty()) {
+            e.py0 = 0;
+            e.py1 = -1;
+        } else {
+            band(d.P_y, e.py0, e.py1);
+        }
+        auto push_rp = [&](const std::vector<int>& ys, int y0, int y1) {
+            const int off = (int)rp.size();
+            auto v = rowptr_of(ys, y0, y1);
+            rp.insert(rp.end(), v.begin(), v.end());
+            return off;
+        };
+        e.urp = push_rp(d.U_y, e.uy0, e.uy1);
+        e.qrp = push_rp(d.Q_y, e.qy0, e.qy1);
+        e.prp = push_rp(d.P_y, e.py0, e.py1);
+        maxN = std::max(maxN, e.N);
+        maxM = std::max(maxM, e.M);
+        dfs.push_back(e);
+    }
+    D.n_used = (int)dfs.size();
+    D.max_N = maxN;
+    D.max_M = maxM;
+    const size_t o_df = A.add(dfs);
+    const size_t o_ux = A.add(ux), o_uy = A.add(uy), o_up = A.add(up), o_ua = A.add(ua);
+    const size_t o_px = A.add(px), o_py = A.add(py), o_pp = A.add(pp), o_pa = A.add(pa);
+    const size_t o_qx = A.add(qx), o_qy = A.add(qy), o_rp = A.add(rp);
+    const size_t o_twn = A.add(twiddles(H.h)), o_twm = A.add(twiddles(H.m)), o_twN = A.add(twiddles(H.H));
+
+    void* base = nullptr;
+    apic_status s = dmalloc(plan, &base, A.host.size());
+    if (s != APIC_OK) return s;
+    APIC_TRY_CUDA(cudaMemcpy(base, A.host.data(), A.host.size(), cudaMemcpyHostToDevice));
+    plan->d_tables = base;
+    char* b = (char*)base;
+    D.pup_x = (const int*)(b + o_pupx);
+    D.pup_y = (const int*)(b + o_pupy);
+    D.pup_lut = (const int*)(b + o_lut);
+    D.pup_rowptr = (const int*)(b + o_puprp);
+    D.led_x = (const int*)(b + o_ledx);
+    D.led_y = (const int*)(b + o_ledy);
+    D.led_pup = (const int*)(b + o_ledp);
+    D.row_il = (const int*)(b + o_il);
+    D.row_pi = (const int*)(b + o_pi);
+    D.row_pl = (const int*)(b + o_pl);
+    D.row_nx = (const int*)(b + o_nx);
+    D.row_ny = (const int*)(b + o_ny);
+    D.row_A = (const float*)(b + o_A);
+    D.Lval = (const double*)(b + o_Lv);
+    D.Lgrad = (const double*)(b + o_Lg);
+    D.ap_x = (const int*)(b + o_apx);
+    D.ap_y = (const int*)(b + o_apy);
+    D.ap_bf = (const uint8_t*)(b + o_apbf);
+    D.st_ptr = (const int*)(b + o_stp);
+    D.st_img = (const int*)(b + o_sti);
+    D.st_pup = (const int*)(b + o_stq);
+    D.ap_rowptr = (const int*)(b + o_aprp);
+    D.df = (const DevDF*)(b + o_df);
+    D.dU_x = (const int*)(b + o_ux);
+    D.dU_y = (const int*)(b + o_uy);
+    D.dU_pup = (const int*)(b + o_up);
+    D.dU_ap = (const int*)(b + o_ua);
+    D.dP_x = (const int*)(b + o_px);
+    D.dP_y = (const int*)(b + o_py);
+    D.dP_pup = (const int*)(b + o_pp);
+    D.dP_ap = (const int*)(b + o_pa);
+    D.dQ_x = (const int*)(b + o_qx);
+    D.dQ_y = (const int*)(b + o_qy);
+    D.d_rowptr = (const int*)(b + o_rp);
+    D.tw_n = (const float2*)(b + o_twn);
+    D.tw_m = (const float2*)(b + o_twm);
+    D.tw_N = (const float2*)(b + o_twN);
+    return APIC_OK;
+}
+
+apic_status configure(apic_plan* plan) {
+    const DevPlan& D = plan->dev;
+    Launch& L = plan->L;
+    L.smem_kk = chunk_smem_bytes(D.h, D.h);
+    const int bufN = std::max(2 * (kChunk / D.h) * (D.h + 1), 2 * (kChunk / D.m) * (D.m + 1));
+    L.smem_df = (size_t)bufN * sizeof(float2) + (size_t)(D.h + D.m) * sizeof(float2) + 64 * sizeof(double);
+    L.smem_syn = chunk_smem_bytes(D.H, D.H);
+    L.smem_sim = chunk_smem_bytes(D.h, D.h);
+    const int o_kk = configure_kernel(0, L.smem_kk), o_ab = configure_kernel(1, 0);
+    const int o_df = configure_kernel(2, L.smem_df), o_syn = configure_kernel(3, L.smem_syn);
+    const int o_sim = configure_kernel(4, L.smem_sim), o_obj = configure_kernel(5, L.smem_syn);
+    if (!o_kk || !o_ab || !o_df || !o_syn || !o_sim || !o_obj) {
+        cudaGetLastError();
+        return fail(APIC_ECUDA, "kernel configuration (shared memory / occupancy) failed");
+    }
+    const int sms = plan->sms;
+    L.grid_kk = sms * o_kk;
+    L.grid_ab = sms * std::min(o_ab, 2);
+    L.grid_df = sms * std::min(o_df, 2);
+    L.grid_syn = sms * std::min(o_syn, o_obj);
+    L.grid_sim = sms * o_sim;
+    return APIC_OK;
+}
+
+apic_status alloc_workspace(apic_plan* p) {
+    const DevPlan& D = p->dev;
+    const size_t T = (size_t)p->max_tiles;
+    apic_status s;
+    if ((s = dmalloc(p, (void**)&p->xdisc, T * D.n_bf * D.npup * sizeof(float2))) != APIC_OK) return s;
+    if ((s = dmalloc(p, (void**)&p->zern, T * APIC_N_ZERNIKE * sizeof(float))) != APIC_OK) return s;
+    if ((s = dmalloc(p, (void**)&p->phi, T * D.npup * sizeof(float))) != APIC_OK) return s;
+    if ((s = dmalloc(p, (void**)&p->spec, T * D.nap * sizeof(float2))) != APIC_OK) return s;
+    if ((s = dmalloc(p, (void**)&p->status, T * sizeof(int32_t))) != APIC_OK) return s;
+    if ((s = dmalloc(p, (void**)&p->c2, T * sizeof(float))) != APIC_OK) return s;
+    if ((s = dmalloc(p, (void**)&p->kk_scratch, (size_t)p->L.grid_kk * D.h * D.h * sizeof(float2))) != APIC_OK)
+        return s;
+    if ((s = dmalloc(p, (void**)&p->beta_scratch, (size_t)p->L.grid_ab * D.nrows * sizeof(float))) != APIC_OK)
+        return s;
+    p->df_per_block = df_scratch_bytes(D);
+    if ((s = dmalloc(p, &p->df_scratch, (size_t)p->L.grid_df * p->df_per_block)) != APIC_OK) return s;
+    return APIC_OK;
+}
+
+apic_status check_plan(const apic_plan* plan, int n_tiles) {
+    if (!plan) return fail(APIC_EINVAL, "plan is NULL");
+    if (plan->host_only) return fail(APIC_EINVAL, "plan was created with APIC_HOST_ONLY");
+    if (n_tiles < 0) return fail(APIC_EINVAL, "n_tiles < 0");
+    return APIC_OK;
+}
+
+apic_status check_stage(const apic_plan* plan, int n_tiles) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (n_tiles > plan->max_tiles) return fail(APIC_EINVAL, "n_tiles exceeds the plan's max_tiles");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device)
+        return fail(APIC_EINVAL, "current device differs from the plan's device");
+    return APIC_OK;
+}
+
+#define APIC_TRY_LAUNCH(expr)                                  \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return cuda_fail(_e, #expr);    \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+const char* apic_status_string(apic_status s) {
+    switch (s) {
+        case APIC_OK: return "APIC_OK";
+        case APIC_EINVAL: return "APIC_EINVAL: invalid argument";
+        case APIC_ENOMEM: return "APIC_ENOMEM: allocation failed";
+        case APIC_ECUDA: return "APIC_ECUDA: CUDA error";
+        case APIC_EGEOMETRY: return "APIC_EGEOMETRY: unusable illumination geometry";
+        case APIC_EINTERNAL: return "APIC_EINTERNAL: internal error";
+    }
+    return "unknown apic_status";
+}
+
+const char* apic_last_error(void) { return g_last_error.c_str(); }
+
+apic_status apic_plan_create(const apic_params* pr, apic_plan** out) {
+    if (!pr || !out) return fail(APIC_EINVAL, "NULL params or out");
+    *out = nullptr;
+    if (!pow2(pr->tile_h) || pr->tile_h != pr->tile_w || pr->tile_h > 1024)
+        return fail(APIC_EINVAL, "tile_h == tile_w must be a power of two in [16, 1024]");
+    if (pr->n_bf < 2 || pr->n_bf > 255 || pr->n_df < 0 || pr->n_df > 4096)
+        return fail(APIC_EINVAL, "n_bf must be in [2, 255] and n_df in [0, 4096]");
+    if (!pr->h_kx || !pr->h_ky) return fail(APIC_EINVAL, "NULL illumination arrays");
+    if (!(pr->na > 0 && pr->na < 1.5f) || !(pr->wavelength_um > 0) || !(pr->pixel_um > 0))
+        return fail(APIC_EINVAL, "na, wavelength_um, pixel_um must be positive");
+    if (pr->upsample < 1 || pr->upsample > 8 || !pow2(pr->tile_h * pr->upsample) || pr->tile_h * pr->upsample > 1024)
+        return fail(APIC_EINVAL, "upsample must keep the output a power of two <= 1024");
+    if (pr->max_tiles < 1) return fail(APIC_EINVAL, "max_tiles < 1");
+
+    apic_plan* plan = new apic_plan();
+    plan->params = *pr;
+    plan->max_tiles = pr->max_tiles;
+    plan->df_iters = pr->df_iters > 0 ? pr->df_iters : 40;
+    plan->df_tol = pr->df_tol > 0 ? pr->df_tol : 1e-5f;
+    plan->ab_passes = pr->ab_passes >= 0 ? pr->ab_passes : 2;
+    const float bgc = pr->bg_contrast;
+    plan->bg_c2 = bgc * bgc;
+    plan->bg_thresh2 = (pr->flags & APIC_SKIP_BACKGROUND) ? bgc * bgc : -1.0f;
+
+    GeomParams g;
+    g.h = pr->tile_h;
+    g.w = pr->tile_w;
+    g.up = pr->upsample;
+    g.n_bf = pr->n_bf;
+    g.n_df = pr->n_df;
+    g.na = (double)pr->na;
+    g.wl = (double)pr->wavelength_um;
+    g.dx = (double)pr->pixel_um;
+    for (int i = 0; i < pr->n_bf + pr->n_df; ++i) {
+        g.kx.push_back((double)pr->h_kx[i]);
+        g.ky.push_back((double)pr->h_ky[i]);
+    }
+    std::string err = build_host_plan(g, plan->host);
+    if (!err.empty()) {
+        delete plan;
+        return fail(APIC_EGEOMETRY, err);
+    }
+    if (plan->host.m > 1024 || plan->host.m > std::max(plan->host.h, 1024)) {
+        delete plan;
+        return fail(APIC_EGEOMETRY, "darkfield correlation grid too large");
+    }
+    if (!(pr->flags & APIC_HOST_ONLY)) {
+        cudaError_t e = cudaGetDevice(&plan->device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, plan->device);
+        if (e != cudaSuccess) {
+            delete plan;
+            return cuda_fail(e, "device query");
+        }
+    }
+    if (pr->flags & APIC_HOST_ONLY) {
+        plan->host_only = true;
+        *out = plan;
+        return APIC_OK;
+    }
+    apic_status s = upload(plan);
+    if (s == APIC_OK) s = configure(plan);
+    if (s == APIC_OK) s = alloc_workspace(plan);
+    if (s != APIC_OK) {
+        apic_plan_destroy(plan);
+        return s;
+    }
+    *out = plan;
+    return APIC_OK;
+}
+
+apic_status apic_plan_destroy(apic_plan* plan) {
+    if (!plan) return APIC_OK;
+    if (!plan->host_only) {
+        cudaDeviceSynchronize();
+        for (void* p : plan->allocs) cudaFree(p);
+    }
+    delete plan;
+    return APIC_OK;
+}
+
+apic_status apic_plan_query(const apic_plan* plan, apic_plan_info* info) {
+    if (!plan || !info) return fail(APIC_EINVAL, "NULL plan or info");
+    const HostPlan& H = plan->host;
+    info->tile_h = H.h;
+    info->tile_w = H.w;
+    info->out_h = H.H;
+    info->out_w = H.W;
+    info->n_bf = H.n_bf;
+    info->n_df = H.n_df;
+    info->n_pupil = (int)H.pup_x.size();
+    info->n_aperture = (int)H.ap_x.size();
+    info->n_rows = (int)H.row_i.size();
+    info->n_df_used = (int)std::count_if(H.df.begin(), H.df.end(), [](const DarkfieldHost& d) { return d.used; });
+    info->fft_m = H.m;
+    info->pupil_rx = H.Rx;
+    info->pupil_ry = H.Ry;
+    return APIC_OK;
+}
+
+apic_status apic_plan_table(const apic_plan* plan, int which, int32_t* dst, size_t count) {
+    if (!plan || !dst) return fail(APIC_EINVAL, "NULL plan or destination");
+    const HostPlan& H = plan->host;
+    const std::vector<int>*xs = nullptr, *ys = nullptr;
+    switch (which) {
+        case APIC_TABLE_LEDS: xs = &H.led_x; ys = &H.led_y; break;
+        case APIC_TABLE_PUPIL: xs = &H.pup_x; ys = &H.pup_y; break;
+        case APIC_TABLE_APERTURE: xs = &H.ap_x; ys = &H.ap_y; break;
+        default: return fail(APIC_EINVAL, "unknown table");
+    }
+    if (count < 2 * xs->size()) return fail(APIC_EINVAL, "destination too small");
+    for (size_t i = 0; i < xs->size(); ++i) {
+        dst[2 * i] = (*xs)[i];
+        dst[2 * i + 1] = (*ys)[i];
+    }
+    return APIC_OK;
+}
+
+apic_status apic_plan_df_set(const apic_plan* plan, int index, int which, int32_t* dst, size_t count,
+                             int32_t* meta) {
+    if (!plan) return fail(APIC_EINVAL, "NULL plan");
+    const HostPlan& H = plan->host;
+    if (index < 0 || index >= (int)H.df.size()) return fail(APIC_EINVAL, "darkfield index out of range");
+    const DarkfieldHost& d = H.df[index];
+    const std::vector<int>*xs, *ys;
+    switch (which) {
+        case 0: xs = &d.U_x; ys = &d.U_y; break;
+        case 1: xs = &d.P_x; ys = &d.P_y; break;
+        case 2: xs = &d.Q_x; ys = &d.Q_y; break;
+        default: return fail(APIC_EINVAL, "which must be 0 (U), 1 (P) or 2 (Q)");
+    }
+    if (meta) {
+        meta[0] = d.led;
+        meta[1] = d.used ? 1 : 0;
+        meta[2] = (int32_t)d.U_x.size();
+        meta[3] = (int32_t)d.P_x.size();
+        meta[4] = (int32_t)d.Q_x.size();
+    }
+    if (!dst) return APIC_OK;
+    if (count < 2 * xs->size()) return fail(APIC_EINVAL, "destination too small");
+    for (size_t i = 0; i < xs->size(); ++i) {
+        dst[2 * i] = (*xs)[i];
+        dst[2 * i + 1] = (*ys)[i];
+    }
+    return APIC_OK;
+}
+
+apic_status apic_background(apic_plan* plan, int n_tiles, const float* I, float* c2, int32_t* status,
+                            void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!I || !status) return fail(APIC_EINVAL, "NULL intensity or status");
+    if (n_tiles == 0) return APIC_OK;
+    APIC_TRY_LAUNCH(launch_background(plan->dev, n_tiles, I, c2, status, plan->bg_c2, (cudaStream_t)stream));
+    return APIC_OK;
+}
+
+
+apic_status apic_kk_spectra(apic_plan* plan, int n_tiles, const float* I, float* xdisc, void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!I || !xdisc) return fail(APIC_EINVAL, "NULL intensity or output");
+    if (n_tiles == 0) return APIC_OK;
+    APIC_TRY_LAUNCH(launch_kk(plan->dev, plan->L, n_tiles, I, (float2*)xdisc, plan->kk_scratch, nullptr,
+                              (cudaStream_t)stream));
+    return APIC_OK;
+}
+
+apic_status apic_aberration(apic_plan* plan, int n_tiles, const float* xdisc, float* zern, void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!xdisc || !zern) return fail(APIC_EINVAL, "NULL input or output");
+    if (n_tiles == 0) return APIC_OK;
+    APIC_TRY_LAUNCH(launch_aberration(plan->dev, plan->L, n_tiles, (const float2*)xdisc, zern, plan->beta_scratch,
+                                      plan->ab_passes, nullptr, (cudaStream_t)stream));
+    return APIC_OK;
+}
+
+apic_status apic_stitch(apic_plan* plan, int n_tiles, const float* xdisc, const float* zern, float* spec,
+                        void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!xdisc || !zern || !spec) return fail(APIC_EINVAL, "NULL argument");
+    if (n_tiles == 0) return APIC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    APIC_TRY_LAUNCH(launch_phase(plan->dev, n_tiles, zern, plan->phi, st));
+    APIC_TRY_LAUNCH(launch_stitch(plan->dev, n_tiles, (const float2*)xdisc, plan->phi, (float2*)spec, nullptr, st));
+    return APIC_OK;
+}
+
+apic_status apic_darkfield(apic_plan* plan, int n_tiles, const float* I, const float* zern, float* spec,
+                           int32_t* status, void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!I || !zern || !spec) return fail(APIC_EINVAL, "NULL argument");
+    if (n_tiles == 0) return APIC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    APIC_TRY_LAUNCH(launch_phase(plan->dev, n_tiles, zern, plan->phi, st));
+    APIC_TRY_LAUNCH(launch_darkfield(plan->dev, plan->L, n_tiles, I, plan->phi, (float2*)spec, plan->df_scratch,
+                                     plan->df_per_block, plan->df_iters, plan->df_tol, status, st));
+    return APIC_OK;
+}
+
+apic_status apic_synthesize(apic_plan* plan, int n_tiles, const float* spec, float* field, void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!spec || !field) return fail(APIC_EINVAL, "NULL argument");
+    if (n_tiles == 0) return APIC_OK;
+    APIC_TRY_LAUNCH(launch_synthesize(plan->dev, plan->L, n_tiles, (const float2*)spec, (float2*)field, nullptr,
+                                      (cudaStream_t)stream));
+    return APIC_OK;
+}
+
+apic_status apic_pupil(apic_plan* plan, int n_tiles, const float* zern, float* pupil, void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!zern || !pupil) return fail(APIC_EINVAL, "NULL argument");
+    if (n_tiles == 0) return APIC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    APIC_TRY_LAUNCH(launch_phase(plan->dev, n_tiles, zern, plan->phi, st));
+    APIC_TRY_LAUNCH(launch_pupil(plan->dev, n_tiles, plan->phi, (float2*)pupil, nullptr, st));
+    return APIC_OK;
+}
+
+apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* I, float* field, float* zern,
+                                   float* pupil, int32_t* status, void* stream) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!I || !field || !zern) return fail(APIC_EINVAL, "NULL intensity, field or zernike buffer");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device)
+        return fail(APIC_EINVAL, "current device differs from the plan's device");
+    const DevPlan& D = plan->dev;
+    const Launch& L = plan->L;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
+    for (int t0 = 0; t0 < n_tiles; t0 += plan->max_tiles) {
+        const int nt = std::min(plan->max_tiles, n_tiles - t0);
+        const float* It = I + (size_t)t0 * in_tile;
+        int32_t* stt = status ? status + t0 : plan->status;
+        float* zt = zern + (size_t)t0 * APIC_N_ZERNIKE;
+        APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, plan->bg_thresh2, st));
+        APIC_TRY_LAUNCH(launch_kk(D, L, nt, It, plan->xdisc, plan->kk_scratch, stt, st));
+        APIC_TRY_LAUNCH(launch_aberration(D, L, nt, plan->xdisc, zt, plan->beta_scratch, plan->ab_passes, stt, st));
+        APIC_TRY_LAUNCH(launch_phase(D, nt, zt, plan->phi, st));
+        APIC_TRY_LAUNCH(launch_stitch(D, nt, plan->xdisc, plan->phi, plan->spec, stt, st));
+        APIC_TRY_LAUNCH(launch_darkfield(D, L, nt, It, plan->phi, plan->spec, plan->df_scratch, plan->df_per_block,
+                                         plan->df_iters, plan->df_tol, stt, st));
+        APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, (float2*)field + (size_t)t0 * out_tile, stt, st));
+        if (pupil)
+            APIC_TRY_LAUNCH(launch_pupil(D, nt, plan->phi, (float2*)pupil + (size_t)t0 * D.h * D.w, stt, st));
+    }
+    return APIC_OK;
+}
+
+apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* obj, const float* zern, float photons,
+                          uint64_t seed, float* I, void* stream) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!obj || !zern || !I) return fail(APIC_EINVAL, "NULL argument");
+    if (!(photons >= 0)) return fail(APIC_EINVAL, "photons must be >= 0");
+    const DevPlan& D = plan->dev;
+    const int chunk = std::min(plan->max_tiles, 64);
+    const size_t need = ((size_t)chunk * D.H * D.W + (size_t)plan->L.grid_sim * D.h * D.w) * sizeof(float2);
+    if (plan->sim_bytes < need) {
+        if (plan->sim_scratch) {
+            APIC_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+            cudaFree(plan->sim_scratch);
+            plan->allocs.erase(std::find(plan->allocs.begin(), plan->allocs.end(), (void*)plan->sim_scratch));
+            plan->sim_scratch = nullptr;
+            plan->sim_bytes = 0;
+        }
+        if ((s = dmalloc(plan, (void**)&plan->sim_scratch, need)) != APIC_OK) return s;
+        plan->sim_bytes = need;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t in_tile = (size_t)D.n_img * D.h * D.w, obj_tile = (size_t)D.H * D.W;
+    for (int t0 = 0; t0 < n_tiles; t0 += chunk) {
+        const int nt = std::min(chunk, n_tiles - t0);
+        APIC_TRY_LAUNCH(launch_phase(D, nt, zern + (size_t)t0 * APIC_N_ZERNIKE, plan->phi, st));
+        APIC_TRY_LAUNCH(launch_sim(D, plan->L, nt, (const float2*)obj + (size_t)t0 * obj_tile, plan->phi, photons,
+                                   (unsigned long long)seed + (unsigned long long)t0 * 0x100000001ull,
+                                   I + (size_t)t0 * in_tile, plan->sim_scratch, st));
+    }
+    return APIC_OK;
+}
+
+}  // extern "C"

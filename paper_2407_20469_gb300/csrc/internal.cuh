@@ -1,0 +1,98 @@
+// internal.cuh - device-side view of a plan and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace apic {
+
+constexpr int kThreads = 512;        // threads per block of the transform kernels
+constexpr int kChunk = 4096;         // complex elements per shared-memory chunk buffer
+
+// One darkfield image admitted by the geometry, in processing order.
+struct DevDF {
+    int led, kx, ky;
+    int N, M, NP;                    // |U|, |Q|, |P|
+    int u_off, q_off, p_off;         // offsets into the concatenated point arrays
+    int uy0, uy1, qy0, qy1, py0, py1;  // band of rows (signed y) of each set
+    int urp, qrp, prp;               // offsets into the concatenated row-pointer array
+};
+
+struct DevPlan {
+    int h, w, H, W, n_bf, n_df, n_img;
+    int npup, nap, nrows, m, n_used;
+    int max_N, max_M;
+    float Rx, Ry;
+    int pup_ax, pup_ay;
+    // pupil
+    const int* pup_x;
+    const int* pup_y;
+    const int* pup_lut;              // (2 pup_ay + 1)(2 pup_ax + 1)
+    const int* pup_rowptr;           // rows -pup_ay..pup_ay of the pupil list
+    const int* led_x;
+    const int* led_y;
+    const int* led_pup;              // NA-matching LED -> pupil index
+    // aberration rows
+    const int* row_il;               // i | (l << 16)
+    const int* row_pi;
+    const int* row_pl;
+    const int* row_nx;
+    const int* row_ny;
+    const float* row_A;              // [rows][12]
+    const double* Lval;              // 12 x 12 lower Cholesky factors
+    const double* Lgrad;
+    // aperture
+    const int* ap_x;
+    const int* ap_y;
+    const uint8_t* ap_bf;
+    const int* st_ptr;
+    const int* st_img;
+    const int* st_pup;
+    int ap_y0, ap_y1;
+    const int* ap_rowptr;            // rows ap_y0..ap_y1
+    // darkfield
+    const DevDF* df;
+    const int* dU_x; const int* dU_y; const int* dU_pup; const int* dU_ap;
+    const int* dP_x; const int* dP_y; const int* dP_pup; const int* dP_ap;
+    const int* dQ_x; const int* dQ_y;
+    const int* d_rowptr;
+    // twiddles
+    const float2* tw_n;              // n = h = w
+    const float2* tw_m;
+    const float2* tw_N;              // N = H = W
+};
+
+// Scratch sizes and grids decided at plan creation.
+struct Launch {
+    int grid_kk, grid_ab, grid_df, grid_syn, grid_sim;
+    size_t smem_kk, smem_df, smem_syn, smem_sim;
+};
+
+// Kernel launchers (return cudaError_t of the launch).
+cudaError_t launch_background(const DevPlan& P, int n_tiles, const float* I, float* c2, int32_t* status,
+                              float bg_thresh2, cudaStream_t st);
+cudaError_t launch_kk(const DevPlan& P, const Launch& L, int n_tiles, const float* I, float2* xdisc,
+                      float2* scratch, const int32_t* status, cudaStream_t st);
+cudaError_t launch_aberration(const DevPlan& P, const Launch& L, int n_tiles, const float2* xdisc, float* zern,
+                              float* beta_scratch, int passes, const int32_t* status, cudaStream_t st);
+cudaError_t launch_phase(const DevPlan& P, int n_tiles, const float* zern, float* phi, cudaStream_t st);
+cudaError_t launch_stitch(const DevPlan& P, int n_tiles, const float2* xdisc, const float* phi, float2* spec,
+                          const int32_t* status, cudaStream_t st);
+cudaError_t launch_darkfield(const DevPlan& P, const Launch& L, int n_tiles, const float* I, const float* phi,
+                             float2* spec, void* scratch, size_t scratch_per_block, int iters, float tol,
+                             int32_t* status, cudaStream_t st);
+cudaError_t launch_synthesize(const DevPlan& P, const Launch& L, int n_tiles, const float2* spec, float2* field,
+                              const int32_t* status, cudaStream_t st);
+cudaError_t launch_pupil(const DevPlan& P, int n_tiles, const float* phi, float2* pupil, const int32_t* status,
+                         cudaStream_t st);
+cudaError_t launch_sim(const DevPlan& P, const Launch& L, int n_tiles, const float2* obj, const float* phi,
+                       float photons, unsigned long long seed, float* I, float2* ohat_scratch, cudaStream_t st);
+
+size_t df_scratch_bytes(const DevPlan& P);
+
+// Sets the dynamic shared-memory limit of a transform kernel and returns its
+// resident blocks per SM (0 on error). which: 0 kk, 1 aberration, 2 darkfield,
+// 3 synthesis, 4 simulated images, 5 object transform.
+int configure_kernel(int which, size_t smem);
+
+}  // namespace apic
