@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 APIC library (one JSON line on stdout).
+
+Workload (one step): 512 tiles of 256 x 256 low-resolution pixels, 8 NA-matching
++ 16 darkfield images each (illumination NA 0.30 / 0.38), 0.25 NA, 0.52 um,
+0.345 um pixels, 2x upsampling to 512 x 512, per-tile Zernike coefficients
+varying as a 2-D quadratic across a 16 x 32 tile grid, Poisson noise at 1e4
+photons per pixel; the sample is a smoothed random transmission (amplitude
+0.8-1.0, phase 0-pi). Inputs are synthesised on the device before timing and
+are larger than L2 (3.2 GB of intensities per step).
+
+value: output Mpx/s = tiles * 512^2 * steps / timed seconds, all ranks.
+e2e:   the same through host buffers (pinned H2D of the intensities and D2H of
+       the fields inside the timed region).
+roofline: the darkfield kernel (the dominant one) against the FP32 ALU peak.
+cpu_baseline: the float64 checker on one tile of the same workload, on the
+       host cores; the GPU result of that tile is compared with it (parity).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU (torchrun): each rank reconstructs its own 512 tiles (weak scaling,
+no collective on the data path); barrier + max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "APIC output Mpx/s at <=1e-3 rel L2 vs FP64 oracle; % of HBM roofline"
+WORKLOAD = ("512 tiles x 256x256 low-res (512x512 output), 8 NA-matching + 16 darkfield images, "
+            "quadratic field-dependent Zernike over a 16x32 tile grid, Poisson 1e4 photons/px")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "darkfield_traffic.json")
+DF_SOURCES = ["kernels_df.cu", "passes.cuh", "fft.cuh", "common.cuh", "internal.cuh"]
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["apic", "reference"], default="apic")
+    ap.add_argument("--tiles", type=int, default=512)
+    ap.add_argument("--tile", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=2407)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- inputs
+
+def field_zernike(rows=16, cols=32, seed=2407):
+    """Per-tile Noll coefficients from a 2-D quadratic field over the tile grid."""
+    from paper_2407_20469_gb300 import synth
+    rng = np.random.default_rng(seed)
+    table = synth.quadratic_field(rng, 1.0)
+    uv = synth.tile_grid_uv(rows, cols)
+    return np.stack([synth.coefficients_at(table, u, v) for u, v in uv]).astype(np.float32)
+
+
+def device_objects(T, H, seed, device, sigma=4.0):
+    """Smoothed random transmissions (amplitude 0.8-1.0, phase 0-pi), interleaved complex64."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    f = torch.fft.fftfreq(H, device=device)
+    gauss = torch.exp(-2.0 * (math.pi * sigma) ** 2 * (f[:, None] ** 2 + f[None, :] ** 2))
+    out = torch.empty((T, H, 2 * H), dtype=torch.float32, device=device)
+    for t0 in range(0, T, 64):
+        t1 = min(T, t0 + 64)
+        z = torch.randn((2, t1 - t0, H, H), device=device, generator=g)
+        s = torch.fft.ifft2(torch.fft.fft2(z) * gauss).real
+        lo = s.amin(dim=(-2, -1), keepdim=True)
+        hi = s.amax(dim=(-2, -1), keepdim=True)
+        s = (s - lo) / (hi - lo)
+        amp = 0.8 + 0.2 * s[0]
+        ph = math.pi * s[1]
+        out[t0:t1] = torch.view_as_real(torch.polar(amp, ph)).reshape(t1 - t0, H, 2 * H)
+    return out
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def oracle_tile_sample(n, seed):
+    """One tile of the workload from the checker's forward model (float64 on the host)."""
+    from oracle import forward, grid
+    from paper_2407_20469_gb300 import synth
+    ill = synth.illumination()
+    g = grid.Geometry(n, n, float(synth.NA), float(synth.WAVELENGTH_UM), float(synth.PIXEL_UM), 2)
+    k = grid.snap_leds(ill.kx, ill.ky, ill.n_bf, g)
+    rng = np.random.default_rng(seed)
+    obj = synth.sample_object(rng, g.H, g.W, 4.0)
+    c = field_zernike()[0].astype(np.float64)
+    I = forward.intensity_stack(obj, g, k, c, photons=synth.PHOTONS, rng=rng).astype(np.float32)
+    return I, g, k, ill
+
+
+def run_oracle(I, g, k, n_bf):
+    from oracle import apic as oapic
+    t0 = time.perf_counter()
+    res = oapic.reconstruct_tile(I.astype(np.float64), g, k, n_bf)
+    return res, time.perf_counter() - t0
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.tile
+    I, g, k, ill = oracle_tile_sample(n, args.seed)
+    for _ in range(args.warmup):
+        run_oracle(I, g, k, ill.n_bf)
+    times = []
+    for _ in range(args.steps):
+        times.append(run_oracle(I, g, k, ill.n_bf)[1])
+    total = sum(times)
+    out_px = (2 * n) ** 2
+    value = args.steps * out_px / total / 1e6
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"1 tile of {n}x{n} per step", "tiles_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": cores, "kind": "oracle",
+                         "sample": f"1 tile of {n}x{n} (8+16 images) per step, numpy float64"},
+        "e2e": {"value": value, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def df_flops_per_solve(n, m, iters):
+    """Algorithmic FP32 flops of darkfield solves: 5 N log2 N per complex N-point 2-D FFT.
+
+    Per solve: F(I_j) (one n x n transform), the known field and P*P (two m x m),
+    the first C^H r (two); per CGLS iteration C d and C^H r (four m x m).
+    """
+    fft = lambda s: 5.0 * s * s * math.log2(s * s)
+    return fft(n) + 4 * fft(m), 4 * fft(m) * iters
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in DF_SOURCES:
+        with open(os.path.join(ROOT, "paper_2407_20469_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2407_20469_gb300 import apic, build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        if rank == 0:
+            build.build()
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+    else:
+        build.build()
+    device = torch.device("cuda", torch.cuda.current_device())
+
+    n, T = args.tile, args.tiles
+    ill = synth.illumination()
+    plan = apic.Plan.from_illumination(n, ill, max_tiles=T)
+    info = plan.info
+    H = info.out_h
+    n_img = info.n_bf + info.n_df
+
+    # ---- inputs (device), outside the timed region
+    zern_true = torch.from_numpy(np.resize(field_zernike(), (T, 15))).to(device)
+    obj = device_objects(T, H, args.seed + 7919 * rank, device)
+    I = torch.empty((T, n_img, n, n), dtype=torch.float32, device=device)
+    plan.simulate(T, obj, zern_true, synth.PHOTONS, args.seed + rank, I)
+    del obj
+    field = torch.empty((T, H, 2 * H), dtype=torch.float32, device=device)
+    zern = torch.empty((T, 15), dtype=torch.float32, device=device)
+    status = torch.empty((T,), dtype=torch.int32, device=device)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        plan.reconstruct_batch(T, I, field, zern, None, status)
+    torch.cuda.synchronize()
+    plan.timing(True)
+    plan.stage_ms(reset=True)
+    plan.counters(reset=True)
+
+    props = torch.cuda.get_device_properties(device)
+    uuid = str(getattr(props, "uuid", ""))
+    gpu_id = ("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(device.index))
+    clocks = ClockSampler(gpu_id)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.5)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.reconstruct_batch(T, I, field, zern, None, status)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stage, calls = plan.stage_ms(reset=True)
+    cnt = plan.counters(reset=True)
+    plan.timing(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status_np = status.cpu().numpy()
+
+    # ---- end to end through host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        I_host = torch.empty(I.shape, dtype=torch.float32, pin_memory=True)
+        I_host.copy_(I)
+        f_host = torch.empty(field.shape, dtype=torch.float32, pin_memory=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.e2e_steps):
+            I.copy_(I_host, non_blocking=True)
+            plan.reconstruct_batch(T, I, field, zern, None, status)
+            f_host.copy_(field, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        if world > 1:
+            t = torch.tensor([ems], dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * T * H * H * args.e2e_steps / (ems / 1e3) / 1e6, "unit": "Mpx/s",
+               "h2d_bytes_per_step": int(I.numel() * 4), "d2h_bytes_per_step": int(field.numel() * 4),
+               "steps": args.e2e_steps}
+        del I_host, f_host
+
+    # ---- roofline of the darkfield kernel (algorithmic flops / live event time)
+    df_ms = stage["darkfield"] / max(calls, 1)
+    setup, per_it = df_flops_per_solve(n, info.fft_m, 1)
+    solves = cnt["df_solves"] / max(calls, 1)
+    iters = cnt["cg_iterations"] / max(calls, 1)
+    flops = solves * setup + iters * per_it
+    achieved = flops / (df_ms / 1e3) / 1e12
+    traffic = None
+    if os.path.exists(TRAFFIC):
+        with open(TRAFFIC) as fh:
+            tr = json.load(fh)
+        if tr.get("source_sha") == source_sha() and tr.get("tile") == n and tr.get("tiles") == T:
+            traffic = tr.get("dram_bytes_per_launch")
+    roofline = {"bound": "alu", "kernel": "k_darkfield", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_kind": "derived FP32 CUDA-core peak (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                "launch_ms": df_ms, "cg_iterations_per_launch": iters, "solves_per_launch": solves,
+                "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage.items()}}
+
+    value = world * T * H * H * args.steps / (ms / 1e3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tiles_per_gpu": T, "tile": n, "output": H, "images": n_img,
+                   "l2": "inputs_larger_than_l2 (3.2 GB intensities per step)", "launch": "direct C-ABI calls",
+                   "tiles_per_s": world * T * args.steps / (ms / 1e3),
+                   "tiles_status_nonzero": int(np.count_nonzero(status_np))},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": cnt["launches"], "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        I1, g1, k1, ill1 = oracle_tile_sample(n, args.seed)
+        res, secs = run_oracle(I1, g1, k1, ill1.n_bf)
+        line["cpu_baseline"] = {"value": (2 * n) ** 2 / secs / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"1 tile of {n}x{n} (8+16 images) of the workload, numpy float64, "
+                                          f"{secs:.1f} s"}
+        # parity of the GPU path on that same tile
+        Id = torch.from_numpy(I1).to(device)[None].contiguous()
+        f1 = torch.empty((1, H, 2 * H), dtype=torch.float32, device=device)
+        z1 = torch.empty((1, 15), dtype=torch.float32, device=device)
+        plan.reconstruct_batch(1, Id, f1, z1, None, None)
+        torch.cuda.synchronize()
+        a = f1[0].cpu().numpy().astype(np.float64)
+        est = a[:, 0::2] + 1j * a[:, 1::2]
+        zr = np.vdot(est, res.field)
+        est = est * (zr / abs(zr))
+        line["parity"] = {"field_rel_l2": float(np.linalg.norm(est - res.field) / np.linalg.norm(res.field)),
+                          "pupil_rms_rad": float(np.sqrt(np.sum((z1[0].cpu().numpy()[3:] - res.c15[3:]) ** 2))),
+                          "sample": "the cpu_baseline tile"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -163,6 +163,28 @@ apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* d_
                                    float* d_field, float* d_zernike, float* d_pupil,
                                    int32_t* d_tile_status, void* stream);
 
+/*
+ * Work counters of a plan since creation or the last reset, for throughput
+ * accounting: h_out[0] kernel launches issued, h_out[1] CGLS iterations run,
+ * h_out[2] darkfield least-squares solves run. Up to n values are written.
+ * Synchronises the device (reads a device counter); reset != 0 zeroes them.
+ */
+apic_status apic_plan_counters(apic_plan* plan, int64_t* h_out, int n, int reset);
+
+/*
+ * Per-stage timing of apic_reconstruct_batch with CUDA events recorded on the
+ * call's stream around every stage launch (a ring of 1024 calls; calls made
+ * while the stream is being captured into a graph are not timed).
+ * apic_plan_timing(plan, 1) creates the events, (plan, 0) stops recording.
+ * apic_plan_stage_ms synchronises the device and writes, for stage s, the
+ * summed milliseconds over the recorded calls to h_ms[s] (s: 0 background,
+ * 1 Kramers-Kronig, 2 aberration, 3 stitch, 4 darkfield, 5 synthesis,
+ * 6 pupil; n <= 7 values) and the number of calls to *h_calls (may be NULL);
+ * reset != 0 clears the ring.
+ */
+apic_status apic_plan_timing(apic_plan* plan, int enable);
+apic_status apic_plan_stage_ms(apic_plan* plan, double* h_ms, int n, int32_t* h_calls, int reset);
+
 /* ---- Stages of apic_reconstruct_batch, for testing and custom pipelines ---- */
 
 /*

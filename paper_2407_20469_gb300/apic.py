@@ -25,7 +25,8 @@ APIC_TABLE_LEDS, APIC_TABLE_PUPIL, APIC_TABLE_APERTURE = 0, 1, 2
 # Every symbol include/apic.h declares (checked by the CPU test suite).
 EXPORTS = [
     "apic_status_string", "apic_last_error", "apic_plan_create", "apic_plan_destroy",
-    "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_reconstruct_batch", "apic_background",
+    "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_counters", "apic_plan_timing",
+    "apic_plan_stage_ms", "apic_reconstruct_batch", "apic_background",
     "apic_kk_spectra", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
     "apic_pupil", "apic_simulate",
 ]
@@ -70,6 +71,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_plan_query": (i32, [vp, C.POINTER(apic_plan_info)]),
         "apic_plan_table": (i32, [vp, i32, C.POINTER(C.c_int32), sz]),
         "apic_plan_df_set": (i32, [vp, i32, i32, C.POINTER(C.c_int32), sz, C.POINTER(C.c_int32)]),
+        "apic_plan_counters": (i32, [vp, C.POINTER(C.c_int64), i32, i32]),
+        "apic_plan_timing": (i32, [vp, i32]),
+        "apic_plan_stage_ms": (i32, [vp, C.POINTER(C.c_double), i32, C.POINTER(C.c_int32), i32]),
         "apic_reconstruct_batch": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "apic_background": (i32, [vp, i32, vp, vp, vp, vp]),
         "apic_kk_spectra": (i32, [vp, i32, vp, vp, vp]),
@@ -177,6 +181,26 @@ class Plan:
         _check(lib.apic_plan_df_set(self.handle, index, which, out.ctypes.data_as(P32), out.size,
                                     meta.ctypes.data_as(P32)), "apic_plan_df_set")
         return out, meta
+
+    def counters(self, reset: bool = False) -> dict:
+        """Work counters: kernel launches, CGLS iterations, darkfield solves (synchronises)."""
+        out = np.zeros(3, dtype=np.int64)
+        _check(load().apic_plan_counters(self.handle, out.ctypes.data_as(C.POINTER(C.c_int64)), 3, int(reset)),
+               "apic_plan_counters")
+        return {"launches": int(out[0]), "cg_iterations": int(out[1]), "df_solves": int(out[2])}
+
+    STAGES = ("background", "kk", "aberration", "stitch", "darkfield", "synthesize", "pupil")
+
+    def timing(self, enable: bool = True):
+        _check(load().apic_plan_timing(self.handle, int(enable)), "apic_plan_timing")
+
+    def stage_ms(self, reset: bool = False):
+        """({stage: summed ms}, calls) over the timed reconstruct_batch calls (synchronises)."""
+        ms = np.zeros(7, dtype=np.float64)
+        calls = C.c_int32(0)
+        _check(load().apic_plan_stage_ms(self.handle, ms.ctypes.data_as(C.POINTER(C.c_double)), 7, C.byref(calls),
+                                         int(reset)), "apic_plan_stage_ms")
+        return dict(zip(self.STAGES, ms.tolist())), int(calls.value)
 
     # -- entry points (same names as the C interface, without the prefix)
     def reconstruct_batch(self, n_tiles, intensity, field, zernike, pupil=None, tile_status=None, stream=None):

@@ -92,6 +92,13 @@ struct apic_plan {
     size_t sim_bytes = 0;
     std::vector<void*> allocs;
     bool host_only = false;
+    unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
+    long long launches = 0;                      // kernel launches issued
+    // stage timing: ring of kTimingSlots calls x kStages x {start, stop}
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    int t_next = 0, t_used = 0;
+    static constexpr int kStages = 7, kTimingSlots = 1024;
 };
 
 namespace {
@@ -287,6 +294,8 @@ apic_status alloc_workspace(apic_plan* p) {
     if ((s = dmalloc(p, (void**)&p->spec, T * D.nap * sizeof(float2))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->status, T * sizeof(int32_t))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->c2, T * sizeof(float))) != APIC_OK) return s;
+    if ((s = dmalloc(p, (void**)&p->d_counters, 4 * sizeof(unsigned long long))) != APIC_OK) return s;
+    APIC_TRY_CUDA(cudaMemset(p->d_counters, 0, 4 * sizeof(unsigned long long)));
     if ((s = dmalloc(p, (void**)&p->kk_scratch, (size_t)p->L.grid_kk * D.h * D.h * sizeof(float2))) != APIC_OK)
         return s;
     if ((s = dmalloc(p, (void**)&p->beta_scratch, (size_t)p->L.grid_ab * D.nrows * sizeof(float))) != APIC_OK)
@@ -317,7 +326,28 @@ apic_status check_stage(const apic_plan* plan, int n_tiles) {
     do {                                                       \
         cudaError_t _e = (expr);                               \
         if (_e != cudaSuccess) return cuda_fail(_e, #expr);    \
+        ++plan->launches;                                      \
     } while (0)
+
+// Records the start (end = 0) or stop (end = 1) event of a stage in the
+// current ring slot; a no-op unless timing is on for this call.
+struct StageTimer {
+    apic_plan* p;
+    cudaStream_t st;
+    int slot = -1;
+    StageTimer(apic_plan* plan, cudaStream_t s) : p(plan), st(s) {
+        if (!p->timing) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        slot = p->t_next;
+        p->t_next = (p->t_next + 1) % apic_plan::kTimingSlots;
+        p->t_used = std::min(p->t_used + 1, apic_plan::kTimingSlots);
+    }
+    void mark(int stage, int end) {
+        if (slot < 0) return;
+        cudaEventRecord(p->events[((size_t)slot * apic_plan::kStages + stage) * 2 + end], st);
+    }
+};
 
 }  // namespace
 
@@ -412,6 +442,7 @@ apic_status apic_plan_destroy(apic_plan* plan) {
     if (!plan->host_only) {
         cudaDeviceSynchronize();
         for (void* p : plan->allocs) cudaFree(p);
+        for (auto e : plan->events) cudaEventDestroy(e);
     }
     delete plan;
     return APIC_OK;
@@ -451,6 +482,54 @@ apic_status apic_plan_table(const apic_plan* plan, int which, int32_t* dst, size
         dst[2 * i] = (*xs)[i];
         dst[2 * i + 1] = (*ys)[i];
     }
+    return APIC_OK;
+}
+
+apic_status apic_plan_timing(apic_plan* plan, int enable) {
+    if (!plan) return fail(APIC_EINVAL, "NULL plan");
+    if (plan->host_only) return fail(APIC_EINVAL, "plan was created with APIC_HOST_ONLY");
+    if (enable && plan->events.empty()) {
+        plan->events.resize((size_t)apic_plan::kTimingSlots * apic_plan::kStages * 2);
+        for (auto& e : plan->events) APIC_TRY_CUDA(cudaEventCreate(&e));
+    }
+    plan->timing = enable != 0;
+    return APIC_OK;
+}
+
+apic_status apic_plan_stage_ms(apic_plan* plan, double* ms, int n, int32_t* calls, int reset) {
+    if (!plan || (!ms && n > 0)) return fail(APIC_EINVAL, "NULL plan or output");
+    if (plan->host_only) return fail(APIC_EINVAL, "plan was created with APIC_HOST_ONLY");
+    APIC_TRY_CUDA(cudaDeviceSynchronize());
+    double acc[apic_plan::kStages] = {0};
+    const int used = plan->t_used;
+    for (int k = 0; k < used && !plan->events.empty(); ++k) {
+        const int slot = ((plan->t_next - 1 - k) % apic_plan::kTimingSlots + apic_plan::kTimingSlots) %
+                         apic_plan::kTimingSlots;
+        for (int sidx = 0; sidx < apic_plan::kStages; ++sidx) {
+            float v = 0.f;
+            const cudaEvent_t a = plan->events[((size_t)slot * apic_plan::kStages + sidx) * 2];
+            const cudaEvent_t b = plan->events[((size_t)slot * apic_plan::kStages + sidx) * 2 + 1];
+            if (cudaEventElapsedTime(&v, a, b) == cudaSuccess) acc[sidx] += v;
+            else cudaGetLastError();
+        }
+    }
+    for (int i = 0; i < n && i < apic_plan::kStages; ++i) ms[i] = acc[i];
+    if (calls) *calls = used;
+    if (reset) plan->t_used = 0;
+    return APIC_OK;
+}
+
+apic_status apic_plan_counters(apic_plan* plan, int64_t* out, int n, int reset) {
+    if (!plan || (!out && n > 0)) return fail(APIC_EINVAL, "NULL plan or output");
+    unsigned long long c[4] = {0, 0, 0, 0};
+    if (!plan->host_only) {
+        APIC_TRY_CUDA(cudaDeviceSynchronize());
+        APIC_TRY_CUDA(cudaMemcpy(c, plan->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+        if (reset) APIC_TRY_CUDA(cudaMemset(plan->d_counters, 0, sizeof(c)));
+    }
+    const int64_t v[3] = {plan->launches, (int64_t)c[1], (int64_t)c[2]};
+    for (int i = 0; i < n && i < 3; ++i) out[i] = v[i];
+    if (reset) plan->launches = 0;
     return APIC_OK;
 }
 
@@ -535,7 +614,7 @@ apic_status apic_darkfield(apic_plan* plan, int n_tiles, const float* I, const f
     cudaStream_t st = (cudaStream_t)stream;
     APIC_TRY_LAUNCH(launch_phase(plan->dev, n_tiles, zern, plan->phi, st));
     APIC_TRY_LAUNCH(launch_darkfield(plan->dev, plan->L, n_tiles, I, plan->phi, (float2*)spec, plan->df_scratch,
-                                     plan->df_per_block, plan->df_iters, plan->df_tol, status, st));
+                                     plan->df_per_block, plan->df_iters, plan->df_tol, status, plan->d_counters, st));
     return APIC_OK;
 }
 
@@ -572,21 +651,38 @@ apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* I,
     const Launch& L = plan->L;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
+    StageTimer tm(plan, st);
     for (int t0 = 0; t0 < n_tiles; t0 += plan->max_tiles) {
         const int nt = std::min(plan->max_tiles, n_tiles - t0);
+        const bool first = t0 == 0, last = t0 + nt >= n_tiles;
         const float* It = I + (size_t)t0 * in_tile;
         int32_t* stt = status ? status + t0 : plan->status;
         float* zt = zern + (size_t)t0 * APIC_N_ZERNIKE;
+        // with several chunks a stage's interval spans from its first start to its last stop
+        if (first) tm.mark(0, 0);
         APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, plan->bg_thresh2, st));
+        if (last) tm.mark(0, 1);
+        if (first) tm.mark(1, 0);
         APIC_TRY_LAUNCH(launch_kk(D, L, nt, It, plan->xdisc, plan->kk_scratch, stt, st));
+        if (last) tm.mark(1, 1);
+        if (first) tm.mark(2, 0);
         APIC_TRY_LAUNCH(launch_aberration(D, L, nt, plan->xdisc, zt, plan->beta_scratch, plan->ab_passes, stt, st));
+        if (last) tm.mark(2, 1);
+        if (first) tm.mark(3, 0);
         APIC_TRY_LAUNCH(launch_phase(D, nt, zt, plan->phi, st));
         APIC_TRY_LAUNCH(launch_stitch(D, nt, plan->xdisc, plan->phi, plan->spec, stt, st));
+        if (last) tm.mark(3, 1);
+        if (first) tm.mark(4, 0);
         APIC_TRY_LAUNCH(launch_darkfield(D, L, nt, It, plan->phi, plan->spec, plan->df_scratch, plan->df_per_block,
-                                         plan->df_iters, plan->df_tol, stt, st));
+                                         plan->df_iters, plan->df_tol, stt, plan->d_counters, st));
+        if (last) tm.mark(4, 1);
+        if (first) tm.mark(5, 0);
         APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, (float2*)field + (size_t)t0 * out_tile, stt, st));
+        if (last) tm.mark(5, 1);
+        if (first) tm.mark(6, 0);
         if (pupil)
             APIC_TRY_LAUNCH(launch_pupil(D, nt, plan->phi, (float2*)pupil + (size_t)t0 * D.h * D.w, stt, st));
+        if (last) tm.mark(6, 1);
     }
     return APIC_OK;
 }

@@ -80,7 +80,7 @@ cudaError_t launch_stitch(const DevPlan& P, int n_tiles, const float2* xdisc, co
                           const int32_t* status, cudaStream_t st);
 cudaError_t launch_darkfield(const DevPlan& P, const Launch& L, int n_tiles, const float* I, const float* phi,
                              float2* spec, void* scratch, size_t scratch_per_block, int iters, float tol,
-                             int32_t* status, cudaStream_t st);
+                             int32_t* status, unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_synthesize(const DevPlan& P, const Launch& L, int n_tiles, const float2* spec, float2* field,
                               const int32_t* status, cudaStream_t st);
 cudaError_t launch_pupil(const DevPlan& P, int n_tiles, const float* phi, float2* pupil, const int32_t* status,

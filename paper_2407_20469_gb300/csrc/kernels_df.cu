@@ -32,7 +32,8 @@ size_t df_scratch_bytes(const DevPlan& P) {
 __global__ void __launch_bounds__(kThreads) k_darkfield(DevPlan P, int n_tiles, const float* __restrict__ I,
                                                         const float* __restrict__ phi, float2* __restrict__ spec,
                                                         char* __restrict__ scratch, size_t per_block, int iters,
-                                                        float tol, int32_t* __restrict__ status) {
+                                                        float tol, int32_t* __restrict__ status,
+                                                        unsigned long long* __restrict__ counters) {
     extern __shared__ float4 smem4[];
     float2* sm = reinterpret_cast<float2*>(smem4);
     const int n = P.h, m = P.m;
@@ -150,7 +151,8 @@ __global__ void __launch_bounds__(kThreads) k_darkfield(DevPlan P, int n_tiles, 
             double gamma = gamma0;
             bool conv = !(gamma0 > 1e-300);
             const double stop = (double)tol * (double)tol * gamma0;
-            for (int it = 0; it < iters && !conv; ++it) {
+            int it = 0;
+            for (; it < iters && !conv; ++it) {
                 const double delta = apply_C();
                 if (!(delta > 0)) break;
                 const double alpha = gamma / delta;
@@ -172,6 +174,10 @@ __global__ void __launch_bounds__(kThreads) k_darkfield(DevPlan P, int n_tiles, 
                 conv = gnew <= stop;
             }
             if (!conv) notconv = true;
+            if (threadIdx.x == 0 && counters) {
+                atomicAdd(counters + 1, (unsigned long long)it);
+                atomicAdd(counters + 2, 1ull);
+            }
             // ---- O(K) = u(c) exp(-j phi(c)) on U
             for (int e = threadIdx.x; e < N; e += blockDim.x) {
                 float sn, cs;
@@ -187,10 +193,10 @@ __global__ void __launch_bounds__(kThreads) k_darkfield(DevPlan P, int n_tiles, 
 
 cudaError_t launch_darkfield(const DevPlan& P, const Launch& L, int n_tiles, const float* I, const float* phi,
                              float2* spec, void* scratch, size_t scratch_per_block, int iters, float tol,
-                             int32_t* status, cudaStream_t st) {
+                             int32_t* status, unsigned long long* counters, cudaStream_t st) {
     const int grid = min(L.grid_df, n_tiles);
     k_darkfield<<<grid, kThreads, L.smem_df, st>>>(P, n_tiles, I, phi, spec, (char*)scratch, scratch_per_block,
-                                                   iters, tol, status);
+                                                   iters, tol, status, counters);
     return cudaGetLastError();
 }
 

@@ -377,7 +377,8 @@ cudaError_t launch_pupil(const DevPlan& P, int n_tiles, const float* phi, float2
 }  // namespace apic
 
 namespace apic {
-__global__ void k_darkfield(DevPlan, int, const float*, const float*, float2*, char*, size_t, int, float, int32_t*);
+__global__ void k_darkfield(DevPlan, int, const float*, const float*, float2*, char*, size_t, int, float, int32_t*,
+                            unsigned long long*);
 __global__ void k_synthesize(DevPlan, int, const float2*, float2*, const int32_t*);
 __global__ void k_sim_images(DevPlan, int, const float2*, const float*, float, unsigned long long, float*, float2*);
 __global__ void k_sim_object(DevPlan, int, const float2*, float2*);
