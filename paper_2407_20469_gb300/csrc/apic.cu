@@ -92,6 +92,9 @@ struct apic_plan {
     size_t sim_bytes = 0;
     std::vector<void*> allocs;
     bool host_only = false;
+    bool use_reg = false;        // register-FFT darkfield kernel
+    size_t smem_dfr = 0;
+    int grid_dfr = 0;
     unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
     long long launches = 0;                      // kernel launches issued
     // stage timing: ring of kTimingSlots calls x kStages x {start, stop}
@@ -157,7 +160,9 @@ apic_status upload(apic_plan* plan) {
     // darkfield tables
     std::vector<DevDF> dfs;
     std::vector<int> ux, uy, up, ua, px, py, pp, pa, qx, qy, rp;
-    int maxN = 1, maxM = 1;
+    std::vector<unsigned> qmask;
+    int maxN = 1, maxM = 1, band_u = 1, band_q = 1;
+    const int mr = H.mr;
     for (const auto& d : H.df) {
         if (!d.used) continue;
         DevDF e{};
@@ -203,16 +208,33 @@ apic_status upload(apic_plan* plan) {
         e.prp = push_rp(d.P_y, e.py0, e.py1);
         maxN = std::max(maxN, e.N);
         maxM = std::max(maxM, e.M);
+        band_u = std::max(band_u, std::max(e.uy1 - e.uy0 + 1, e.py1 - e.py0 + 1));
+        band_q = std::max(band_q, e.qy1 - e.qy0 + 1);
+        e.qmask_off = (int)qmask.size();
+        if (mr > 0) {   // Q membership per band row on the register grid
+            const int words = mr / 32;
+            qmask.resize(qmask.size() + (size_t)(e.qy1 - e.qy0 + 1) * words, 0u);
+            for (size_t q = 0; q < d.Q_x.size(); ++q) {
+                const int xi = ((d.Q_x[q] % mr) + mr) % mr;
+                qmask[e.qmask_off + (size_t)(d.Q_y[q] - e.qy0) * words + (xi >> 5)] |= 1u << (xi & 31);
+            }
+        }
         dfs.push_back(e);
     }
     D.n_used = (int)dfs.size();
     D.max_N = maxN;
     D.max_M = maxM;
+    D.mr = mr;
+    D.band_u = band_u;
+    D.band_q = band_q;
+    if (qmask.empty()) qmask.push_back(0u);
     const size_t o_df = A.add(dfs);
     const size_t o_ux = A.add(ux), o_uy = A.add(uy), o_up = A.add(up), o_ua = A.add(ua);
     const size_t o_px = A.add(px), o_py = A.add(py), o_pp = A.add(pp), o_pa = A.add(pa);
     const size_t o_qx = A.add(qx), o_qy = A.add(qy), o_rp = A.add(rp);
     const size_t o_twn = A.add(twiddles(H.h)), o_twm = A.add(twiddles(H.m)), o_twN = A.add(twiddles(H.H));
+    const size_t o_twr = A.add(twiddles(std::max(mr, 16)));
+    const size_t o_qm = A.add(qmask);
 
     void* base = nullptr;
     apic_status s = dmalloc(plan, &base, A.host.size());
@@ -257,6 +279,8 @@ apic_status upload(apic_plan* plan) {
     D.tw_n = (const float2*)(b + o_twn);
     D.tw_m = (const float2*)(b + o_twm);
     D.tw_N = (const float2*)(b + o_twN);
+    D.tw_r = (const float2*)(b + o_twr);
+    D.d_qmask = (const unsigned*)(b + o_qm);
     return APIC_OK;
 }
 
@@ -276,6 +300,22 @@ apic_status configure(apic_plan* plan) {
         return fail(APIC_ECUDA, "kernel configuration (shared memory / occupancy) failed");
     }
     const int sms = plan->sms;
+    plan->use_reg = false;
+    if (D.mr > 0 && !(plan->params.flags & APIC_LEGACY_DF)) {
+        const size_t smem = dfr_smem_bytes(D.mr / 16, D.h / 16, std::max(D.band_q, D.band_u), D.max_N);
+        int dev_max = 0;
+        cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
+        if (smem <= (size_t)dev_max) {
+            const int occ = configure_dfr(D.mr / 16, D.h / 16, smem);
+            if (occ > 0) {
+                plan->use_reg = true;
+                plan->smem_dfr = smem;
+                plan->grid_dfr = sms * occ;
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
     L.grid_kk = sms * o_kk;
     L.grid_ab = sms * std::min(o_ab, 2);
     L.grid_df = sms * std::min(o_df, 2);
@@ -300,9 +340,22 @@ apic_status alloc_workspace(apic_plan* p) {
         return s;
     if ((s = dmalloc(p, (void**)&p->beta_scratch, (size_t)p->L.grid_ab * D.nrows * sizeof(float))) != APIC_OK)
         return s;
-    p->df_per_block = df_scratch_bytes(D);
-    if ((s = dmalloc(p, &p->df_scratch, (size_t)p->L.grid_df * p->df_per_block)) != APIC_OK) return s;
+    if (p->use_reg) {
+        p->df_per_block = dfr_scratch_bytes(D);
+        if ((s = dmalloc(p, &p->df_scratch, (size_t)p->grid_dfr * p->df_per_block)) != APIC_OK) return s;
+    } else {
+        p->df_per_block = df_scratch_bytes(D);
+        if ((s = dmalloc(p, &p->df_scratch, (size_t)p->L.grid_df * p->df_per_block)) != APIC_OK) return s;
+    }
     return APIC_OK;
+}
+
+cudaError_t launch_df(apic_plan* p, int n_tiles, const float* I, float2* spec, int32_t* status, cudaStream_t st) {
+    if (p->use_reg)
+        return launch_darkfield_reg(p->dev, p->grid_dfr, p->smem_dfr, n_tiles, I, p->phi, spec, p->df_scratch,
+                                    p->df_per_block, p->df_iters, p->df_tol, status, p->d_counters, st);
+    return launch_darkfield(p->dev, p->L, n_tiles, I, p->phi, spec, p->df_scratch, p->df_per_block, p->df_iters,
+                            p->df_tol, status, p->d_counters, st);
 }
 
 apic_status check_plan(const apic_plan* plan, int n_tiles) {
@@ -461,7 +514,7 @@ apic_status apic_plan_query(const apic_plan* plan, apic_plan_info* info) {
     info->n_aperture = (int)H.ap_x.size();
     info->n_rows = (int)H.row_i.size();
     info->n_df_used = (int)std::count_if(H.df.begin(), H.df.end(), [](const DarkfieldHost& d) { return d.used; });
-    info->fft_m = H.m;
+    info->fft_m = plan->use_reg ? H.mr : H.m;
     info->pupil_rx = H.Rx;
     info->pupil_ry = H.Ry;
     return APIC_OK;
@@ -613,8 +666,7 @@ apic_status apic_darkfield(apic_plan* plan, int n_tiles, const float* I, const f
     if (n_tiles == 0) return APIC_OK;
     cudaStream_t st = (cudaStream_t)stream;
     APIC_TRY_LAUNCH(launch_phase(plan->dev, n_tiles, zern, plan->phi, st));
-    APIC_TRY_LAUNCH(launch_darkfield(plan->dev, plan->L, n_tiles, I, plan->phi, (float2*)spec, plan->df_scratch,
-                                     plan->df_per_block, plan->df_iters, plan->df_tol, status, plan->d_counters, st));
+    APIC_TRY_LAUNCH(launch_df(plan, n_tiles, I, (float2*)spec, status, st));
     return APIC_OK;
 }
 
@@ -673,8 +725,7 @@ apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* I,
         APIC_TRY_LAUNCH(launch_stitch(D, nt, plan->xdisc, plan->phi, plan->spec, stt, st));
         if (last) tm.mark(3, 1);
         if (first) tm.mark(4, 0);
-        APIC_TRY_LAUNCH(launch_darkfield(D, L, nt, It, plan->phi, plan->spec, plan->df_scratch, plan->df_per_block,
-                                         plan->df_iters, plan->df_tol, stt, plan->d_counters, st));
+        APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
         if (last) tm.mark(4, 1);
         if (first) tm.mark(5, 0);
         APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, (float2*)field + (size_t)t0 * out_tile, stt, st));

@@ -16,11 +16,14 @@ struct DevDF {
     int u_off, q_off, p_off;         // offsets into the concatenated point arrays
     int uy0, uy1, qy0, qy1, py0, py1;  // band of rows (signed y) of each set
     int urp, qrp, prp;               // offsets into the concatenated row-pointer array
+    int qmask_off;                   // offset of the Q-membership bit rows (register grid)
 };
 
 struct DevPlan {
     int h, w, H, W, n_bf, n_df, n_img;
     int npup, nap, nrows, m, n_used;
+    int mr;                          // register-FFT correlation grid (16 B), 0 if unsupported
+    int band_u, band_q;              // largest U/P and Q row bands of the used images
     int max_N, max_M;
     float Rx, Ry;
     int pup_ax, pup_ay;
@@ -56,10 +59,12 @@ struct DevPlan {
     const int* dP_x; const int* dP_y; const int* dP_pup; const int* dP_ap;
     const int* dQ_x; const int* dQ_y;
     const int* d_rowptr;
+    const unsigned* d_qmask;         // per used image: Q band rows x (mr / 32) words
     // twiddles
     const float2* tw_n;              // n = h = w
     const float2* tw_m;
     const float2* tw_N;              // N = H = W
+    const float2* tw_r;              // mr
 };
 
 // Scratch sizes and grids decided at plan creation.
@@ -89,6 +94,14 @@ cudaError_t launch_sim(const DevPlan& P, const Launch& L, int n_tiles, const flo
                        float photons, unsigned long long seed, float* I, float2* ohat_scratch, cudaStream_t st);
 
 size_t df_scratch_bytes(const DevPlan& P);
+
+// register-FFT darkfield kernel (m = 16 B, n = 16 BN)
+size_t dfr_smem_bytes(int B, int BN, int max_band, int max_N);
+size_t dfr_scratch_bytes(const DevPlan& P);
+int configure_dfr(int B, int BN, size_t smem);
+cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
+                                 const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
+                                 float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
 
 // Sets the dynamic shared-memory limit of a transform kernel and returns its
 // resident blocks per SM (0 on error). which: 0 kk, 1 aberration, 2 darkfield,

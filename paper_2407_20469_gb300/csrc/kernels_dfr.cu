@@ -1,0 +1,500 @@
+// kernels_dfr.cu - darkfield spectrum extension (WSI-APIC Eq. 11-13) with
+// register-resident half-warp FFTs on an m x m correlation grid, m = 16 B.
+//
+// Per darkfield image j (pupil frame c = K + k_j; U unknown, P known, Q lags):
+//   b(k) = F(I_j)(k) - (P*P)(k) on Q                              (Eq. 13 left)
+//   C u  = series coefficients on Q of u(x) conj p(x)              (Eq. 13 right)
+//   min ||C u - b|| by CG on the normal equations C^H C u = C^H b (CGNR): per
+//   iteration w = C^H mask_Q C d as five passes over the grid
+//     R1 rows of U: scatter d, inverse transform along x     -> GU
+//     C1 columns:   inverse along y, * conj(p) / m^2, forward along y -> GQ
+//     R2 rows of Q: forward along x, keep Q, inverse along x (in place)
+//     C2 columns:   inverse along y, * p / m^2, forward along y        -> GU
+//     R3 rows of U: forward along x, gather w on U, <d, w>
+//   then x += alpha d, s -= alpha w, d = s + beta d. Transforms FP32; inner
+//   products, step lengths and the solution FP64.
+// GU / GQ are band-row grids (only rows holding U, P or Q points) and the known
+// field p is stored column-major, all in the block's scratch (L2-resident).
+// One block per tile (persistent); images of a tile are sequential. Each pass
+// is a separate (non-inlined) function so registers are allocated per pass.
+#include <math.h>
+
+#include <algorithm>
+
+#include "../../include/apic.h"
+#include "internal.cuh"
+#include "regfft.cuh"
+
+namespace apic {
+
+namespace {
+
+constexpr int kHW = kThreads / 16;     // half-warps per block (32)
+constexpr int kStageLd = 33;           // column stage: 32 columns + 1 pad
+
+__device__ __forceinline__ int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+struct HW {
+    int t, hw;
+    unsigned mask;
+    float2* hs;
+    __device__ HalfWarp h() const { return HalfWarp{t, mask, hs}; }
+};
+
+// ---- per-point functors
+struct ValKnown {       // P(c) = O_known(K) exp(j phi(c))
+    const float2* sp;
+    const float* ph;
+    const int* ap;
+    const int* pup;
+    __device__ float2 operator()(int e) const {
+        float sn, cs;
+        sincosf(ph[pup[e]], &sn, &cs);
+        return cmul(sp[ap[e]], make_float2(cs, sn));
+    }
+};
+struct ValVec {
+    const float2* v;
+    __device__ float2 operator()(int e) const { return v[e]; }
+};
+struct OutStart {       // s = d = C^H b, x = 0; returns |s|^2
+    float2* sv;
+    float2* dv;
+    double2* xv;
+    __device__ double operator()(int e, float2 v) const {
+        sv[e] = v;
+        dv[e] = v;
+        xv[e] = make_double2(0.0, 0.0);
+        return (double)v.x * v.x + (double)v.y * v.y;
+    }
+};
+struct OutDot {         // w = C^H C d; returns Re <d, w>
+    float2* wv;
+    const float2* dv;
+    __device__ double operator()(int e, float2 v) const {
+        wv[e] = v;
+        const float2 d = dv[e];
+        return (double)d.x * v.x + (double)d.y * v.y;
+    }
+};
+
+// ---- per-column mid operations (lanes t < B; o[k1] is the value at y = t + B k1)
+template <int B>
+struct MidKnownField {  // store p column-major, replace by |p|^2
+    float2* PF;
+    __device__ void operator()(float2 (&o)[16], int x, int t) const {
+        float2* col = PF + (size_t)x * (16 * B);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) {
+            col[t + B * k1] = o[k1];
+            o[k1] = make_float2(cabs2(o[k1]), 0.f);
+        }
+    }
+};
+template <int B, bool CONJ>
+struct MidTimesField {  // o *= p / m^2 or conj(p) / m^2
+    const float2* PF;
+    float scale;
+    __device__ void operator()(float2 (&o)[16], int x, int t) const {
+        const float2* col = PF + (size_t)x * (16 * B);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) {
+            const float2 p = col[t + B * k1];
+            o[k1] = cscale(CONJ ? cmulc(o[k1], p) : cmul(o[k1], p), scale);
+        }
+    }
+};
+
+// ---- passes
+
+// rows of a band: scatter val(e) at x = px[e], inverse transform along x, store rows of G
+template <int B, class Val>
+__device__ __noinline__ void pass_rows_in(HW w, const float2* tw, float2* G, int nrows, const int* rp,
+                                          const int* px, Val val) {
+    constexpr int m = 16 * B;
+    const HalfWarp h = w.h();
+    for (int b = w.hw; b < nrows; b += kHW) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) w.hs[w.t + 16 * j] = make_float2(0.f, 0.f);
+        __syncwarp(w.mask);
+        for (int e = rp[b] + w.t; e < rp[b + 1]; e += 16) w.hs[freq_index(px[e], m)] = val(e);
+        __syncwarp(w.mask);
+        float2 v[B], o[16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = w.hs[w.t + 16 * j];
+        __syncwarp(w.mask);
+        fft_alpha<B, true>(v, o, h, tw);
+        if (w.t < B) {
+            float2* row = G + (size_t)b * m;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) row[w.t + B * k1] = o[k1];
+        }
+    }
+}
+
+// rows of a band of G: forward transform along x; returns sum of out(e, value) over this lane's points
+template <int B, class Out>
+__device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float2* G, int nrows, const int* rp,
+                                             const int* px, Out out) {
+    constexpr int m = 16 * B;
+    const HalfWarp h = w.h();
+    double acc = 0.0;
+    for (int b = w.hw; b < nrows; b += kHW) {
+        const float2* row = G + (size_t)b * m;
+        float2 v[B], o[16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        fft_alpha<B, false>(v, o, h, tw);
+        if (w.t < B) {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + B * k1] = o[k1];
+        }
+        __syncwarp(w.mask);
+        for (int e = rp[b] + w.t; e < rp[b + 1]; e += 16) acc += out(e, w.hs[freq_index(px[e], m)]);
+        __syncwarp(w.mask);
+    }
+    return acc;
+}
+
+// columns: rows yi0.. (ni of them) of Gi are the input, the rest zero; inverse along
+// y, mid, forward along y; rows yo0.. (no) stored to Go. Ends with __syncthreads.
+template <int B, class Mid>
+__device__ __noinline__ void pass_cols(HW w, const float2* tw, float2* stage, const float2* Gi, int yi0, int ni,
+                                       float2* Go, int yo0, int no, Mid mid) {
+    constexpr int m = 16 * B;
+    const HalfWarp h = w.h();
+    for (int c0 = 0; c0 < m; c0 += kHW) {
+        for (int idx = threadIdx.x; idx < ni * kHW; idx += blockDim.x) {
+            const int b = idx >> 5, c = idx & 31;
+            stage[b * kStageLd + c] = Gi[(size_t)b * m + c0 + c];
+        }
+        __syncthreads();
+        float2 v[B], o[16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int bb = sfreq(w.t + 16 * j, m) - yi0;
+            v[j] = (bb >= 0 && bb < ni) ? stage[bb * kStageLd + w.hw] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        fft_alpha<B, true>(v, o, h, tw);
+        if (w.t < B) mid(o, c0 + w.hw, w.t);
+        fft_beta<B, false>(o, v, h, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < B; ++k1) {
+            const int bb = sfreq(w.t + 16 * k1, m) - yo0;
+            if (bb >= 0 && bb < no) stage[bb * kStageLd + w.hw] = v[k1];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < no * kHW; idx += blockDim.x) {
+            const int b = idx >> 5, c = idx & 31;
+            Go[(size_t)b * m + c0 + c] = stage[b * kStageLd + c];
+        }
+        __syncthreads();
+    }
+}
+
+// rows of Q in place: forward along x, keep the Q lags, inverse along x. Ends with __syncthreads.
+template <int B>
+__device__ __noinline__ void pass_rows_mask(HW w, const float2* tw, float2* G, int nrows, const unsigned* qmask) {
+    constexpr int m = 16 * B;
+    const HalfWarp h = w.h();
+    for (int b = w.hw; b < nrows; b += kHW) {
+        float2* row = G + (size_t)b * m;
+        const unsigned* mk = qmask + (size_t)b * (m / 32);
+        float2 v[B], o[16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        fft_alpha<B, false>(v, o, h, tw);
+        if (w.t < B) {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const int kx = w.t + B * k1;
+                if (!((mk[kx >> 5] >> (kx & 31)) & 1u)) o[k1] = make_float2(0.f, 0.f);
+            }
+        }
+        fft_beta<B, true>(o, v, h, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < B; ++k1) row[w.t + 16 * k1] = v[k1];
+    }
+    __syncthreads();
+}
+
+// columns of the real image (n = 16 BN): forward along y, rows qy0.. (nQ) stored to GX (row length n)
+template <int BN>
+__device__ __noinline__ void pass_image_cols(HW w, const float2* tw, float2* stage, const float* img, float2* GX,
+                                             int qy0, int nQ) {
+    constexpr int n = 16 * BN;
+    const HalfWarp h = w.h();
+    float* stage_f = reinterpret_cast<float*>(stage);
+    for (int c0 = 0; c0 < n; c0 += kHW) {
+        for (int idx = threadIdx.x; idx < n * kHW; idx += blockDim.x) {
+            const int y = idx >> 5, c = idx & 31;
+            stage_f[y * kStageLd + c] = img[(size_t)y * n + c0 + c];
+        }
+        __syncthreads();
+        float2 v[BN], o[16];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) v[j] = make_float2(stage_f[(w.t + 16 * j) * kStageLd + w.hw], 0.f);
+        __syncthreads();
+        fft_alpha<BN, false>(v, o, h, tw);
+        if (w.t < BN) {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const int bb = sfreq(w.t + BN * k1, n) - qy0;
+                if (bb >= 0 && bb < nQ) stage[bb * kStageLd + w.hw] = o[k1];
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nQ * kHW; idx += blockDim.x) {
+            const int b = idx >> 5, c = idx & 31;
+            GX[(size_t)b * n + c0 + c] = stage[b * kStageLd + c];
+        }
+        __syncthreads();
+    }
+}
+
+// rows of GX (length n): forward along x, bq[e] = value / n^2 at the Q points. Ends with __syncthreads.
+template <int BN>
+__device__ __noinline__ void pass_image_rows(HW w, const float2* tw, const float2* GX, int nQ, const int* qrp,
+                                             const int* Qx, float2* bq) {
+    constexpr int n = 16 * BN;
+    const HalfWarp h = w.h();
+    const float inv_n2 = 1.f / (float)(n * n);
+    for (int b = w.hw; b < nQ; b += kHW) {
+        const float2* row = GX + (size_t)b * n;
+        float2 v[BN], o[16];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) v[j] = row[w.t + 16 * j];
+        fft_alpha<BN, false>(v, o, h, tw);
+        if (w.t < BN) {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + BN * k1] = o[k1];
+        }
+        __syncwarp(w.mask);
+        for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16) bq[e] = cscale(w.hs[freq_index(Qx[e], n)], inv_n2);
+        __syncwarp(w.mask);
+    }
+    __syncthreads();
+}
+
+// rows of Q holding the column-transformed |p|^2: forward along x, b = bq - (P*P)/m^2
+// on Q (kept in bq), then the rows of b inverse-transformed along x. Ends with __syncthreads.
+template <int B>
+__device__ __noinline__ void pass_rows_rhs(HW w, const float2* tw, float2* GQ, int nQ, const int* qrp,
+                                           const int* Qx, float2* bq) {
+    constexpr int m = 16 * B;
+    const HalfWarp h = w.h();
+    const float inv_m2 = 1.f / (float)(m * m);
+    for (int b = w.hw; b < nQ; b += kHW) {
+        float2* row = GQ + (size_t)b * m;
+        float2 v[B], o[16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        fft_alpha<B, false>(v, o, h, tw);
+        if (w.t < B) {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + B * k1] = o[k1];
+        }
+        __syncwarp(w.mask);
+        for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16)
+            bq[e] = csub(bq[e], cscale(w.hs[freq_index(Qx[e], m)], inv_m2));
+        __syncwarp(w.mask);
+#pragma unroll
+        for (int j = 0; j < B; ++j) w.hs[w.t + 16 * j] = make_float2(0.f, 0.f);
+        __syncwarp(w.mask);
+        for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16) w.hs[freq_index(Qx[e], m)] = bq[e];
+        __syncwarp(w.mask);
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = w.hs[w.t + 16 * j];
+        __syncwarp(w.mask);
+        fft_alpha<B, true>(v, o, h, tw);
+        if (w.t < B) {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) row[w.t + B * k1] = o[k1];
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+template <int B, int BN>
+struct DFLayout {
+    static constexpr int hws = HWSize<B>::value > HWSize<BN>::value ? HWSize<B>::value : HWSize<BN>::value;
+};
+
+size_t dfr_smem_bytes(int B, int BN, int max_band, int max_N) {
+    const int hws = std::max(std::max(17 * B, 16 * (B + 1)), std::max(17 * BN, 16 * (BN + 1)));
+    size_t b = ((size_t)kHW * hws * sizeof(float2) + 15) & ~(size_t)15;   // half-warp areas
+    const size_t stage_c = (size_t)max_band * kStageLd * sizeof(float2);
+    const size_t stage_f = (size_t)(16 * BN) * kStageLd * sizeof(float);
+    b += (std::max(stage_c, stage_f) + 15) & ~(size_t)15;                  // column stage
+    b += (size_t)max_N * (sizeof(double2) + 3 * sizeof(float2));           // x, d, s, w
+    b += (size_t)(16 * B + 16 * BN) * sizeof(float2);                       // twiddles
+    b += 64 * sizeof(double);
+    return (b + 15) & ~(size_t)15;
+}
+
+size_t dfr_scratch_bytes(const DevPlan& P) {
+    const int m = P.mr, n = P.h;
+    size_t s = (size_t)P.band_u * m * sizeof(float2);                        // GU
+    s += (size_t)P.band_q * m * sizeof(float2);                              // GQ
+    s += std::max((size_t)m * m, (size_t)P.band_q * n) * sizeof(float2);     // PF / F(I) rows
+    s += (size_t)P.max_M * sizeof(float2);                                   // b on Q
+    return (s + 255) & ~(size_t)255;
+}
+
+template <int B, int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
+                float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
+                int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
+    constexpr int m = 16 * B, n = 16 * BN, HWS = DFLayout<B, BN>::hws;
+    extern __shared__ float4 smem4[];
+    char* sp_ = reinterpret_cast<char*>(smem4);
+    float2* hw_area = reinterpret_cast<float2*>(sp_);
+    sp_ += ((size_t)kHW * HWS * sizeof(float2) + 15) & ~(size_t)15;
+    const size_t bytes_c = (size_t)(P.band_q > P.band_u ? P.band_q : P.band_u) * kStageLd * sizeof(float2);
+    const size_t bytes_f = (size_t)n * kStageLd * sizeof(float);
+    float2* stage = reinterpret_cast<float2*>(sp_);
+    sp_ += ((bytes_c > bytes_f ? bytes_c : bytes_f) + 15) & ~(size_t)15;
+    double2* xv = reinterpret_cast<double2*>(sp_);
+    sp_ += (size_t)P.max_N * sizeof(double2);
+    float2* dv = reinterpret_cast<float2*>(sp_);
+    float2* sv = dv + P.max_N;
+    float2* wv = sv + P.max_N;
+    float2* tw_m = wv + P.max_N;
+    float2* tw_n = tw_m + m;
+    double* red = reinterpret_cast<double*>(tw_n + n);
+
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tw_m[i] = P.tw_r[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw_n[i] = P.tw_n[i];
+    __syncthreads();
+
+    HW w;
+    w.hw = threadIdx.x >> 4;
+    w.t = threadIdx.x & 15;
+    w.mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
+    w.hs = hw_area + w.hw * HWS;
+
+    char* base = scratch + (size_t)blockIdx.x * per_block;
+    float2* GU = reinterpret_cast<float2*>(base);
+    float2* GQ = GU + (size_t)P.band_u * m;
+    float2* PF = GQ + (size_t)P.band_q * m;          // column-major known field, or F(I) rows
+    float2* bq = PF + (size_t)max(m * m, P.band_q * n);
+    const float inv_m2 = 1.f / (float)(m * m);
+
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
+        const float* ph = phi + (size_t)tile * P.npup;
+        float2* sp = spec + (size_t)tile * P.nap;
+        bool notconv = false;
+        for (int di = 0; di < P.n_used; ++di) {
+            const DevDF& D = P.df[di];
+            const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
+            const int uy0 = D.uy0, qy0 = D.qy0, py0 = D.py0;
+            const int N = D.N, nU = D.uy1 - uy0 + 1, nQ = D.qy1 - qy0 + 1, nP = D.py1 - py0 + 1;
+            const int *urp = P.d_rowptr + D.urp, *qrp = P.d_rowptr + D.qrp, *prp = P.d_rowptr + D.prp;
+            const unsigned* qmask = P.d_qmask + D.qmask_off;
+            const float* img = I + ((size_t)tile * P.n_img + D.led) * n * n;
+
+            // b = F(I_j) on Q
+            pass_image_cols<BN>(w, tw_n, stage, img, PF, qy0, nQ);
+            pass_image_rows<BN>(w, tw_n, PF, nQ, qrp, P.dQ_x + q_off, bq);
+            // known field p (column-major in PF), b -= P*P, rows of b inverse along x
+            pass_rows_in<B>(w, tw_m, GU, nP, prp, P.dP_x + p_off,
+                            ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
+            __syncthreads();
+            pass_cols<B>(w, tw_m, stage, GU, py0, nP, GQ, qy0, nQ, MidKnownField<B>{PF});
+            pass_rows_rhs<B>(w, tw_m, GQ, nQ, qrp, P.dQ_x + q_off, bq);
+            // s = d = C^H b
+            pass_cols<B>(w, tw_m, stage, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
+            const double g0 = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutStart{sv, dv, xv});
+            const double gamma0 = block_sum(g0, red);
+
+            // CGNR
+            double gamma = gamma0;
+            bool conv = !(gamma0 > 1e-300);
+            const double stop = (double)tol * (double)tol * gamma0;
+            int it = 0;
+            for (; it < iters && !conv; ++it) {
+                pass_rows_in<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, ValVec{dv});
+                __syncthreads();
+                pass_cols<B>(w, tw_m, stage, GU, uy0, nU, GQ, qy0, nQ, MidTimesField<B, true>{PF, inv_m2});
+                pass_rows_mask<B>(w, tw_m, GQ, nQ, qmask);
+                pass_cols<B>(w, tw_m, stage, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
+                const double dw = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutDot{wv, dv});
+                const double delta = block_sum(dw, red);
+                if (!(delta > 0)) break;
+                const double alpha = gamma / delta;
+                const float af = (float)alpha;
+                double g2 = 0;
+                for (int e = threadIdx.x; e < N; e += blockDim.x) {
+                    const float2 d = dv[e];
+                    double2 x = xv[e];
+                    x.x += alpha * d.x;
+                    x.y += alpha * d.y;
+                    xv[e] = x;
+                    const float2 s = csub(sv[e], cscale(wv[e], af));
+                    sv[e] = s;
+                    g2 += (double)s.x * s.x + (double)s.y * s.y;
+                }
+                const double gnew = block_sum(g2, red);
+                const float bf = (float)(gnew / gamma);
+                gamma = gnew;
+                for (int e = threadIdx.x; e < N; e += blockDim.x) dv[e] = cadd(sv[e], cscale(dv[e], bf));
+                __syncthreads();
+                conv = gnew <= stop;
+            }
+            if (!conv) notconv = true;
+            if (threadIdx.x == 0 && counters) {
+                atomicAdd(counters + 1, (unsigned long long)it);
+                atomicAdd(counters + 2, 1ull);
+            }
+            const int* Upup = P.dU_pup + u_off;
+            const int* Uap = P.dU_ap + u_off;
+            for (int e = threadIdx.x; e < N; e += blockDim.x) {
+                float sn, cs;
+                sincosf(ph[Upup[e]], &sn, &cs);
+                const double2 x = xv[e];
+                sp[Uap[e]] = cmul(make_float2((float)x.x, (float)x.y), make_float2(cs, -sn));
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && notconv && status) atomicOr(status + tile, APIC_TILE_NOTCONV);
+    }
+}
+
+using DFRKernel = void (*)(DevPlan, int, const float*, const float*, float2*, char*, size_t, int, float, int32_t*,
+                           unsigned long long*);
+
+DFRKernel dfr_kernel(int B, int BN) {
+    if (B == 4 && BN == 4) return k_darkfield_reg<4, 4>;
+    if (B == 6 && BN == 8) return k_darkfield_reg<6, 8>;
+    if (B == 8 && BN == 8) return k_darkfield_reg<8, 8>;
+    if (B == 12 && BN == 16) return k_darkfield_reg<12, 16>;
+    if (B == 16 && BN == 16) return k_darkfield_reg<16, 16>;
+    return nullptr;
+}
+
+int configure_dfr(int B, int BN, size_t smem) {
+    DFRKernel f = dfr_kernel(B, BN);
+    if (!f) return 0;
+    if (cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, smem) != cudaSuccess) return 0;
+    return occ;
+}
+
+cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
+                                 const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
+                                 float tol, int32_t* status, unsigned long long* counters, cudaStream_t st) {
+    DFRKernel f = dfr_kernel(P.mr / 16, P.h / 16);
+    if (!f) return cudaErrorInvalidValue;
+    f<<<min(grid, n_tiles), kThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol,
+                                                  status, counters);
+    return cudaGetLastError();
+}
+
+}  // namespace apic

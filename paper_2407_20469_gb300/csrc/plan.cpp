@@ -305,6 +305,11 @@ std::string build_host_plan(const GeomParams& p, HostPlan& P) {
     // ---- correlation grid: alias-free for lags up to 2 rint (m >= 4 rint + 1)
     P.m = 16;
     while (P.m < 4 * rint + 1) P.m *= 2;
+    for (int B : {4, 6, 8, 12, 16})
+        if (16 * B >= 4 * rint + 1) {
+            P.mr = 16 * B;
+            break;
+        }
     for (auto& d : P.df)
         for (size_t q = 0; q < d.Q_x.size(); ++q)
             if (2 * std::abs(d.Q_x[q]) >= p.w || 2 * std::abs(d.Q_y[q]) >= p.h)

@@ -48,7 +48,8 @@ struct HostPlan {
     double Lval[144] = {0}, Lgrad[144] = {0}; // Cholesky factors (lower, row-major)
     // darkfield images in processing order (increasing |k|, then angle)
     std::vector<DarkfieldHost> df;
-    int m = 0;                                // grid of the darkfield correlations
+    int m = 0;                                // grid of the darkfield correlations (power of two)
+    int mr = 0;                               // register-FFT grid 16 B (B in 4, 6, 8, 12, 16), 0 if none
 
     int pupil_index(int kx, int ky) const;
 };

@@ -236,3 +236,27 @@ def test_full_size_batch_sampled_tiles():
         assert rel_l2(as_complex(field[t:t + 1])[0], res.field) < FIELD_TOL
         assert pupil_rms(z[t].cpu().numpy(), res.c15) < PUPIL_TOL
     assert torch.isfinite(field).all()
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_register_and_legacy_darkfield_kernels_agree(n):
+    """The register-FFT darkfield kernel (correlation grid 16 B) and the shared-memory
+    Stockham kernel (power-of-two grid) solve the same least-squares problems."""
+    I, _, _ = make_tiles(n, 2, seed=90 + n)
+    fields = []
+    for flags in (0, apic.APIC_LEGACY_DF):
+        plan = new_plan(n, max_tiles=2, flags=flags)
+        H = plan.info.out_h
+        field = torch.zeros((2, H, 2 * H), dtype=torch.float32, device="cuda")
+        z = torch.zeros((2, 15), dtype=torch.float32, device="cuda")
+        st = torch.zeros(2, dtype=torch.int32, device="cuda")
+        plan.reconstruct_batch(2, dev(I), field, z, None, st)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy() == 0)
+        fields.append(as_complex(field))
+        if flags == 0:
+            assert plan.info.fft_m % 16 == 0 and plan.info.fft_m <= n
+    for t in range(2):
+        assert rel_l2(fields[0][t], fields[1][t]) < 2e-4
+    res = oracle_tile(I[0], n)
+    assert rel_l2(fields[0][0], res.field) < FIELD_TOL
