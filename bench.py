@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=2407)
+    ap.add_argument("--df-tol", type=float, default=0.0, help="CGLS tolerance (0: library default)")
+    ap.add_argument("--df-iters", type=int, default=0, help="CGLS iteration cap (0: library default)")
     return ap.parse_args()
 
 
@@ -245,7 +247,7 @@ def gpu_arm(args):
 
     n, T = args.tile, args.tiles
     ill = synth.illumination()
-    plan = apic.Plan.from_illumination(n, ill, max_tiles=T)
+    plan = apic.Plan.from_illumination(n, ill, max_tiles=T, df_tol=args.df_tol, df_iters=args.df_iters)
     info = plan.info
     H = info.out_h
     n_img = info.n_bf + info.n_df
@@ -353,6 +355,7 @@ def gpu_arm(args):
         "config": {"workload": WORKLOAD, "tiles_per_gpu": T, "tile": n, "output": H, "images": n_img,
                    "l2": "inputs_larger_than_l2 (3.2 GB intensities per step)", "launch": "direct C-ABI calls",
                    "tiles_per_s": world * T * args.steps / (ms / 1e3),
+                   "df_tol": args.df_tol or "library default", "fft_m": info.fft_m,
                    "tiles_status_nonzero": int(np.count_nonzero(status_np))},
         "roofline": roofline, "e2e": e2e, "gpu_launches": cnt["launches"], "clocks": clk,
     }

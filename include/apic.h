@@ -83,7 +83,7 @@ typedef struct {
     int upsample;                /* output upsampling factor u (2)                             */
     int max_tiles;               /* largest n_tiles of one call; larger calls are chunked     */
     int df_iters;                /* CGLS iterations per darkfield image (<= 0: 40)            */
-    float df_tol;                /* CGLS relative gradient tolerance (<= 0: 1e-6)             */
+    float df_tol;                /* CG stop: ||C^H r|| <= df_tol ||C^H b|| (<= 0: 1e-4)       */
     int ab_passes;               /* value passes of the aberration solve (< 0: 2)             */
     float bg_contrast;           /* background threshold on RMS contrast (Sec. 3.2; 0.02)     */
     int flags;                   /* APIC_SKIP_BACKGROUND                                       */

@@ -157,40 +157,30 @@ __device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float
 }
 
 // columns: rows yi0.. (ni of them) of Gi are the input, the rest zero; inverse along
-// y, mid, forward along y; rows yo0.. (no) stored to Go. Ends with __syncthreads.
+// y, mid, forward along y; rows yo0.. (no) stored to Go. Each half-warp reads and
+// writes its own columns straight from the (L2-resident) grids. Ends with __syncthreads.
 template <int B, class Mid>
-__device__ __noinline__ void pass_cols(HW w, const float2* tw, float2* stage, const float2* Gi, int yi0, int ni,
-                                       float2* Go, int yo0, int no, Mid mid) {
+__device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi, int yi0, int ni, float2* Go,
+                                       int yo0, int no, Mid mid) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
-    for (int c0 = 0; c0 < m; c0 += kHW) {
-        for (int idx = threadIdx.x; idx < ni * kHW; idx += blockDim.x) {
-            const int b = idx >> 5, c = idx & 31;
-            stage[b * kStageLd + c] = Gi[(size_t)b * m + c0 + c];
-        }
-        __syncthreads();
+    for (int x = w.hw; x < m; x += kHW) {
         float2 v[B], o[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             const int bb = sfreq(w.t + 16 * j, m) - yi0;
-            v[j] = (bb >= 0 && bb < ni) ? stage[bb * kStageLd + w.hw] : make_float2(0.f, 0.f);
+            v[j] = (bb >= 0 && bb < ni) ? Gi[(size_t)bb * m + x] : make_float2(0.f, 0.f);
         }
-        __syncthreads();
         fft_alpha<B, true>(v, o, h, tw);
-        if (w.t < B) mid(o, c0 + w.hw, w.t);
+        if (w.t < B) mid(o, x, w.t);
         fft_beta<B, false>(o, v, h, tw);
 #pragma unroll
         for (int k1 = 0; k1 < B; ++k1) {
             const int bb = sfreq(w.t + 16 * k1, m) - yo0;
-            if (bb >= 0 && bb < no) stage[bb * kStageLd + w.hw] = v[k1];
+            if (bb >= 0 && bb < no) Go[(size_t)bb * m + x] = v[k1];
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < no * kHW; idx += blockDim.x) {
-            const int b = idx >> 5, c = idx & 31;
-            Go[(size_t)b * m + c0 + c] = stage[b * kStageLd + c];
-        }
-        __syncthreads();
     }
+    __syncthreads();
 }
 
 // rows of Q in place: forward along x, keep the Q lags, inverse along x. Ends with __syncthreads.
@@ -330,7 +320,7 @@ size_t dfr_smem_bytes(int B, int BN, int max_band, int max_N) {
     const size_t stage_f = (size_t)(16 * BN) * kStageLd * sizeof(float);
     b += (std::max(stage_c, stage_f) + 15) & ~(size_t)15;                  // column stage
     b += (size_t)max_N * (sizeof(double2) + 3 * sizeof(float2));           // x, d, s, w
-    b += (size_t)(16 * B + 16 * BN) * sizeof(float2);                       // twiddles
+    b += (size_t)2 * (16 * B + 16 * BN) * sizeof(float2);                   // step twiddles
     b += 64 * sizeof(double);
     return (b + 15) & ~(size_t)15;
 }
@@ -364,11 +354,11 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
     float2* sv = dv + P.max_N;
     float2* wv = sv + P.max_N;
     float2* tw_m = wv + P.max_N;
-    float2* tw_n = tw_m + m;
-    double* red = reinterpret_cast<double*>(tw_n + n);
+    float2* tw_n = tw_m + 2 * m;
+    double* red = reinterpret_cast<double*>(tw_n + 2 * n);
 
-    for (int i = threadIdx.x; i < m; i += blockDim.x) tw_m[i] = P.tw_r[i];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw_n[i] = P.tw_n[i];
+    make_step_twiddles(tw_m, P.tw_r, B);
+    make_step_twiddles(tw_n, P.tw_n, BN);
     __syncthreads();
 
     HW w;
@@ -405,10 +395,10 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             pass_rows_in<B>(w, tw_m, GU, nP, prp, P.dP_x + p_off,
                             ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
             __syncthreads();
-            pass_cols<B>(w, tw_m, stage, GU, py0, nP, GQ, qy0, nQ, MidKnownField<B>{PF});
+            pass_cols<B>(w, tw_m, GU, py0, nP, GQ, qy0, nQ, MidKnownField<B>{PF});
             pass_rows_rhs<B>(w, tw_m, GQ, nQ, qrp, P.dQ_x + q_off, bq);
             // s = d = C^H b
-            pass_cols<B>(w, tw_m, stage, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
+            pass_cols<B>(w, tw_m, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
             const double g0 = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutStart{sv, dv, xv});
             const double gamma0 = block_sum(g0, red);
 
@@ -420,9 +410,9 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             for (; it < iters && !conv; ++it) {
                 pass_rows_in<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, ValVec{dv});
                 __syncthreads();
-                pass_cols<B>(w, tw_m, stage, GU, uy0, nU, GQ, qy0, nQ, MidTimesField<B, true>{PF, inv_m2});
+                pass_cols<B>(w, tw_m, GU, uy0, nU, GQ, qy0, nQ, MidTimesField<B, true>{PF, inv_m2});
                 pass_rows_mask<B>(w, tw_m, GQ, nQ, qmask);
-                pass_cols<B>(w, tw_m, stage, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
+                pass_cols<B>(w, tw_m, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
                 const double dw = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutDot{wv, dv});
                 const double delta = block_sum(dw, red);
                 if (!(delta > 0)) break;

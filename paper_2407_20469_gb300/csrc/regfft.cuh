@@ -167,8 +167,11 @@ struct DFT<4, INV> {
     }
 };
 
-// Half-warp helpers: lane t in [0, 16), the half-warp mask, its shared area hs
-// and the N-entry forward twiddle table tw (W_N^k = exp(-2 pi i k / N)).
+// Half-warp helpers: lane t in [0, 16), the half-warp mask, its shared area hs.
+// Twiddles between the steps come from a per-length table in shared memory laid
+// out for conflict-free lane access: tw[k2 * 16 + t] = W_N^(t k2) (k2 < B) for
+// alpha, followed by tw[16 B + k2 * B + u] = W_N^(u k2) (k2 < 16) for beta;
+// W = exp(-2 pi i / N). make_step_twiddles fills it from a plain N-entry table.
 struct HalfWarp {
     int t;
     unsigned mask;
@@ -185,13 +188,24 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int k, bool inv) {
     return inv ? make_float2(w.x, -w.y) : w;
 }
 
+// Fills the 2 * 16 B step twiddles of length N = 16 B from a plain table W_N^k.
+__device__ inline void make_step_twiddles(float2* dst, const float2* plain, int B) {
+    const int N = 16 * B;
+    for (int i = threadIdx.x; i < 16 * B; i += blockDim.x) {
+        const int k2 = i >> 4, t = i & 15;               // alpha: [k2 < B][t < 16]
+        dst[i] = plain[(t * k2) % N];
+        const int k2b = i / B, u = i - k2b * B;          // beta: [k2 < 16][u < B]
+        dst[16 * B + i] = plain[(u * k2b) % N];
+    }
+}
+
 // alpha: v[j] = x[t + 16 j] -> lanes t < B: o[k1] = X[t + B k1].
 template <int B, bool INV>
 __device__ __forceinline__ void fft_alpha(float2 (&v)[B], float2 (&o)[16], const HalfWarp& h, const float2* tw) {
     static_assert(B <= 16, "alpha needs B <= 16");
     DFT<B, INV>::run(v);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) h.hs[k2 * 17 + h.t] = cmul(v[k2], tw_get(tw, h.t * k2, INV));
+    for (int k2 = 0; k2 < B; ++k2) h.hs[k2 * 17 + h.t] = cmul(v[k2], tw_get(tw, k2 * 16 + h.t, INV));
     __syncwarp(h.mask);
     // lanes t >= B have no step-B work; they transform a copy of row 0 (discarded)
     const int row = h.t < B ? h.t : 0;
@@ -208,7 +222,7 @@ __device__ __forceinline__ void fft_beta(float2 (&o)[16], float2 (&v)[B], const 
     DFT<16, INV>::run(o);           // lanes t >= B transform values they do not store
     if (h.t < B) {
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) h.hs[k2 * (B + 1) + h.t] = cmul(o[k2], tw_get(tw, h.t * k2, INV));
+        for (int k2 = 0; k2 < 16; ++k2) h.hs[k2 * (B + 1) + h.t] = cmul(o[k2], tw_get(tw, 16 * B + k2 * B + h.t, INV));
     }
     __syncwarp(h.mask);
 #pragma unroll
