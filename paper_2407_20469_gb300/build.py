@@ -3,6 +3,9 @@
 Every translation unit under csrc/ is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a) and linked with the shared CUDA
 runtime. Run ``python -m paper_2407_20469_gb300.build`` or call ``build()``.
+Extra nvcc flags may be given in the environment variable APIC_NVCC_FLAGS
+(e.g. -DAPIC_DF_THREADS=512 for the darkfield block size); use force=True
+(--force) when changing them.
 """
 from __future__ import annotations
 
@@ -36,7 +39,8 @@ def sources():
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    env_flags = os.environ.get("APIC_NVCC_FLAGS", "").split()
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *env_flags, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
         cmd.insert(2, "c++")

@@ -29,7 +29,11 @@ namespace apic {
 
 namespace {
 
-constexpr int kHW = kThreads / 16;     // half-warps per block (32)
+#ifndef APIC_DF_THREADS
+#define APIC_DF_THREADS 512
+#endif
+constexpr int kDFThreads = APIC_DF_THREADS;  // threads per block of this kernel
+constexpr int kHW = kDFThreads / 16;         // half-warps per block
 constexpr int kStageLd = 33;           // column stage: 32 columns + 1 pad
 
 __device__ __forceinline__ int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
@@ -209,33 +213,39 @@ __device__ __noinline__ void pass_rows_mask(HW w, const float2* tw, float2* G, i
     __syncthreads();
 }
 
-// columns of the real image (n = 16 BN): forward along y, rows qy0.. (nQ) stored to GX (row length n)
+// columns of the real image (n = 16 BN): forward along y, rows qy0.. (nQ) stored to GX
+// (row length n). Chunks of 32 columns staged through shared memory for coalesced
+// image reads; half-warps 0..31 transform them. Ends with __syncthreads.
 template <int BN>
 __device__ __noinline__ void pass_image_cols(HW w, const float2* tw, float2* stage, const float* img, float2* GX,
                                              int qy0, int nQ) {
     constexpr int n = 16 * BN;
     const HalfWarp h = w.h();
     float* stage_f = reinterpret_cast<float*>(stage);
-    for (int c0 = 0; c0 < n; c0 += kHW) {
-        for (int idx = threadIdx.x; idx < n * kHW; idx += blockDim.x) {
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
             const int y = idx >> 5, c = idx & 31;
             stage_f[y * kStageLd + c] = img[(size_t)y * n + c0 + c];
         }
         __syncthreads();
         float2 v[BN], o[16];
+        if (w.hw < 32) {
 #pragma unroll
-        for (int j = 0; j < BN; ++j) v[j] = make_float2(stage_f[(w.t + 16 * j) * kStageLd + w.hw], 0.f);
+            for (int j = 0; j < BN; ++j) v[j] = make_float2(stage_f[(w.t + 16 * j) * kStageLd + w.hw], 0.f);
+        }
         __syncthreads();
-        fft_alpha<BN, false>(v, o, h, tw);
-        if (w.t < BN) {
+        if (w.hw < 32) {
+            fft_alpha<BN, false>(v, o, h, tw);
+            if (w.t < BN) {
 #pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) {
-                const int bb = sfreq(w.t + BN * k1, n) - qy0;
-                if (bb >= 0 && bb < nQ) stage[bb * kStageLd + w.hw] = o[k1];
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const int bb = sfreq(w.t + BN * k1, n) - qy0;
+                    if (bb >= 0 && bb < nQ) stage[bb * kStageLd + w.hw] = o[k1];
+                }
             }
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nQ * kHW; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < nQ * 32; idx += blockDim.x) {
             const int b = idx >> 5, c = idx & 31;
             GX[(size_t)b * n + c0 + c] = stage[b * kStageLd + c];
         }
@@ -335,7 +345,7 @@ size_t dfr_scratch_bytes(const DevPlan& P) {
 }
 
 template <int B, int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kDFThreads, 1)
 k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
                 float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
                 int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
@@ -473,7 +483,7 @@ int configure_dfr(int B, int BN, size_t smem) {
     if (cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kDFThreads, smem) != cudaSuccess) return 0;
     return occ;
 }
 
@@ -482,7 +492,7 @@ cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_
                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st) {
     DFRKernel f = dfr_kernel(P.mr / 16, P.h / 16);
     if (!f) return cudaErrorInvalidValue;
-    f<<<min(grid, n_tiles), kThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol,
+    f<<<min(grid, n_tiles), kDFThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol,
                                                   status, counters);
     return cudaGetLastError();
 }
