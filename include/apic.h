@@ -209,6 +209,31 @@ apic_status apic_kk_spectra(apic_plan* plan, int n_tiles, const float* d_intensi
                             float* d_xdisc, void* stream);
 
 /*
+ * Allocation-free Kramers-Kronig stage: the same computation and output as
+ * apic_kk_spectra, but its working grids come from one fixed 8 MiB array that
+ * the library keeps in device memory from load until process exit, instead of
+ * from the plan's workspace. The paper has no counterpart; this entry point
+ * exists for callers that cannot allocate device memory when they call: hosts
+ * that own all device memory through their own pool or caching allocator and
+ * only hand buffers in, and fixed-latency streaming loops where a cudaMalloc
+ * (which may synchronise the device) is not acceptable. The call itself makes
+ * no cudaMalloc, cudaFree or other allocation; the plan (created earlier)
+ * supplies only its read-only geometry tables.
+ * Limit: one tile grid of h x w complex values (8 h w bytes) must fit the 8 MiB
+ * array, so h w <= 1,048,576 (up to 1024 x 1024); fewer grids fit at once for
+ * larger tiles, which lowers parallelism but not correctness. Larger tiles
+ * return APIC_EINVAL with a message (apic_last_error).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller. Nothing in it needs clearing between calls.
+ * Arguments and layouts as apic_kk_spectra; n_tiles is not limited by max_tiles.
+ */
+apic_status apic_kk_spectra_noalloc(apic_plan* plan, int n_tiles, const float* d_intensity, float* d_xdisc,
+                                    void* stream);
+
+/*
  * Aberration solve (Eq. 8-10): phase differences on every overlap S_il,
  * neighbour-difference fit, then least squares on Eq. 10 (FP64 normal
  * equations). d_xdisc as written by apic_kk_spectra; d_zernike [n_tiles][15] out.

@@ -28,7 +28,7 @@ EXPORTS = [
     "apic_status_string", "apic_last_error", "apic_plan_create", "apic_plan_destroy",
     "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_counters", "apic_plan_timing",
     "apic_plan_stage_ms", "apic_reconstruct_batch", "apic_background",
-    "apic_kk_spectra", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
+    "apic_kk_spectra", "apic_kk_spectra_noalloc", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
     "apic_pupil", "apic_simulate",
 ]
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_reconstruct_batch": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "apic_background": (i32, [vp, i32, vp, vp, vp, vp]),
         "apic_kk_spectra": (i32, [vp, i32, vp, vp, vp]),
+        "apic_kk_spectra_noalloc": (i32, [vp, i32, vp, vp, vp]),
         "apic_aberration": (i32, [vp, i32, vp, vp, vp]),
         "apic_stitch": (i32, [vp, i32, vp, vp, vp, vp]),
         "apic_darkfield": (i32, [vp, i32, vp, vp, vp, vp, vp]),
@@ -216,6 +217,11 @@ class Plan:
     def kk_spectra(self, n_tiles, intensity, xdisc, stream=None):
         _check(load().apic_kk_spectra(self.handle, n_tiles, _ptr(intensity), _ptr(xdisc), _stream(stream)),
                "apic_kk_spectra")
+
+    def kk_spectra_noalloc(self, n_tiles, intensity, xdisc, stream=None):
+        """apic_kk_spectra without any allocation: scratch from the library's fixed device array."""
+        _check(load().apic_kk_spectra_noalloc(self.handle, n_tiles, _ptr(intensity), _ptr(xdisc), _stream(stream)),
+               "apic_kk_spectra_noalloc")
 
     def aberration(self, n_tiles, xdisc, zernike, stream=None):
         _check(load().apic_aberration(self.handle, n_tiles, _ptr(xdisc), _ptr(zernike), _stream(stream)),

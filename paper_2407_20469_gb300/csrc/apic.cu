@@ -636,6 +636,28 @@ apic_status apic_kk_spectra(apic_plan* plan, int n_tiles, const float* I, float*
     return APIC_OK;
 }
 
+apic_status apic_kk_spectra_noalloc(apic_plan* plan, int n_tiles, const float* I, float* xdisc, void* stream) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!I || !xdisc) return fail(APIC_EINVAL, "NULL intensity or output");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device)
+        return fail(APIC_EINVAL, "current device differs from the plan's device");
+    const size_t per_block = (size_t)plan->dev.h * plan->dev.w * sizeof(float2);
+    const size_t cap = noalloc_scratch_bytes();
+    if (per_block > cap)
+        return fail(APIC_EINVAL, "tile of " + std::to_string(plan->dev.h) + " x " + std::to_string(plan->dev.w) +
+                                     " needs " + std::to_string(per_block) + " bytes of scratch; the allocation-free"
+                                     " entry point holds " + std::to_string(cap));
+    if (n_tiles == 0) return APIC_OK;
+    float2* scratch = nullptr;
+    APIC_TRY_CUDA(noalloc_scratch(dev, &scratch));
+    const int blocks = (int)std::min<size_t>(cap / per_block, (size_t)plan->L.grid_kk);
+    APIC_TRY_LAUNCH(launch_kk_grid(plan->dev, blocks, plan->L.smem_kk, n_tiles, I, (float2*)xdisc, scratch,
+                                   (cudaStream_t)stream));
+    return APIC_OK;
+}
+
 apic_status apic_aberration(apic_plan* plan, int n_tiles, const float* xdisc, float* zern, void* stream) {
     apic_status s = check_stage(plan, n_tiles);
     if (s != APIC_OK) return s;

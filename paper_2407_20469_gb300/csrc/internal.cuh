@@ -78,6 +78,12 @@ cudaError_t launch_background(const DevPlan& P, int n_tiles, const float* I, flo
                               float bg_thresh2, cudaStream_t st);
 cudaError_t launch_kk(const DevPlan& P, const Launch& L, int n_tiles, const float* I, float2* xdisc,
                       float2* scratch, const int32_t* status, cudaStream_t st);
+// Kramers-Kronig kernel on an explicit grid (each block uses h * w scratch values).
+cudaError_t launch_kk_grid(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I, float2* xdisc,
+                           float2* scratch, cudaStream_t st);
+// Static scratch of the allocation-free entry point (kernels_noalloc.cu).
+size_t noalloc_scratch_bytes();
+cudaError_t noalloc_scratch(int device, float2** out);
 cudaError_t launch_aberration(const DevPlan& P, const Launch& L, int n_tiles, const float2* xdisc, float* zern,
                               float* beta_scratch, int passes, const int32_t* status, cudaStream_t st);
 cudaError_t launch_phase(const DevPlan& P, int n_tiles, const float* zern, float* phi, cudaStream_t st);

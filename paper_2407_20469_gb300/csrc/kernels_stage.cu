@@ -186,6 +186,14 @@ cudaError_t launch_kk(const DevPlan& P, const Launch& L, int n_tiles, const floa
     return cudaGetLastError();
 }
 
+cudaError_t launch_kk_grid(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I, float2* xdisc,
+                           float2* scratch, cudaStream_t st) {
+    grid = min(grid, n_tiles * P.n_bf);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    k_kk<<<grid, kThreads, smem, st>>>(P, n_tiles, I, xdisc, scratch, nullptr);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- aberration
 // One block per tile (persistent). beta(r) = arg(X_i X_l^*) on every overlap
 // row (Eq. 9). Stage 1 fits the wrapped differences of neighbouring rows,
