@@ -65,9 +65,10 @@ typedef enum {
 #define APIC_HOST_ONLY        2   /* build the geometry only: no device memory, no CUDA
                                      calls; only apic_plan_query / apic_plan_table /
                                      apic_plan_df_set / apic_plan_destroy accept it */
-#define APIC_LEGACY_DF        4   /* darkfield solve with the shared-memory Stockham kernel
-                                     on a power-of-two grid instead of the register-FFT
-                                     kernel on the smaller 16 B grid (for comparison)   */
+#define APIC_LEGACY_KERNELS   4   /* Kramers-Kronig and darkfield stages with the shared-
+                                     memory Stockham kernels (darkfield on a power-of-two
+                                     grid) instead of the register-FFT kernels (for
+                                     comparison)                                          */
 
 /* Number of Zernike coefficients per tile (Noll j = 1..15; j = 1..3 always 0). */
 #define APIC_N_ZERNIKE 15

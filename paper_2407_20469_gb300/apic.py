@@ -19,7 +19,7 @@ APIC_OK, APIC_EINVAL, APIC_ENOMEM, APIC_ECUDA, APIC_EGEOMETRY, APIC_EINTERNAL = 
 APIC_TILE_OK, APIC_TILE_BACKGROUND, APIC_TILE_NOTCONV, APIC_TILE_BADINPUT = 0, 1, 2, 4
 APIC_SKIP_BACKGROUND = 1
 APIC_HOST_ONLY = 2
-APIC_LEGACY_DF = 4
+APIC_LEGACY_KERNELS = 4
 APIC_N_ZERNIKE = 15
 APIC_TABLE_LEDS, APIC_TABLE_PUPIL, APIC_TABLE_APERTURE = 0, 1, 2
 

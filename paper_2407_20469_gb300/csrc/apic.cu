@@ -95,6 +95,9 @@ struct apic_plan {
     bool use_reg = false;        // register-FFT darkfield kernel
     size_t smem_dfr = 0;
     int grid_dfr = 0;
+    bool use_kkr = false;        // register-FFT Kramers-Kronig kernel
+    size_t smem_kkr = 0;
+    int grid_kkr = 0;
     unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
     long long launches = 0;                      // kernel launches issued
     // stage timing: ring of kTimingSlots calls x kStages x {start, stop}
@@ -301,7 +304,19 @@ apic_status configure(apic_plan* plan) {
     }
     const int sms = plan->sms;
     plan->use_reg = false;
-    if (D.mr > 0 && !(plan->params.flags & APIC_LEGACY_DF)) {
+    plan->use_kkr = false;
+    if (D.h == D.w && (D.h == 64 || D.h == 128 || D.h == 256) && !(plan->params.flags & APIC_LEGACY_KERNELS)) {
+        const size_t smem = kkr_smem_bytes(D.h / 16);
+        const int occ = configure_kkr(D.h / 16, smem);
+        if (occ > 0) {
+            plan->use_kkr = true;
+            plan->smem_kkr = smem;
+            plan->grid_kkr = sms * occ;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (D.mr > 0 && !(plan->params.flags & APIC_LEGACY_KERNELS)) {
         const size_t smem = dfr_smem_bytes(D.mr / 16, D.h / 16, std::max(D.band_q, D.band_u), D.max_N);
         int dev_max = 0;
         cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
@@ -336,8 +351,8 @@ apic_status alloc_workspace(apic_plan* p) {
     if ((s = dmalloc(p, (void**)&p->c2, T * sizeof(float))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->d_counters, 4 * sizeof(unsigned long long))) != APIC_OK) return s;
     APIC_TRY_CUDA(cudaMemset(p->d_counters, 0, 4 * sizeof(unsigned long long)));
-    if ((s = dmalloc(p, (void**)&p->kk_scratch, (size_t)p->L.grid_kk * D.h * D.h * sizeof(float2))) != APIC_OK)
-        return s;
+    const size_t kk_blocks = (size_t)std::max(p->L.grid_kk, p->grid_kkr);
+    if ((s = dmalloc(p, (void**)&p->kk_scratch, kk_blocks * D.h * D.h * sizeof(float2))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->beta_scratch, (size_t)p->L.grid_ab * D.nrows * sizeof(float))) != APIC_OK)
         return s;
     if (p->use_reg) {
@@ -348,6 +363,16 @@ apic_status alloc_workspace(apic_plan* p) {
         if ((s = dmalloc(p, &p->df_scratch, (size_t)p->L.grid_df * p->df_per_block)) != APIC_OK) return s;
     }
     return APIC_OK;
+}
+
+// Kramers-Kronig stage on `blocks` blocks (<= 0: the plan's grid) with the given scratch.
+cudaError_t launch_kk_any(apic_plan* p, int blocks, int n_tiles, const float* I, float2* xdisc, float2* scratch,
+                          const int32_t* status, cudaStream_t st) {
+    if (p->use_kkr)
+        return launch_kk_reg(p->dev, blocks > 0 ? std::min(blocks, p->grid_kkr) : p->grid_kkr, p->smem_kkr, n_tiles,
+                             I, xdisc, scratch, status, st);
+    return launch_kk_grid(p->dev, blocks > 0 ? std::min(blocks, p->L.grid_kk) : p->L.grid_kk, p->L.smem_kk, n_tiles,
+                          I, xdisc, scratch, status, st);
 }
 
 cudaError_t launch_df(apic_plan* p, int n_tiles, const float* I, float2* spec, int32_t* status, cudaStream_t st) {
@@ -631,8 +656,8 @@ apic_status apic_kk_spectra(apic_plan* plan, int n_tiles, const float* I, float*
     if (s != APIC_OK) return s;
     if (!I || !xdisc) return fail(APIC_EINVAL, "NULL intensity or output");
     if (n_tiles == 0) return APIC_OK;
-    APIC_TRY_LAUNCH(launch_kk(plan->dev, plan->L, n_tiles, I, (float2*)xdisc, plan->kk_scratch, nullptr,
-                              (cudaStream_t)stream));
+    APIC_TRY_LAUNCH(launch_kk_any(plan, 0, n_tiles, I, (float2*)xdisc, plan->kk_scratch, nullptr,
+                                  (cudaStream_t)stream));
     return APIC_OK;
 }
 
@@ -652,9 +677,8 @@ apic_status apic_kk_spectra_noalloc(apic_plan* plan, int n_tiles, const float* I
     if (n_tiles == 0) return APIC_OK;
     float2* scratch = nullptr;
     APIC_TRY_CUDA(noalloc_scratch(dev, &scratch));
-    const int blocks = (int)std::min<size_t>(cap / per_block, (size_t)plan->L.grid_kk);
-    APIC_TRY_LAUNCH(launch_kk_grid(plan->dev, blocks, plan->L.smem_kk, n_tiles, I, (float2*)xdisc, scratch,
-                                   (cudaStream_t)stream));
+    const int blocks = (int)std::min<size_t>(cap / per_block, (size_t)std::max(plan->L.grid_kk, plan->grid_kkr));
+    APIC_TRY_LAUNCH(launch_kk_any(plan, blocks, n_tiles, I, (float2*)xdisc, scratch, nullptr, (cudaStream_t)stream));
     return APIC_OK;
 }
 
@@ -737,7 +761,7 @@ apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* I,
         APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, plan->bg_thresh2, st));
         if (last) tm.mark(0, 1);
         if (first) tm.mark(1, 0);
-        APIC_TRY_LAUNCH(launch_kk(D, L, nt, It, plan->xdisc, plan->kk_scratch, stt, st));
+        APIC_TRY_LAUNCH(launch_kk_any(plan, 0, nt, It, plan->xdisc, plan->kk_scratch, stt, st));
         if (last) tm.mark(1, 1);
         if (first) tm.mark(2, 0);
         APIC_TRY_LAUNCH(launch_aberration(D, L, nt, plan->xdisc, zt, plan->beta_scratch, plan->ab_passes, stt, st));

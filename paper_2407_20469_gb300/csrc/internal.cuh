@@ -78,9 +78,14 @@ cudaError_t launch_background(const DevPlan& P, int n_tiles, const float* I, flo
                               float bg_thresh2, cudaStream_t st);
 cudaError_t launch_kk(const DevPlan& P, const Launch& L, int n_tiles, const float* I, float2* xdisc,
                       float2* scratch, const int32_t* status, cudaStream_t st);
-// Kramers-Kronig kernel on an explicit grid (each block uses h * w scratch values).
+// Kramers-Kronig kernels on an explicit grid (each block uses h * w scratch values):
+// shared-memory Stockham version, and the register-FFT version (n = 16 BN, BN in 4, 8, 16).
 cudaError_t launch_kk_grid(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I, float2* xdisc,
-                           float2* scratch, cudaStream_t st);
+                           float2* scratch, const int32_t* status, cudaStream_t st);
+size_t kkr_smem_bytes(int BN);
+int configure_kkr(int BN, size_t smem);
+cudaError_t launch_kk_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I, float2* xdisc,
+                          float2* scratch, const int32_t* status, cudaStream_t st);
 // Static scratch of the allocation-free entry point (kernels_noalloc.cu).
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(int device, float2** out);

@@ -1,0 +1,176 @@
+// kernels_kkr.cu - Kramers-Kronig recovery (WSI-APIC Eq. 4-7) with
+// register-resident half-warp FFTs (n = 16 BN).
+//
+// One block per (tile, NA-matching image) problem, persistent over problems;
+// an n x n complex scratch grid per block (L2-resident). Each half-warp
+// transforms one row or column at a time:
+//   P1 rows: log(max(I, 1e-6 mean I)), forward transform along x
+//   P2 cols: forward along y, half-plane mask of Eq. 5, inverse along y
+//   P3 rows: inverse along x, / n^2, exp (Eq. 6), forward along x
+//   P4 cols: forward along y, / n^2 (Fourier-series coefficients, Eq. 7)
+// then the values at K = k_p - k_i for the pupil points k_p are gathered.
+#include <math.h>
+
+#include "../../include/apic.h"
+#include "internal.cuh"
+#include "regfft.cuh"
+
+namespace apic {
+
+namespace {
+
+constexpr int kKKThreads = 512;
+constexpr int kKKHW = kKKThreads / 16;
+
+__device__ __forceinline__ int sfreq_kk(int i, int n) { return i < n / 2 ? i : i - n; }
+
+}  // namespace
+
+size_t kkr_smem_bytes(int BN) {
+    const int hws = std::max(17 * BN, 16 * (BN + 1));
+    return (size_t)kKKHW * hws * sizeof(float2) + (size_t)2 * 16 * BN * sizeof(float2) + 64 * sizeof(double);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kKKThreads, 1)
+k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict__ xdisc, float2* __restrict__ scratch,
+         const int32_t* __restrict__ status) {
+    constexpr int n = 16 * BN, HWS = HWSize<BN>::value;
+    extern __shared__ float4 smem4[];
+    float2* hw_area = reinterpret_cast<float2*>(smem4);
+    float2* tw = hw_area + kKKHW * HWS;
+    double* red = reinterpret_cast<double*>(tw + 2 * n);
+    make_step_twiddles(tw, P.tw_n, BN);
+    __syncthreads();
+
+    const int hw = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const HalfWarp h{t, (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu, hw_area + hw * HWS};
+    float2* G = scratch + (size_t)blockIdx.x * n * n;
+    const float inv_n2 = 1.0f / (float)(n * n);
+    const long long hh = (long long)P.h * P.h, ww = (long long)P.w * P.w;
+    const int nprob = n_tiles * P.n_bf;
+
+    for (int prob = blockIdx.x; prob < nprob; prob += gridDim.x) {
+        const int tile = prob / P.n_bf, i = prob - tile * P.n_bf;
+        if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
+        const float* img = I + ((size_t)tile * P.n_img + i) * n * n;
+        const int kix = P.led_x[i], kiy = P.led_y[i];
+        double s = 0;
+        const float4* img4 = reinterpret_cast<const float4*>(img);
+        for (int q = threadIdx.x; q < n * n / 4; q += blockDim.x) {
+            const float4 v = img4[q];
+            s += (double)v.x + v.y + v.z + v.w;
+        }
+        s = block_sum(s, red);
+        const float eps = (float)(1e-6 * s / ((double)n * n));
+
+        // P1: rows, log then forward along x
+        for (int r = hw; r < n; r += kKKHW) {
+            const float* row = img + (size_t)r * n;
+            float2 v[BN], o[16];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) v[j] = make_float2(logf(fmaxf(row[t + 16 * j], eps)), 0.f);
+            fft_alpha<BN, false>(v, o, h, tw);
+            if (t < BN) {
+                float2* gr = G + (size_t)r * n;
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) gr[t + BN * k1] = o[k1];
+            }
+        }
+        __syncthreads();
+        // P2: columns, forward along y, Eq. 5 mask, inverse along y
+        for (int x = hw; x < n; x += kKKHW) {
+            float2 v[BN], o[16];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * n + x];
+            fft_alpha<BN, false>(v, o, h, tw);
+            if (t < BN) {
+                const long long kxp = (long long)sfreq_kk(x, n) * kix * hh;
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const long long dot = kxp + (long long)sfreq_kk(t + BN * k1, n) * kiy * ww;
+                    const float f = dot < 0 ? 1.f : (dot == 0 ? 0.5f : 0.f);
+                    o[k1] = cscale(o[k1], f);
+                }
+            }
+            fft_beta<BN, true>(o, v, h, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < BN; ++k1) G[(size_t)(t + 16 * k1) * n + x] = v[k1];
+        }
+        __syncthreads();
+        // P3: rows, inverse along x, exp, forward along x
+        for (int r = hw; r < n; r += kKKHW) {
+            float2* gr = G + (size_t)r * n;
+            float2 v[BN], o[16];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) v[j] = gr[t + 16 * j];
+            fft_alpha<BN, true>(v, o, h, tw);
+            if (t < BN) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const float2 z = cscale(o[k1], inv_n2);
+                    float sn, cs;
+                    sincosf(z.y, &sn, &cs);
+                    const float e = expf(z.x);
+                    o[k1] = make_float2(e * cs, e * sn);
+                }
+            }
+            fft_beta<BN, false>(o, v, h, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < BN; ++k1) gr[t + 16 * k1] = v[k1];
+        }
+        __syncthreads();
+        // P4: columns, forward along y, series normalisation
+        for (int x = hw; x < n; x += kKKHW) {
+            float2 v[BN], o[16];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * n + x];
+            fft_alpha<BN, false>(v, o, h, tw);
+            if (t < BN) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) G[(size_t)(t + BN * k1) * n + x] = cscale(o[k1], inv_n2);
+            }
+        }
+        __syncthreads();
+        float2* out = xdisc + ((size_t)tile * P.n_bf + i) * P.npup;
+        for (int p = threadIdx.x; p < P.npup; p += blockDim.x) {
+            const int Kx = P.pup_x[p] - kix, Ky = P.pup_y[p] - kiy;
+            out[p] = G[(size_t)freq_index(Ky, n) * n + freq_index(Kx, n)];
+        }
+        __syncthreads();
+    }
+}
+
+using KKRKernel = void (*)(DevPlan, int, const float*, float2*, float2*, const int32_t*);
+
+static KKRKernel kkr_kernel(int BN) {
+    switch (BN) {
+        case 4: return k_kk_reg<4>;
+        case 8: return k_kk_reg<8>;
+        case 16: return k_kk_reg<16>;
+        default: return nullptr;
+    }
+}
+
+int configure_kkr(int BN, size_t smem) {
+    KKRKernel f = kkr_kernel(BN);
+    if (!f) return 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kKKThreads, smem) != cudaSuccess) return 0;
+    return occ;
+}
+
+cudaError_t launch_kk_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I, float2* xdisc,
+                          float2* scratch, const int32_t* status, cudaStream_t st) {
+    KKRKernel f = kkr_kernel(P.h / 16);
+    if (!f) return cudaErrorInvalidValue;
+    grid = min(grid, n_tiles * P.n_bf);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    f<<<grid, kKKThreads, smem, st>>>(P, n_tiles, I, xdisc, scratch, status);
+    return cudaGetLastError();
+}
+
+}  // namespace apic

@@ -187,10 +187,10 @@ cudaError_t launch_kk(const DevPlan& P, const Launch& L, int n_tiles, const floa
 }
 
 cudaError_t launch_kk_grid(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I, float2* xdisc,
-                           float2* scratch, cudaStream_t st) {
+                           float2* scratch, const int32_t* status, cudaStream_t st) {
     grid = min(grid, n_tiles * P.n_bf);
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    k_kk<<<grid, kThreads, smem, st>>>(P, n_tiles, I, xdisc, scratch, nullptr);
+    k_kk<<<grid, kThreads, smem, st>>>(P, n_tiles, I, xdisc, scratch, status);
     return cudaGetLastError();
 }
 

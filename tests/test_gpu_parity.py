@@ -239,12 +239,13 @@ def test_full_size_batch_sampled_tiles():
 
 
 @pytest.mark.parametrize("n", [64, 128, 256])
-def test_register_and_legacy_darkfield_kernels_agree(n):
-    """The register-FFT darkfield kernel (correlation grid 16 B) and the shared-memory
-    Stockham kernel (power-of-two grid) solve the same least-squares problems."""
+def test_register_and_legacy_kernels_agree(n):
+    """The register-FFT Kramers-Kronig and darkfield kernels (correlation grid 16 B)
+    and the shared-memory Stockham kernels (power-of-two grid) compute the same
+    spectra and solve the same least-squares problems."""
     I, _, _ = make_tiles(n, 2, seed=90 + n)
     fields = []
-    for flags in (0, apic.APIC_LEGACY_DF):
+    for flags in (0, apic.APIC_LEGACY_KERNELS):
         plan = new_plan(n, max_tiles=2, flags=flags)
         H = plan.info.out_h
         field = torch.zeros((2, H, 2 * H), dtype=torch.float32, device="cuda")
