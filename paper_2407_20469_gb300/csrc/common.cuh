@@ -46,4 +46,26 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return t;
 }
 
+// Block-wide sum of doubles. Warps reduce with shuffles, warp 0 combines the
+// warp partials and broadcasts the total, so each thread does five FP64 adds
+// rather than one per warp. `red` holds 64 doubles; the caller alternates
+// `parity` (0/1) between consecutive calls so that partials of one call are
+// never overwritten while another warp is still reading them.
+__device__ __forceinline__ double block_sum2(double v, double* red, int& parity) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    double* r = red + parity * 32;
+    if (lane == 0) r[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < nw ? r[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) r[31] = t;
+    }
+    __syncthreads();
+    const double total = r[31];
+    parity ^= 1;
+    return total;
+}
+
 }  // namespace apic

@@ -11,8 +11,8 @@
 //     R2 rows of Q: forward along x, keep Q, inverse along x (in place)
 //     C2 columns:   inverse along y, * p / m^2, forward along y        -> GU
 //     R3 rows of U: forward along x, gather w on U, <d, w>
-//   then x += alpha d, s -= alpha w, d = s + beta d. Transforms FP32; inner
-//   products, step lengths and the solution FP64.
+//   then x += alpha d, s -= alpha w, and d = s + beta d (folded into the next
+//   R1). Transforms FP32; inner products, step lengths and the solution FP64.
 // GU / GQ are band-row grids (only rows holding U, P or Q points) and the known
 // field p is stored column-major, all in the block's scratch (L2-resident).
 // One block per tile (persistent); images of a tile are sequential. Each pass
@@ -57,9 +57,15 @@ struct ValKnown {       // P(c) = O_known(K) exp(j phi(c))
         return cmul(sp[ap[e]], make_float2(cs, sn));
     }
 };
-struct ValVec {
-    const float2* v;
-    __device__ float2 operator()(int e) const { return v[e]; }
+struct ValNextDir {     // d = s + beta d (stored back), scattered into the rows
+    const float2* sv;
+    float2* dv;
+    float beta;
+    __device__ float2 operator()(int e) const {
+        const float2 d = cadd(sv[e], cscale(dv[e], beta));
+        dv[e] = d;
+        return d;
+    }
 };
 struct OutStart {       // s = d = C^H b, x = 0; returns |s|^2
     float2* sv;
@@ -86,7 +92,8 @@ struct OutDot {         // w = C^H C d; returns Re <d, w>
 template <int B>
 struct MidKnownField {  // store p column-major, replace by |p|^2
     float2* PF;
-    __device__ void operator()(float2 (&o)[16], int x, int t) const {
+    static constexpr bool kReadsField = false;
+    __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&)[16]) const {
         float2* col = PF + (size_t)x * (16 * B);
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) {
@@ -96,14 +103,14 @@ struct MidKnownField {  // store p column-major, replace by |p|^2
     }
 };
 template <int B, bool CONJ>
-struct MidTimesField {  // o *= p / m^2 or conj(p) / m^2
+struct MidTimesField {  // o *= p / m^2 or conj(p) / m^2 (p loaded by the caller)
     const float2* PF;
     float scale;
-    __device__ void operator()(float2 (&o)[16], int x, int t) const {
-        const float2* col = PF + (size_t)x * (16 * B);
+    static constexpr bool kReadsField = true;
+    __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&pf)[16]) const {
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) {
-            const float2 p = col[t + B * k1];
+            const float2 p = pf[k1];
             o[k1] = cscale(CONJ ? cmulc(o[k1], p) : cmul(o[k1], p), scale);
         }
     }
@@ -162,21 +169,28 @@ __device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float
 
 // columns: rows yi0.. (ni of them) of Gi are the input, the rest zero; inverse along
 // y, mid, forward along y; rows yo0.. (no) stored to Go. Each half-warp reads and
-// writes its own columns straight from the (L2-resident) grids. Ends with __syncthreads.
+// writes its own columns straight from the (L2-resident) grids; the known-field
+// values of the column are loaded up front with the inputs. Ends with __syncthreads.
 template <int B, class Mid>
 __device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi, int yi0, int ni, float2* Go,
                                        int yo0, int no, Mid mid) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
     for (int x = w.hw; x < m; x += kHW) {
-        float2 v[B], o[16];
+        float2 v[B], o[16], pf[16];
+        if (Mid::kReadsField) {    // issued with the inputs so both latencies overlap
+            const float2* col = mid.PF + (size_t)x * m;
+            const int tt = w.t < B ? w.t : 0;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) pf[k1] = col[tt + B * k1];
+        }
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             const int bb = sfreq(w.t + 16 * j, m) - yi0;
             v[j] = (bb >= 0 && bb < ni) ? Gi[(size_t)bb * m + x] : make_float2(0.f, 0.f);
         }
         fft_alpha<B, true>(v, o, h, tw);
-        if (w.t < B) mid(o, x, w.t);
+        if (w.t < B) mid(o, x, w.t, pf);
         fft_beta<B, false>(o, v, h, tw);
 #pragma unroll
         for (int k1 = 0; k1 < B; ++k1) {
@@ -410,21 +424,23 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             // s = d = C^H b
             pass_cols<B>(w, tw_m, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
             const double g0 = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutStart{sv, dv, xv});
-            const double gamma0 = block_sum(g0, red);
+            int par = 0;
+            const double gamma0 = block_sum2(g0, red, par);
 
             // CGNR
             double gamma = gamma0;
             bool conv = !(gamma0 > 1e-300);
             const double stop = (double)tol * (double)tol * gamma0;
             int it = 0;
+            float bf = 0.f;                  // first direction: d = s
             for (; it < iters && !conv; ++it) {
-                pass_rows_in<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, ValVec{dv});
+                pass_rows_in<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, ValNextDir{sv, dv, bf});
                 __syncthreads();
                 pass_cols<B>(w, tw_m, GU, uy0, nU, GQ, qy0, nQ, MidTimesField<B, true>{PF, inv_m2});
                 pass_rows_mask<B>(w, tw_m, GQ, nQ, qmask);
                 pass_cols<B>(w, tw_m, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
                 const double dw = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutDot{wv, dv});
-                const double delta = block_sum(dw, red);
+                const double delta = block_sum2(dw, red, par);
                 if (!(delta > 0)) break;
                 const double alpha = gamma / delta;
                 const float af = (float)alpha;
@@ -439,11 +455,9 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
                     sv[e] = s;
                     g2 += (double)s.x * s.x + (double)s.y * s.y;
                 }
-                const double gnew = block_sum(g2, red);
-                const float bf = (float)(gnew / gamma);
+                const double gnew = block_sum2(g2, red, par);
+                bf = (float)(gnew / gamma);
                 gamma = gnew;
-                for (int e = threadIdx.x; e < N; e += blockDim.x) dv[e] = cadd(sv[e], cscale(dv[e], bf));
-                __syncthreads();
                 conv = gnew <= stop;
             }
             if (!conv) notconv = true;
