@@ -189,6 +189,21 @@ apic_status apic_plan_counters(apic_plan* plan, int64_t* h_out, int n, int reset
 apic_status apic_plan_timing(apic_plan* plan, int enable);
 apic_status apic_plan_stage_ms(apic_plan* plan, double* h_ms, int n, int32_t* h_calls, int reset);
 
+/*
+ * apic_reconstruct_batch from and to HOST memory, pipelined: the tiles are
+ * processed in chunks (the first one GPU-wide wave of the darkfield kernel,
+ * the rest up to four waves or max_tiles); while one chunk is reconstructed, the next chunk's
+ * intensities are copied in and the previous chunk's results copied out
+ * (three internal streams, two sets of device staging buffers that the plan
+ * allocates on first use and keeps). For the copies to overlap the host
+ * buffers must be pinned (cudaHostAlloc / cudaHostRegister); pageable buffers
+ * work but serialise. Returns when all results are in host memory.
+ *   h_intensity [n_tiles][n_bf + n_df][h][w] f32, h_field [n_tiles][u h][u w]
+ *   complex64, h_zernike [n_tiles][15] f32, h_tile_status [n_tiles] or NULL.
+ */
+apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_intensity, float* h_field,
+                                  float* h_zernike, int32_t* h_tile_status);
+
 /* ---- Stages of apic_reconstruct_batch, for testing and custom pipelines ---- */
 
 /*

@@ -27,7 +27,7 @@ APIC_TABLE_LEDS, APIC_TABLE_PUPIL, APIC_TABLE_APERTURE = 0, 1, 2
 EXPORTS = [
     "apic_status_string", "apic_last_error", "apic_plan_create", "apic_plan_destroy",
     "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_counters", "apic_plan_timing",
-    "apic_plan_stage_ms", "apic_reconstruct_batch", "apic_background",
+    "apic_plan_stage_ms", "apic_reconstruct_batch", "apic_reconstruct_host", "apic_background",
     "apic_kk_spectra", "apic_kk_spectra_noalloc", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
     "apic_pupil", "apic_simulate",
 ]
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_plan_timing": (i32, [vp, i32]),
         "apic_plan_stage_ms": (i32, [vp, C.POINTER(C.c_double), i32, C.POINTER(C.c_int32), i32]),
         "apic_reconstruct_batch": (i32, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "apic_reconstruct_host": (i32, [vp, i32, vp, vp, vp, vp]),
         "apic_background": (i32, [vp, i32, vp, vp, vp, vp]),
         "apic_kk_spectra": (i32, [vp, i32, vp, vp, vp]),
         "apic_kk_spectra_noalloc": (i32, [vp, i32, vp, vp, vp]),
@@ -209,6 +210,11 @@ class Plan:
         _check(load().apic_reconstruct_batch(self.handle, n_tiles, _ptr(intensity), _ptr(field), _ptr(zernike),
                                              _ptr(pupil), _ptr(tile_status), _stream(stream)),
                "apic_reconstruct_batch")
+
+    def reconstruct_host(self, n_tiles, intensity, field, zernike, tile_status=None):
+        """Host-memory reconstruction, pipelined in chunks (pass pinned CPU tensors for overlap)."""
+        _check(load().apic_reconstruct_host(self.handle, n_tiles, _ptr(intensity), _ptr(field), _ptr(zernike),
+                                            _ptr(tile_status)), "apic_reconstruct_host")
 
     def background(self, n_tiles, intensity, contrast2, tile_status, stream=None):
         _check(load().apic_background(self.handle, n_tiles, _ptr(intensity), _ptr(contrast2), _ptr(tile_status),

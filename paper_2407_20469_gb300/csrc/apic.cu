@@ -95,6 +95,17 @@ struct apic_plan {
     bool use_reg = false;        // register-FFT darkfield kernel
     size_t smem_dfr = 0;
     int grid_dfr = 0;
+    // host-buffer pipeline (apic_reconstruct_host), created on first use
+    struct HostIO {
+        bool ready = false;
+        int chunk = 0;
+        cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+        cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
+        float* d_in[2] = {};
+        float* d_field[2] = {};
+        float* d_zern[2] = {};
+        int32_t* d_status[2] = {};
+    } io;
     bool use_kkr = false;        // register-FFT Kramers-Kronig kernel
     size_t smem_kkr = 0;
     int grid_kkr = 0;
@@ -521,6 +532,16 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         cudaDeviceSynchronize();
         for (void* p : plan->allocs) cudaFree(p);
         for (auto e : plan->events) cudaEventDestroy(e);
+        if (plan->io.ready) {
+            for (int b = 0; b < 2; ++b) {
+                cudaEventDestroy(plan->io.in_done[b]);
+                cudaEventDestroy(plan->io.comp_done[b]);
+                cudaEventDestroy(plan->io.out_done[b]);
+            }
+            cudaStreamDestroy(plan->io.s_in);
+            cudaStreamDestroy(plan->io.s_comp);
+            cudaStreamDestroy(plan->io.s_out);
+        }
     }
     delete plan;
     return APIC_OK;
@@ -781,6 +802,72 @@ apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* I,
             APIC_TRY_LAUNCH(launch_pupil(D, nt, plan->phi, (float2*)pupil + (size_t)t0 * D.h * D.w, stt, st));
         if (last) tm.mark(6, 1);
     }
+    return APIC_OK;
+}
+
+apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I, float* h_field, float* h_zern,
+                                  int32_t* h_status) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!h_I || !h_field || !h_zern) return fail(APIC_EINVAL, "NULL intensity, field or zernike buffer");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device)
+        return fail(APIC_EINVAL, "current device differs from the plan's device");
+    if (n_tiles == 0) return APIC_OK;
+    const DevPlan& D = plan->dev;
+    const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
+    auto& io = plan->io;
+    // chunk sizes follow the darkfield grid (one tile per block): the first chunk
+    // is one full wave so computation starts after a short copy, the rest go in
+    // chunks of up to four waves; the total number of waves matches one batch.
+    const int wave = std::max(1, plan->use_reg ? plan->grid_dfr : plan->L.grid_df);
+    const int max_chunk = std::max(1, std::min(plan->max_tiles, 4 * wave));
+    if (!io.ready) {
+        io.chunk = max_chunk;
+        const size_t C = (size_t)io.chunk;
+        APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_in, cudaStreamNonBlocking));
+        APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_comp, cudaStreamNonBlocking));
+        APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_out, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.in_done[b], cudaEventDisableTiming));
+            APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.comp_done[b], cudaEventDisableTiming));
+            APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.out_done[b], cudaEventDisableTiming));
+            if ((s = dmalloc(plan, (void**)&io.d_in[b], C * in_tile * sizeof(float))) != APIC_OK) return s;
+            if ((s = dmalloc(plan, (void**)&io.d_field[b], C * out_tile * sizeof(float2))) != APIC_OK) return s;
+            if ((s = dmalloc(plan, (void**)&io.d_zern[b], C * APIC_N_ZERNIKE * sizeof(float))) != APIC_OK) return s;
+            if ((s = dmalloc(plan, (void**)&io.d_status[b], C * sizeof(int32_t))) != APIC_OK) return s;
+        }
+        io.ready = true;
+    }
+    int k = 0;
+    for (int t0 = 0, nt = 0; t0 < n_tiles; t0 += nt, ++k) {
+        nt = std::min(k == 0 ? std::min(wave, io.chunk) : io.chunk, n_tiles - t0);
+        const int b = k & 1;
+        // copy in once buffer b's previous reconstruction has consumed its inputs
+        if (k >= 2) APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_in, io.comp_done[b], 0));
+        APIC_TRY_CUDA(cudaMemcpyAsync(io.d_in[b], h_I + (size_t)t0 * in_tile, (size_t)nt * in_tile * sizeof(float),
+                                      cudaMemcpyHostToDevice, io.s_in));
+        APIC_TRY_CUDA(cudaEventRecord(io.in_done[b], io.s_in));
+        // reconstruct once the inputs are in and buffer b's previous results are out
+        APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_comp, io.in_done[b], 0));
+        if (k >= 2) APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_comp, io.out_done[b], 0));
+        s = apic_reconstruct_batch(plan, nt, io.d_in[b], io.d_field[b], io.d_zern[b], nullptr, io.d_status[b],
+                                   io.s_comp);
+        if (s != APIC_OK) return s;
+        APIC_TRY_CUDA(cudaEventRecord(io.comp_done[b], io.s_comp));
+        // copy out
+        APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.comp_done[b], 0));
+        APIC_TRY_CUDA(cudaMemcpyAsync(h_field + (size_t)t0 * out_tile * 2, io.d_field[b],
+                                      (size_t)nt * out_tile * sizeof(float2), cudaMemcpyDeviceToHost, io.s_out));
+        APIC_TRY_CUDA(cudaMemcpyAsync(h_zern + (size_t)t0 * APIC_N_ZERNIKE, io.d_zern[b],
+                                      (size_t)nt * APIC_N_ZERNIKE * sizeof(float), cudaMemcpyDeviceToHost, io.s_out));
+        if (h_status)
+            APIC_TRY_CUDA(cudaMemcpyAsync(h_status + t0, io.d_status[b], (size_t)nt * sizeof(int32_t),
+                                          cudaMemcpyDeviceToHost, io.s_out));
+        APIC_TRY_CUDA(cudaEventRecord(io.out_done[b], io.s_out));
+    }
+    APIC_TRY_CUDA(cudaStreamSynchronize(io.s_out));
+    APIC_TRY_CUDA(cudaStreamSynchronize(io.s_comp));
     return APIC_OK;
 }
 

@@ -336,3 +336,24 @@ def test_512_tiles_with_8_24_images_recover_a_known_object():
     truth[ap[:, 1] % H, ap[:, 0] % H] = O[ap[:, 1] % H, ap[:, 0] % H]
     assert rel_l2(as_complex(field)[0], grid.synthesize(truth)) < 1e-2
     assert pupil_rms(zz[0].cpu().numpy(), c_true[0]) < PUPIL_TOL
+
+
+def test_reconstruct_host_matches_device_path():
+    """apic_reconstruct_host (pinned host buffers, chunked pipeline) returns what
+    apic_reconstruct_batch returns on device buffers."""
+    n, count = 64, 5
+    I, _, _ = make_tiles(n, count, seed=81)
+    plan = new_plan(n, max_tiles=2)                     # chunks of 2: double buffering used
+    H = plan.info.out_h
+    field = torch.zeros((count, H, 2 * H), dtype=torch.float32, device="cuda")
+    z = torch.zeros((count, 15), dtype=torch.float32, device="cuda")
+    st = torch.zeros(count, dtype=torch.int32, device="cuda")
+    plan.reconstruct_batch(count, dev(I), field, z, None, st)
+    torch.cuda.synchronize()
+    Ih = torch.from_numpy(I).pin_memory()
+    fh = torch.zeros((count, H, 2 * H), dtype=torch.float32).pin_memory()
+    zh = torch.zeros((count, 15), dtype=torch.float32).pin_memory()
+    sh = torch.full((count,), -1, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        plan.reconstruct_host(count, Ih, fh, zh, sh)
+        assert torch.equal(fh, field.cpu()) and torch.equal(zh, z.cpu()) and torch.equal(sh, st.cpu())
