@@ -59,6 +59,10 @@ typedef enum {
 #define APIC_TILE_BACKGROUND  1   /* below the background-contrast threshold (Sec. 3.2) */
 #define APIC_TILE_NOTCONV     2   /* a darkfield solve stopped above its tolerance      */
 #define APIC_TILE_BADINPUT    4   /* non-finite or negative intensity in the stack      */
+#define APIC_TILE_LEARNED     8   /* low contrast: pupil taken from the network, tile
+                                     reconstructed with it (apic_reconstruct_learned)   */
+#define APIC_TILE_WARM       16   /* the solve started from the network's coefficients
+                                     left the smaller residual and was kept             */
 
 /* Plan flags. */
 #define APIC_SKIP_BACKGROUND  1   /* background tiles: outputs zeroed, no reconstruction */
@@ -91,6 +95,7 @@ typedef struct {
 } apic_params;
 
 typedef struct apic_plan apic_plan;
+typedef struct apic_net apic_net;
 
 /* Sizes of a plan's fixed index sets (for callers laying out stage buffers). */
 typedef struct {
@@ -293,6 +298,88 @@ apic_status apic_pupil(apic_plan* plan, int n_tiles, const float* d_zernike, flo
 apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* d_object,
                           const float* d_zernike, float photons, uint64_t seed,
                           float* d_intensity, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned aberration network. The paper has no counterpart: its aberration
+ * estimate is the closed-form solve of Eq. 10 alone. This small CNN predicts
+ * the field-dependent Noll coefficients 4..15 of a tile from the magnitudes of
+ * its NA-matching intensity spectra and its position, replaces the solve on
+ * low-contrast tiles (where Eq. 10 is ill-conditioned) and warm-starts it
+ * elsewhere; the closed-form solve stays the fallback and the judge.
+ *
+ * Input features, per tile: feat [64][64][8] float32 (NHWC), channel i =
+ *   log(|F(I_i)(kx, ky)| / |F(I_i)(0, 0)| + 1e-4) at [ky + 32][kx + 32],
+ *   kx, ky in [-32, 32), F the unnormalised 2-D DFT, I_i the i-th NA-matching
+ *   image; uv [2] float32, the tile position on the slide.
+ * Layers: conv3x3(pad 1) 8->32, ReLU, maxpool 2 | conv 32->64, ReLU, pool |
+ *   conv 64->128, ReLU, pool | conv 128->256, ReLU, global mean | concat uv |
+ *   dense 258->256, ReLU | dense 256->12. BF16 weights and layer inputs,
+ *   FP32 accumulation, FP32 master weights, gradients and optimizer state.
+ * Parameters (apic_net_param_count() = 459244 floats): six row-major
+ *   matrices W_l [out_l][taps_l + 1] back to back, bias in the last column;
+ *   conv taps ordered (dy, dx, c_in) with dy, dx in 0..2 (offsets -1..1),
+ *   dense taps the input features (256 means, then u, v for the first).
+ * All device pointers; calls are asynchronous on `stream` unless stated.
+ * ------------------------------------------------------------------------ */
+
+/* Floats per parameter vector / per tile of features. */
+size_t apic_net_param_count(void);
+size_t apic_net_feature_count(void);
+
+/* Network with workspace for batches up to max_batch (1..65536) on the current
+ * device; parameters start at zero. Errors: APIC_EINVAL, APIC_ENOMEM, APIC_ECUDA. */
+apic_status apic_net_create(int max_batch, apic_net** out);
+/* Free the network (synchronises the device first). NULL is a no-op. */
+apic_status apic_net_destroy(apic_net* net);
+
+/* Copy parameters from / to host memory (count must be apic_net_param_count());
+ * set_params also clears the optimizer moments. Synchronous. */
+apic_status apic_net_set_params(apic_net* net, const float* h_params, size_t count);
+apic_status apic_net_get_params(const apic_net* net, float* h_params, size_t count);
+/* Gradients of the last apic_net_backward, same layout. Synchronous. */
+apic_status apic_net_get_grads(const apic_net* net, float* h_grads, size_t count);
+
+/* Forward pass: d_feat [batch][64][64][8], d_uv [batch][2] (NULL: zeros),
+ * d_out [batch][15] (Noll 1..3 written as 0; NULL: kept internally). The
+ * features must stay valid until the matching apic_net_backward. */
+apic_status apic_net_forward(apic_net* net, int batch, const float* d_feat, const float* d_uv,
+                             float* d_out, void* stream);
+/* Mean squared error of the last forward against d_target [batch][15] (Noll
+ * 4..15 used) and its gradient with respect to every parameter. d_loss: one
+ * float, or NULL. */
+apic_status apic_net_backward(apic_net* net, const float* d_target, float* d_loss, void* stream);
+/* AdamW step (bias-corrected moments, decoupled weight decay) with the last
+ * gradients; step counts from 1. */
+apic_status apic_net_adamw(apic_net* net, float lr, float beta1, float beta2, float eps,
+                           float weight_decay, int step, void* stream);
+/* Activation of the last forward copied to host float32 (synchronous):
+ * which 0..3 the ReLU output of conv layer 0..3 ([batch][H][H][C], H = 64, 32,
+ * 16, 8), 4 the dense input [batch][258], 5 the hidden layer [batch][256], 6 the
+ * outputs [batch][12]. count must match. */
+apic_status apic_net_activation(const apic_net* net, int which, float* h_out, size_t count);
+
+/* Network input features of n_tiles stacks (the plan's first 8 images, which
+ * must be its 8 NA-matching images): d_feat [n_tiles][64][64][8]. Tiles of 64,
+ * 128 or 256 pixels. */
+apic_status apic_features(apic_plan* plan, int n_tiles, const float* d_intensity, float* d_feat,
+                          void* stream);
+
+/* Learned-assisted reconstruction modes. */
+#define APIC_NET_WARM     1   /* solved tiles also refine from the network's coefficients and
+                                 keep the solution with the smaller wrapped residual        */
+#define APIC_NET_REPLACE  2   /* tiles below bg_contrast take the network's coefficients and
+                                 are reconstructed with them (APIC_TILE_LEARNED)             */
+
+/*
+ * apic_reconstruct_batch with the network: features and network forward per
+ * chunk, then the stages as there, with the aberration stage per `mode`.
+ * d_uv [n_tiles][2] tile positions. With APIC_NET_REPLACE low-contrast tiles
+ * are never skipped. Same buffers and errors as apic_reconstruct_batch.
+ */
+apic_status apic_reconstruct_learned(apic_plan* plan, apic_net* net, int mode, int n_tiles,
+                                     const float* d_intensity, const float* d_uv, float* d_field,
+                                     float* d_zernike, float* d_pupil, int32_t* d_tile_status,
+                                     void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libapic.so")
 
 APIC_OK, APIC_EINVAL, APIC_ENOMEM, APIC_ECUDA, APIC_EGEOMETRY, APIC_EINTERNAL = range(6)
 APIC_TILE_OK, APIC_TILE_BACKGROUND, APIC_TILE_NOTCONV, APIC_TILE_BADINPUT = 0, 1, 2, 4
+APIC_TILE_LEARNED, APIC_TILE_WARM = 8, 16
+APIC_NET_WARM, APIC_NET_REPLACE = 1, 2
 APIC_SKIP_BACKGROUND = 1
 APIC_HOST_ONLY = 2
 APIC_LEGACY_KERNELS = 4
@@ -29,7 +31,9 @@ EXPORTS = [
     "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_counters", "apic_plan_timing",
     "apic_plan_stage_ms", "apic_reconstruct_batch", "apic_reconstruct_host", "apic_background",
     "apic_kk_spectra", "apic_kk_spectra_noalloc", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
-    "apic_pupil", "apic_simulate",
+    "apic_pupil", "apic_simulate", "apic_net_param_count", "apic_net_feature_count", "apic_net_create",
+    "apic_net_destroy", "apic_net_set_params", "apic_net_get_params", "apic_net_get_grads", "apic_net_forward",
+    "apic_net_backward", "apic_net_adamw", "apic_net_activation", "apic_features", "apic_reconstruct_learned",
 ]
 
 
@@ -86,6 +90,19 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_synthesize": (i32, [vp, i32, vp, vp, vp]),
         "apic_pupil": (i32, [vp, i32, vp, vp, vp]),
         "apic_simulate": (i32, [vp, i32, vp, vp, f32, C.c_uint64, vp, vp]),
+        "apic_net_param_count": (sz, []),
+        "apic_net_feature_count": (sz, []),
+        "apic_net_create": (i32, [i32, C.POINTER(vp)]),
+        "apic_net_destroy": (i32, [vp]),
+        "apic_net_set_params": (i32, [vp, C.POINTER(C.c_float), sz]),
+        "apic_net_get_params": (i32, [vp, C.POINTER(C.c_float), sz]),
+        "apic_net_get_grads": (i32, [vp, C.POINTER(C.c_float), sz]),
+        "apic_net_forward": (i32, [vp, i32, vp, vp, vp, vp]),
+        "apic_net_backward": (i32, [vp, vp, vp, vp]),
+        "apic_net_adamw": (i32, [vp, f32, f32, f32, f32, f32, i32, vp]),
+        "apic_net_activation": (i32, [vp, i32, C.POINTER(C.c_float), sz]),
+        "apic_features": (i32, [vp, i32, vp, vp, vp]),
+        "apic_reconstruct_learned": (i32, [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -251,3 +268,120 @@ class Plan:
     def simulate(self, n_tiles, obj, zernike, photons, seed, intensity, stream=None):
         _check(load().apic_simulate(self.handle, n_tiles, _ptr(obj), _ptr(zernike), float(photons), int(seed),
                                     _ptr(intensity), _stream(stream)), "apic_simulate")
+
+    def features(self, n_tiles, intensity, feat, stream=None):
+        """Network input features [n_tiles][64][64][8] of the first 8 images of each stack."""
+        _check(load().apic_features(self.handle, n_tiles, _ptr(intensity), _ptr(feat), _stream(stream)),
+               "apic_features")
+
+    def reconstruct_learned(self, net: "Net", mode, n_tiles, intensity, uv, field, zernike, pupil=None,
+                            tile_status=None, stream=None):
+        _check(load().apic_reconstruct_learned(self.handle, net.handle, int(mode), n_tiles, _ptr(intensity), _ptr(uv),
+                                               _ptr(field), _ptr(zernike), _ptr(pupil), _ptr(tile_status),
+                                               _stream(stream)), "apic_reconstruct_learned")
+
+
+# ----------------------------------------------------------------------------- network
+
+CONV_CHANNELS = (8, 32, 64, 128, 256)
+HIDDEN, OUTPUTS = 256, 12
+CROP = 64
+
+
+def param_shapes():
+    """Per-layer (name, shape) in the oracle's convention: conv w [co, ci, 3, 3], dense w [out, in]."""
+    shapes = []
+    for l in range(4):
+        ci, co = CONV_CHANNELS[l], CONV_CHANNELS[l + 1]
+        shapes += [(f"w{l}", (co, ci, 3, 3)), (f"b{l}", (co,))]
+    shapes += [("w4", (HIDDEN, CONV_CHANNELS[4] + 2)), ("b4", (HIDDEN,)), ("w5", (OUTPUTS, HIDDEN)), ("b5", (OUTPUTS,))]
+    return shapes
+
+
+def pack_params(p: dict) -> np.ndarray:
+    """Per-layer arrays -> the library's flat vector (W_l [out][taps + 1], taps (dy, dx, ci), bias last)."""
+    out = []
+    for l in range(6):
+        w, b = np.asarray(p[f"w{l}"], dtype=np.float64), np.asarray(p[f"b{l}"], dtype=np.float64)
+        if l < 4:
+            w = w.transpose(0, 2, 3, 1).reshape(w.shape[0], -1)
+        out.append(np.concatenate([w, b[:, None]], axis=1).ravel())
+    return np.concatenate(out).astype(np.float32)
+
+
+def unpack_params(v: np.ndarray) -> dict:
+    """Inverse of pack_params (float64 arrays)."""
+    v = np.asarray(v, dtype=np.float64)
+    p, o = {}, 0
+    shapes = dict(param_shapes())
+    for l in range(6):
+        ws = shapes[f"w{l}"]
+        rows = ws[0]
+        taps = int(np.prod(ws[1:]))
+        m = v[o:o + rows * (taps + 1)].reshape(rows, taps + 1)
+        o += rows * (taps + 1)
+        w = m[:, :taps]
+        if l < 4:
+            w = w.reshape(rows, 3, 3, ws[1]).transpose(0, 3, 1, 2)
+        p[f"w{l}"] = np.ascontiguousarray(w)
+        p[f"b{l}"] = m[:, taps].copy()
+    return p
+
+
+class Net:
+    """An apic_net: the aberration network with workspace for batches up to max_batch."""
+
+    def __init__(self, max_batch: int):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.apic_net_create(int(max_batch), C.byref(h)), "apic_net_create")
+        self.handle = h
+        self.max_batch = int(max_batch)
+        self.n_params = int(lib.apic_net_param_count())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().apic_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat: np.ndarray):
+        v = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(load().apic_net_set_params(self.handle, v.ctypes.data_as(C.POINTER(C.c_float)), v.size),
+               "apic_net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        v = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().apic_net_get_params(self.handle, v.ctypes.data_as(C.POINTER(C.c_float)), v.size),
+               "apic_net_get_params")
+        return v
+
+    def get_grads(self) -> np.ndarray:
+        v = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().apic_net_get_grads(self.handle, v.ctypes.data_as(C.POINTER(C.c_float)), v.size),
+               "apic_net_get_grads")
+        return v
+
+    def forward(self, batch, feat, uv, out=None, stream=None):
+        _check(load().apic_net_forward(self.handle, int(batch), _ptr(feat), _ptr(uv), _ptr(out), _stream(stream)),
+               "apic_net_forward")
+
+    def backward(self, target, loss=None, stream=None):
+        _check(load().apic_net_backward(self.handle, _ptr(target), _ptr(loss), _stream(stream)), "apic_net_backward")
+
+    def adamw(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+        _check(load().apic_net_adamw(self.handle, float(lr), float(beta1), float(beta2), float(eps),
+                                     float(weight_decay), int(step), _stream(stream)), "apic_net_adamw")
+
+    def activation(self, which: int, batch: int) -> np.ndarray:
+        shapes = {0: (64, 64, 32), 1: (32, 32, 64), 2: (16, 16, 128), 3: (8, 8, 256), 4: (258,), 5: (256,),
+                  6: (12,)}
+        out = np.zeros((batch,) + shapes[which], dtype=np.float32)
+        _check(load().apic_net_activation(self.handle, int(which), out.ctypes.data_as(C.POINTER(C.c_float)),
+                                          out.size), "apic_net_activation")
+        return out

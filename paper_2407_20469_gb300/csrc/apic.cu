@@ -109,6 +109,8 @@ struct apic_plan {
     bool use_kkr = false;        // register-FFT Kramers-Kronig kernel
     size_t smem_kkr = 0;
     int grid_kkr = 0;
+    float* feat = nullptr;                       // learned path: features, network coefficients
+    float* c_net = nullptr;
     unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
     long long launches = 0;                      // kernel launches issued
     // stage timing: ring of kTimingSlots calls x kStages x {start, stop}
@@ -438,7 +440,84 @@ struct StageTimer {
     }
 };
 
+// Learned-path buffers (features and network coefficients for max_tiles tiles),
+// allocated on the first learned call.
+apic_status learned_buffers(apic_plan* p) {
+    if (p->feat) return APIC_OK;
+    if (!p->use_kkr) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (p->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
+    apic_status s;
+    if ((s = dmalloc(p, (void**)&p->feat, (size_t)p->max_tiles * feature_floats() * sizeof(float))) != APIC_OK)
+        return s;
+    if ((s = dmalloc(p, (void**)&p->c_net, (size_t)p->max_tiles * APIC_N_ZERNIKE * sizeof(float))) != APIC_OK)
+        return s;
+    return APIC_OK;
+}
+
+// Background, Kramers-Kronig, aberration (learned when `net`), stitching,
+// darkfield, synthesis and pupil over chunks of max_tiles tiles.
+apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, const float* I, const float* uv,
+                        float* field, float* zern, float* pupil, int32_t* status, cudaStream_t st) {
+    const DevPlan& D = plan->dev;
+    const Launch& L = plan->L;
+    const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
+    const bool replace = net && (mode & APIC_NET_REPLACE);
+    const float thresh2 = replace ? plan->bg_c2 : plan->bg_thresh2;
+    StageTimer tm(plan, st);
+    for (int t0 = 0; t0 < n_tiles; t0 += plan->max_tiles) {
+        const int nt = std::min(plan->max_tiles, n_tiles - t0);
+        const bool first = t0 == 0, last = t0 + nt >= n_tiles;
+        const float* It = I + (size_t)t0 * in_tile;
+        int32_t* stt = status ? status + t0 : plan->status;
+        float* zt = zern + (size_t)t0 * APIC_N_ZERNIKE;
+        // with several chunks a stage's interval spans from its first start to its last stop
+        if (first) tm.mark(0, 0);
+        APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
+        if (last) tm.mark(0, 1);
+        if (first) tm.mark(1, 0);
+        APIC_TRY_LAUNCH(launch_kk_any(plan, 0, nt, It, plan->xdisc, plan->kk_scratch, stt, st));
+        if (last) tm.mark(1, 1);
+        if (first) tm.mark(2, 0);
+        if (net) {
+            APIC_TRY_LAUNCH(launch_features(D, plan->grid_kkr, nt, It, plan->feat, plan->kk_scratch, st));
+            const int nb = net_max_batch(net);
+            for (int b0 = 0; b0 < nt; b0 += nb) {
+                const int bn = std::min(nb, nt - b0);
+                const long long before = net_launches(net);
+                APIC_TRY_CUDA(net_predict(net, bn, plan->feat + (size_t)b0 * feature_floats(),
+                                          uv + (size_t)(t0 + b0) * 2, plan->c_net + (size_t)b0 * APIC_N_ZERNIKE, st));
+                plan->launches += net_launches(net) - before;
+            }
+        }
+        APIC_TRY_LAUNCH(launch_aberration(D, L, nt, plan->xdisc, zt, plan->beta_scratch, plan->ab_passes, stt, st,
+                                          net ? plan->c_net : nullptr, net && (mode & APIC_NET_WARM) ? 1 : 0));
+        if (last) tm.mark(2, 1);
+        if (first) tm.mark(3, 0);
+        APIC_TRY_LAUNCH(launch_phase(D, nt, zt, plan->phi, st));
+        APIC_TRY_LAUNCH(launch_stitch(D, nt, plan->xdisc, plan->phi, plan->spec, stt, st));
+        if (last) tm.mark(3, 1);
+        if (first) tm.mark(4, 0);
+        APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
+        if (last) tm.mark(4, 1);
+        if (first) tm.mark(5, 0);
+        APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, (float2*)field + (size_t)t0 * out_tile, stt, st));
+        if (last) tm.mark(5, 1);
+        if (first) tm.mark(6, 0);
+        if (pupil)
+            APIC_TRY_LAUNCH(launch_pupil(D, nt, plan->phi, (float2*)pupil + (size_t)t0 * D.h * D.w, stt, st));
+        if (last) tm.mark(6, 1);
+    }
+    return APIC_OK;
+}
+
 }  // namespace
+
+namespace apic {
+int record_error(int status, const char* msg) {
+    g_last_error = msg ? msg : "";
+    return status;
+}
+}  // namespace apic
 
 extern "C" {
 
@@ -766,42 +845,33 @@ apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* I,
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device)
         return fail(APIC_EINVAL, "current device differs from the plan's device");
-    const DevPlan& D = plan->dev;
-    const Launch& L = plan->L;
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
-    StageTimer tm(plan, st);
-    for (int t0 = 0; t0 < n_tiles; t0 += plan->max_tiles) {
-        const int nt = std::min(plan->max_tiles, n_tiles - t0);
-        const bool first = t0 == 0, last = t0 + nt >= n_tiles;
-        const float* It = I + (size_t)t0 * in_tile;
-        int32_t* stt = status ? status + t0 : plan->status;
-        float* zt = zern + (size_t)t0 * APIC_N_ZERNIKE;
-        // with several chunks a stage's interval spans from its first start to its last stop
-        if (first) tm.mark(0, 0);
-        APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, plan->bg_thresh2, st));
-        if (last) tm.mark(0, 1);
-        if (first) tm.mark(1, 0);
-        APIC_TRY_LAUNCH(launch_kk_any(plan, 0, nt, It, plan->xdisc, plan->kk_scratch, stt, st));
-        if (last) tm.mark(1, 1);
-        if (first) tm.mark(2, 0);
-        APIC_TRY_LAUNCH(launch_aberration(D, L, nt, plan->xdisc, zt, plan->beta_scratch, plan->ab_passes, stt, st));
-        if (last) tm.mark(2, 1);
-        if (first) tm.mark(3, 0);
-        APIC_TRY_LAUNCH(launch_phase(D, nt, zt, plan->phi, st));
-        APIC_TRY_LAUNCH(launch_stitch(D, nt, plan->xdisc, plan->phi, plan->spec, stt, st));
-        if (last) tm.mark(3, 1);
-        if (first) tm.mark(4, 0);
-        APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
-        if (last) tm.mark(4, 1);
-        if (first) tm.mark(5, 0);
-        APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, (float2*)field + (size_t)t0 * out_tile, stt, st));
-        if (last) tm.mark(5, 1);
-        if (first) tm.mark(6, 0);
-        if (pupil)
-            APIC_TRY_LAUNCH(launch_pupil(D, nt, plan->phi, (float2*)pupil + (size_t)t0 * D.h * D.w, stt, st));
-        if (last) tm.mark(6, 1);
-    }
+    return reconstruct(plan, nullptr, 0, n_tiles, I, nullptr, field, zern, pupil, status, (cudaStream_t)stream);
+}
+
+apic_status apic_reconstruct_learned(apic_plan* plan, apic_net* net, int mode, int n_tiles, const float* I,
+                                     const float* uv, float* field, float* zern, float* pupil, int32_t* status,
+                                     void* stream) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!net) return fail(APIC_EINVAL, "NULL network");
+    if (!I || !uv || !field || !zern) return fail(APIC_EINVAL, "NULL intensity, position, field or zernike buffer");
+    if (mode & ~(APIC_NET_WARM | APIC_NET_REPLACE)) return fail(APIC_EINVAL, "unknown mode bits");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device)
+        return fail(APIC_EINVAL, "current device differs from the plan's device");
+    if ((s = learned_buffers(plan)) != APIC_OK) return s;
+    return reconstruct(plan, net, mode, n_tiles, I, uv, field, zern, pupil, status, (cudaStream_t)stream);
+}
+
+apic_status apic_features(apic_plan* plan, int n_tiles, const float* I, float* feat, void* stream) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!I || !feat) return fail(APIC_EINVAL, "NULL intensity or features");
+    if (!plan->use_kkr) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (plan->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
+    if (n_tiles == 0) return APIC_OK;
+    APIC_TRY_LAUNCH(launch_features(plan->dev, plan->grid_kkr, n_tiles, I, feat, plan->kk_scratch,
+                                    (cudaStream_t)stream));
     return APIC_OK;
 }
 

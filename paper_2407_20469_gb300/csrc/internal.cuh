@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct apic_net;
+
 namespace apic {
 
 constexpr int kThreads = 512;        // threads per block of the transform kernels
@@ -74,8 +76,9 @@ struct Launch {
 };
 
 // Kernel launchers (return cudaError_t of the launch).
+// learned != 0: low-contrast tiles get APIC_TILE_LEARNED instead of APIC_TILE_BACKGROUND.
 cudaError_t launch_background(const DevPlan& P, int n_tiles, const float* I, float* c2, int32_t* status,
-                              float bg_thresh2, cudaStream_t st);
+                              float bg_thresh2, cudaStream_t st, int learned = 0);
 cudaError_t launch_kk(const DevPlan& P, const Launch& L, int n_tiles, const float* I, float2* xdisc,
                       float2* scratch, const int32_t* status, cudaStream_t st);
 // Kramers-Kronig kernels on an explicit grid (each block uses h * w scratch values):
@@ -89,8 +92,10 @@ cudaError_t launch_kk_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, 
 // Static scratch of the allocation-free entry point (kernels_noalloc.cu).
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(int device, float2** out);
+// c0 [tiles][15] learned coefficients or NULL; warm: also refine from c0 and keep the lower residual.
 cudaError_t launch_aberration(const DevPlan& P, const Launch& L, int n_tiles, const float2* xdisc, float* zern,
-                              float* beta_scratch, int passes, const int32_t* status, cudaStream_t st);
+                              float* beta_scratch, int passes, int32_t* status, cudaStream_t st,
+                              const float* c0 = nullptr, int warm = 0);
 cudaError_t launch_phase(const DevPlan& P, int n_tiles, const float* zern, float* phi, cudaStream_t st);
 cudaError_t launch_stitch(const DevPlan& P, int n_tiles, const float2* xdisc, const float* phi, float2* spec,
                           const int32_t* status, cudaStream_t st);
@@ -113,6 +118,19 @@ int configure_dfr(int B, int BN, size_t smem);
 cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
                                  const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
+
+// Network features (net.cu): feat [n_tiles][64][64][8] from the first 8 images
+// of each stack; `scratch` holds h * 64 complex values per block of `grid`.
+cudaError_t launch_features(const DevPlan& P, int grid, int n_tiles, const float* I, float* feat, float2* scratch,
+                            cudaStream_t st);
+size_t feature_floats();
+// Network forward on B tiles (net.cu); out15 [B][15].
+cudaError_t net_predict(struct ::apic_net* n, int B, const float* feat, const float* uv, float* out15,
+                        cudaStream_t st);
+int net_max_batch(const struct ::apic_net* n);
+long long net_launches(const struct ::apic_net* n);
+// Records the message returned by apic_last_error (apic.cu).
+int record_error(int status, const char* msg);
 
 // Sets the dynamic shared-memory limit of a transform kernel and returns its
 // resident blocks per SM (0 on error). which: 0 kk, 1 aberration, 2 darkfield,

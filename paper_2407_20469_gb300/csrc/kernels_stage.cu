@@ -15,7 +15,7 @@ namespace apic {
 // tiles below the threshold and stacks with negative or non-finite values.
 __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles, const float* __restrict__ I,
                                                          float* __restrict__ c2, int32_t* __restrict__ status,
-                                                         float thresh2) {
+                                                         float thresh2, int learned) {
     __shared__ double red[64];
     const int tile = blockIdx.x;
     if (tile >= n_tiles) return;
@@ -48,15 +48,15 @@ __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles,
         const float v = (float)(acc / P.n_bf);
         if (c2) c2[tile] = v;
         int st = 0;
-        if (v < thresh2) st |= APIC_TILE_BACKGROUND;
+        if (v < thresh2) st |= learned ? APIC_TILE_LEARNED : APIC_TILE_BACKGROUND;
         if (anybad) st |= APIC_TILE_BADINPUT;
         status[tile] = st;
     }
 }
 
 cudaError_t launch_background(const DevPlan& P, int n_tiles, const float* I, float* c2, int32_t* status,
-                              float thresh2, cudaStream_t st) {
-    k_background<<<n_tiles, kThreads, 0, st>>>(P, n_tiles, I, c2, status, thresh2);
+                              float thresh2, cudaStream_t st, int learned) {
+    k_background<<<n_tiles, kThreads, 0, st>>>(P, n_tiles, I, c2, status, thresh2, learned);
     return cudaGetLastError();
 }
 
@@ -230,16 +230,63 @@ __device__ void chol_solve12(const double* L, const double* b, double* x) {
     }
 }
 
+// Refinement passes c <- c + LS(wrap(beta - D c)) from the coefficients in
+// cc / cf (shared); returns the sum of squared wrapped residuals of the rows
+// at the final coefficients (every thread gets it).
+__device__ double value_passes(const DevPlan& P, const float* beta, int passes, double* cc, float* cf, double* dc,
+                               double* rhs, double* red) {
+    float g[12];
+    for (int pass = 0; pass < passes; ++pass) {
+        for (int z = 0; z < 12; ++z) g[z] = 0.f;
+        for (int r = threadIdx.x; r < P.nrows; r += blockDim.x) {
+            const float* A = P.row_A + (size_t)r * 12;
+            float pred = 0.f;
+            for (int z = 0; z < 12; ++z) pred += A[z] * cf[z];
+            const float e = wrap_pi(beta[r] - pred);
+            for (int z = 0; z < 12; ++z) g[z] += A[z] * e;
+        }
+        reduce12(g, red, rhs);
+        if (threadIdx.x == 0) {
+            chol_solve12(P.Lval, rhs, dc);
+            for (int z = 0; z < 12; ++z) {
+                cc[z] += dc[z];
+                cf[z] = (float)cc[z];
+            }
+        }
+        __syncthreads();
+    }
+    double res = 0;
+    for (int r = threadIdx.x; r < P.nrows; r += blockDim.x) {
+        const float* A = P.row_A + (size_t)r * 12;
+        float pred = 0.f;
+        for (int z = 0; z < 12; ++z) pred += A[z] * cf[z];
+        const float e = wrap_pi(beta[r] - pred);
+        res += (double)(e * e);
+    }
+    return block_sum(res, red);
+}
+
+// c0 [tiles][15] (may be NULL): learned coefficients. Tiles marked
+// APIC_TILE_LEARNED take c0 as their result. With `warm`, every solved tile
+// also runs the refinement passes from c0 and keeps whichever of the two
+// solutions leaves the smaller wrapped residual (then sets APIC_TILE_WARM).
 __global__ void __launch_bounds__(kThreads) k_aberration(DevPlan P, int n_tiles, const float2* __restrict__ xdisc,
                                                          float* __restrict__ zern, float* __restrict__ beta_scratch,
-                                                         int passes, const int32_t* __restrict__ status) {
+                                                         int passes, int32_t* __restrict__ status,
+                                                         const float* __restrict__ c0, int warm) {
     __shared__ double red[16 * 12];
-    __shared__ double rhs[12], cc[12], dc[12];
+    __shared__ double rhs[12], cc[12], dc[12], cbest[12];
     __shared__ float cf[12];
     float* beta = beta_scratch + (size_t)blockIdx.x * P.nrows;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (skip_tile(status, tile)) {
             if (threadIdx.x < APIC_N_ZERNIKE) zern[(size_t)tile * APIC_N_ZERNIKE + threadIdx.x] = 0.f;
+            continue;
+        }
+        if (c0 && status && (status[tile] & APIC_TILE_LEARNED)) {
+            if (threadIdx.x < APIC_N_ZERNIKE)
+                zern[(size_t)tile * APIC_N_ZERNIKE + threadIdx.x] =
+                    threadIdx.x < 3 ? 0.f : c0[(size_t)tile * APIC_N_ZERNIKE + threadIdx.x];
             continue;
         }
         const float2* X = xdisc + (size_t)tile * P.n_bf * P.npup;
@@ -270,35 +317,34 @@ __global__ void __launch_bounds__(kThreads) k_aberration(DevPlan P, int n_tiles,
             for (int z = 0; z < 12; ++z) cf[z] = (float)cc[z];
         }
         __syncthreads();
-        for (int pass = 0; pass < passes; ++pass) {
-            for (int z = 0; z < 12; ++z) g[z] = 0.f;
-            for (int r = threadIdx.x; r < P.nrows; r += blockDim.x) {
-                const float* A = P.row_A + (size_t)r * 12;
-                float pred = 0.f;
-                for (int z = 0; z < 12; ++z) pred += A[z] * cf[z];
-                const float e = wrap_pi(beta[r] - pred);
-                for (int z = 0; z < 12; ++z) g[z] += A[z] * e;
-            }
-            reduce12(g, red, rhs);
-            if (threadIdx.x == 0) {
-                chol_solve12(P.Lval, rhs, dc);
-                for (int z = 0; z < 12; ++z) {
-                    cc[z] += dc[z];
-                    cf[z] = (float)cc[z];
-                }
+        bool won = false;
+        if (c0 && warm) {
+            const double res = value_passes(P, beta, passes, cc, cf, dc, rhs, red);
+            if (threadIdx.x < 12) {
+                cbest[threadIdx.x] = cc[threadIdx.x];
+                cc[threadIdx.x] = c0[(size_t)tile * APIC_N_ZERNIKE + 3 + threadIdx.x];
+                cf[threadIdx.x] = (float)cc[threadIdx.x];
             }
             __syncthreads();
+            const double res_w = value_passes(P, beta, passes, cc, cf, dc, rhs, red);
+            won = res_w < res;
+            if (!won && threadIdx.x < 12) cc[threadIdx.x] = cbest[threadIdx.x];
+            __syncthreads();
+        } else {
+            value_passes(P, beta, passes, cc, cf, dc, rhs, red);
         }
         if (threadIdx.x < APIC_N_ZERNIKE)
             zern[(size_t)tile * APIC_N_ZERNIKE + threadIdx.x] = threadIdx.x < 3 ? 0.f : (float)cc[threadIdx.x - 3];
+        if (won && status && threadIdx.x == 0) status[tile] |= APIC_TILE_WARM;
         __syncthreads();
     }
 }
 
 cudaError_t launch_aberration(const DevPlan& P, const Launch& L, int n_tiles, const float2* xdisc, float* zern,
-                              float* beta_scratch, int passes, const int32_t* status, cudaStream_t st) {
+                              float* beta_scratch, int passes, int32_t* status, cudaStream_t st, const float* c0,
+                              int warm) {
     const int grid = min(L.grid_ab, n_tiles);
-    k_aberration<<<grid, kThreads, 0, st>>>(P, n_tiles, xdisc, zern, beta_scratch, passes, status);
+    k_aberration<<<grid, kThreads, 0, st>>>(P, n_tiles, xdisc, zern, beta_scratch, passes, status, c0, warm);
     return cudaGetLastError();
 }
 

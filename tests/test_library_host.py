@@ -24,7 +24,7 @@ def built():
 
 def test_library_exports_every_declared_symbol():
     header = open(os.path.join(ROOT, "include", "apic.h")).read()
-    declared = set(re.findall(r"^(?:apic_status|const char\*)\s+(apic_\w+)\(", header, re.M))
+    declared = set(re.findall(r"^(?:apic_status|const char\*|size_t)\s+(apic_\w+)\(", header, re.M))
     assert declared == set(apic.EXPORTS)
     lib = apic.load()
     for name in declared:

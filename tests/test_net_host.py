@@ -1,0 +1,32 @@
+"""CPU checks of the network's parameter layout (no GPU calls)."""
+import numpy as np
+
+from oracle import cnn
+from paper_2407_20469_gb300 import apic
+
+
+def test_param_count_matches_definition():
+    p = cnn.init_params(np.random.default_rng(0))
+    assert apic.load().apic_net_param_count() == cnn.param_count(p) == 459244
+    assert apic.load().apic_net_feature_count() == 64 * 64 * 8
+
+
+def test_pack_unpack_round_trip_and_layout():
+    rng = np.random.default_rng(1)
+    p = cnn.init_params(rng)
+    for k in list(p):
+        if k.startswith("b"):
+            p[k] = rng.standard_normal(p[k].shape)
+    flat = apic.pack_params(p)
+    assert flat.dtype == np.float32 and flat.size == cnn.param_count(p)
+    q = apic.unpack_params(flat)
+    for k in p:
+        assert q[k].shape == p[k].shape
+        np.testing.assert_allclose(q[k], p[k].astype(np.float32), rtol=0, atol=0)
+    # conv 0: row co has 9 * 8 taps ordered (dy, dx, ci), then the bias
+    co, ci, dy, dx = 3, 5, 2, 1
+    assert flat[co * 73 + (dy * 3 + dx) * 8 + ci] == np.float32(p["w0"][co, ci, dy, dx])
+    assert flat[co * 73 + 72] == np.float32(p["b0"][co])
+    # last layer: 12 rows of 256 weights + bias at the end of the vector
+    assert flat[-1] == np.float32(p["b5"][11])
+    assert flat[-2] == np.float32(p["w5"][11, 255])
