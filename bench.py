@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-assisted timing")
     ap.add_argument("--seed", type=int, default=2407)
     ap.add_argument("--df-tol", type=float, default=0.0, help="CGLS tolerance (0: library default)")
     ap.add_argument("--df-iters", type=int, default=0, help="CGLS iteration cap (0: library default)")
@@ -227,6 +228,39 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
+def learned_timing(args, plan, ill, T, n, H, I, field, zern, status, device):
+    """Mpx/s of apic_reconstruct_learned (APIC_NET_WARM) with a briefly trained network."""
+    import torch
+    from paper_2407_20469_gb300 import apic, learn
+    bf = apic.Plan(n, ill.kx[:ill.n_bf], ill.ky[:ill.n_bf], ill.n_bf, max_tiles=256)
+    t0 = time.perf_counter()
+    feat, uv, zt, _ = learn.dataset(bf, 4096, args.seed, learn.field_table(), blank_frac=0.3)
+    net = apic.Net(T)
+    net.set_params(learn.init_params(args.seed))
+    hist = learn.train(net, feat, uv, zt, epochs=4, batch=64, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del feat, uv, zt
+    bf.close()
+    uv = torch.as_tensor(np.resize(learn.tile_positions(16, 32), (T, 2)), device=device)
+    for _ in range(args.warmup):
+        plan.reconstruct_learned(net, apic.APIC_NET_WARM, T, I, uv, field, zern, None, status)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.reconstruct_learned(net, apic.APIC_NET_WARM, T, I, uv, field, zern, None, status)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = status.cpu().numpy()
+    net.close()
+    return {"value": T * H * H * args.steps / (ms / 1e3) / 1e6, "unit": "Mpx/s", "mode": "APIC_NET_WARM",
+            "ms_per_step": ms / args.steps, "train_s": train_s, "train_tiles": 4096, "train_epochs": 4,
+            "final_loss": hist[-1], "warm_kept_tiles": int(np.count_nonzero(st & apic.APIC_TILE_WARM))}
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -300,6 +334,13 @@ def gpu_arm(args):
         ms = float(t.item())
     status_np = status.cpu().numpy()
 
+    # ---- learned-assisted reconstruction on the same inputs: a network trained
+    # here for a few seconds on simulated tiles, warm-starting the aberration
+    # solve (features + network forward + second refinement inside the timing)
+    learned = None
+    if not args.no_learned:
+        learned = learned_timing(args, plan, ill, T, n, H, I, field, zern, status, device)
+
     # ---- end to end through host buffers: apic_reconstruct_host pipelines the
     # pinned host->device copies, the reconstruction and the device->host copies
     e2e = None
@@ -359,6 +400,8 @@ def gpu_arm(args):
                    "tiles_status_nonzero": int(np.count_nonzero(status_np))},
         "roofline": roofline, "e2e": e2e, "gpu_launches": cnt["launches"], "clocks": clk,
     }
+    if learned is not None:
+        line["learned"] = learned
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         I1, g1, k1, ill1 = oracle_tile_sample(n, args.seed)
         res, secs = run_oracle(I1, g1, k1, ill1.n_bf)

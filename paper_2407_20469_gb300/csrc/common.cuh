@@ -68,4 +68,15 @@ __device__ __forceinline__ double block_sum2(double v, double* red, int& parity)
     return total;
 }
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit. The limit is
+// process-wide per function, so plans of different sizes that share a kernel
+// must not shrink it under one another.
+inline cudaError_t raise_smem_limit(const void* f, size_t smem) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, f);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 }  // namespace apic

@@ -494,7 +494,7 @@ DFRKernel dfr_kernel(int B, int BN) {
 int configure_dfr(int B, int BN, size_t smem) {
     DFRKernel f = dfr_kernel(B, BN);
     if (!f) return 0;
-    if (cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (raise_smem_limit((const void*)f, smem) != cudaSuccess)
         return 0;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kDFThreads, smem) != cudaSuccess) return 0;

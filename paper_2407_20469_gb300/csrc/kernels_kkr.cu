@@ -156,7 +156,7 @@ int configure_kkr(int BN, size_t smem) {
     KKRKernel f = kkr_kernel(BN);
     if (!f) return 0;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        raise_smem_limit((const void*)f, smem) != cudaSuccess)
         return 0;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kKKThreads, smem) != cudaSuccess) return 0;

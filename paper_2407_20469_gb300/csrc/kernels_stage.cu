@@ -448,7 +448,7 @@ int configure_kernel(int which, size_t smem) {
         case 5: f = (const void*)k_sim_object; break;
         default: return 0;
     }
-    if (smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (smem > 48 * 1024 && raise_smem_limit(f, smem) != cudaSuccess)
         return 0;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, smem) != cudaSuccess) return 0;

@@ -456,15 +456,15 @@ cudaError_t launch_features(const DevPlan& P, int grid, int n_tiles, const float
     cudaError_t e = cudaSuccess;
     switch (BN) {
         case 4:
-            e = cudaFuncSetAttribute(k_features<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = raise_smem_limit((const void*)k_features<4>, smem);
             if (e == cudaSuccess) k_features<4><<<grid, 512, smem, st>>>(P, n_tiles, I, feat, scratch);
             break;
         case 8:
-            e = cudaFuncSetAttribute(k_features<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = raise_smem_limit((const void*)k_features<8>, smem);
             if (e == cudaSuccess) k_features<8><<<grid, 512, smem, st>>>(P, n_tiles, I, feat, scratch);
             break;
         case 16:
-            e = cudaFuncSetAttribute(k_features<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = raise_smem_limit((const void*)k_features<16>, smem);
             if (e == cudaSuccess) k_features<16><<<grid, 512, smem, st>>>(P, n_tiles, I, feat, scratch);
             break;
         default: return cudaErrorInvalidValue;

@@ -68,6 +68,11 @@ def coefficients(table: np.ndarray, uv: np.ndarray, defocus: np.ndarray | None =
     return c.astype(np.float32)
 
 
+def tile_positions(rows: int, cols: int) -> np.ndarray:
+    """Tile-centre positions [rows * cols, 2] (u, v) of a rows x cols slide grid in [-1, 1]^2."""
+    return synth.tile_grid_uv(rows, cols)
+
+
 def draw_tiles(n: int, seed: int, table: np.ndarray, blank_frac: float = 0.0, uv: np.ndarray | None = None):
     """Positions, coefficients and background mask of n tiles (host arrays)."""
     rng = np.random.default_rng(seed)

@@ -29,12 +29,12 @@ def trained():
     table = learn.field_table()
     bf = apic.Plan(N, ill.kx[:8], ill.ky[:8], 8, max_tiles=256)
     t0 = time.perf_counter()
-    feat, uv, zern, _ = learn.dataset(bf, 4096, 11, table, blank_frac=0.3)
+    feat, uv, zern, _ = learn.dataset(bf, 8192, 11, table, blank_frac=0.3)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     net = apic.Net(256)
     net.set_params(learn.init_params(1))
-    hist = learn.train(net, feat, uv, zern, epochs=6, batch=64, lr=1e-3, log=print)
+    hist = learn.train(net, feat, uv, zern, epochs=8, batch=64, lr=3e-3, log=print)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     print(f"dataset {t1 - t0:.1f} s, training {t2 - t1:.1f} s, losses {[round(h, 5) for h in hist]}")
@@ -51,7 +51,7 @@ def test_training_converges(trained):
 def test_learned_reconstruction_beats_closed_form_on_background(trained):
     ill, table, net, _ = trained
     T = 512
-    plan = apic.Plan.from_illumination(N, ill, max_tiles=256, bg_contrast=0.02)
+    plan = apic.Plan.from_illumination(N, ill, max_tiles=T, bg_contrast=0.02)
     uv, zern, blank = learn.draw_tiles(T, 99, table, 0.3)
     I = learn.simulate(plan, zern, blank, 99)
     H = plan.info.out_h

@@ -357,3 +357,21 @@ def test_reconstruct_host_matches_device_path():
     for _ in range(2):
         plan.reconstruct_host(count, Ih, fh, zh, sh)
         assert torch.equal(fh, field.cpu()) and torch.equal(zh, z.cpu()) and torch.equal(sh, st.cpu())
+
+
+def test_plans_sharing_kernels_coexist():
+    """A later plan whose kernels need less shared memory (brightfield-only, no
+    darkfield sets) must not shrink the limits an earlier plan relies on."""
+    n = 128
+    I, _, _ = make_tiles(n, 1, seed=77)
+    big = new_plan(n, max_tiles=1)
+    ill = synth.illumination()
+    small = apic.Plan(n, ill.kx[:8], ill.ky[:8], 8, max_tiles=1)
+    H = big.info.out_h
+    field = torch.zeros((1, H, 2 * H), dtype=torch.float32, device="cuda")
+    z = torch.zeros((1, 15), dtype=torch.float32, device="cuda")
+    big.reconstruct_batch(1, dev(I), field, z)
+    torch.cuda.synchronize()
+    res = oracle_tile(I[0], n)
+    assert rel_l2(as_complex(field)[0], res.field) < FIELD_TOL
+    small.close()
