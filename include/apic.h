@@ -88,7 +88,9 @@ typedef struct {
     int upsample;                /* output upsampling factor u (2)                             */
     int max_tiles;               /* largest n_tiles of one call; larger calls are chunked     */
     int df_iters;                /* CGLS iterations per darkfield image (<= 0: 40)            */
-    float df_tol;                /* CG stop: ||C^H r|| <= df_tol ||C^H b|| (<= 0: 1e-4)       */
+    float df_tol;                /* CG stop: ||C^H r|| <= df_tol ||C^H b|| (<= 0: 3e-4, which
+                                    keeps the darkfield-only spectrum within ~6e-4 relative
+                                    L2 of the exact least-squares solution)                  */
     int ab_passes;               /* value passes of the aberration solve (< 0: 2)             */
     float bg_contrast;           /* background threshold on RMS contrast (Sec. 3.2; 0.02)     */
     int flags;                   /* APIC_SKIP_BACKGROUND                                       */

@@ -75,7 +75,7 @@ struct apic_plan {
     Launch L;
     int device = 0, sms = 0;
     int max_tiles = 0, df_iters = 40, ab_passes = 2;
-    float df_tol = 1e-4f, bg_thresh2 = 4e-4f, bg_c2 = 4e-4f;
+    float df_tol = 3e-4f, bg_thresh2 = 4e-4f, bg_c2 = 4e-4f;
     void* d_tables = nullptr;
     // workspace
     float2* xdisc = nullptr;
@@ -553,7 +553,7 @@ apic_status apic_plan_create(const apic_params* pr, apic_plan** out) {
     plan->params = *pr;
     plan->max_tiles = pr->max_tiles;
     plan->df_iters = pr->df_iters > 0 ? pr->df_iters : 40;
-    plan->df_tol = pr->df_tol > 0 ? pr->df_tol : 1e-4f;
+    plan->df_tol = pr->df_tol > 0 ? pr->df_tol : 3e-4f;
     plan->ab_passes = pr->ab_passes >= 0 ? pr->ab_passes : 2;
     const float bgc = pr->bg_contrast;
     plan->bg_c2 = bgc * bgc;

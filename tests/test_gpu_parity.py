@@ -144,7 +144,8 @@ def test_stitch_darkfield_synthesize_from_oracle_inputs():
     ref_df = res.spectrum.get(ap)
     assert np.linalg.norm(got_df - ref_df) / np.linalg.norm(ref_df) < 2e-4
     dfm = ~m
-    assert np.linalg.norm(got_df[dfm] - ref_df[dfm]) / np.linalg.norm(ref_df[dfm]) < 2e-3
+    # the darkfield-only part alone also stays within the field bar (CG stops at 3e-4)
+    assert np.linalg.norm(got_df[dfm] - ref_df[dfm]) / np.linalg.norm(ref_df[dfm]) < FIELD_TOL
     assert int(st.item()) == 0
     # final inverse transform of the checker's spectrum
     field = torch.zeros((1, g.H, 2 * g.W), dtype=torch.float32, device="cuda")
