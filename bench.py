@@ -43,7 +43,8 @@ WORKLOAD = ("512 tiles x 256x256 low-res (512x512 output), 8 NA-matching + 16 da
             "quadratic field-dependent Zernike over a 16x32 tile grid, Poisson 1e4 photons/px")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "darkfield_traffic.json")
-DF_SOURCES = ["kernels_df.cu", "passes.cuh", "fft.cuh", "common.cuh", "internal.cuh"]
+DEFAULT_DF_TOL = 3e-4          # the library's darkfield CG tolerance (apic_params.df_tol <= 0)
+DF_SOURCES = ["kernels_dfr.cu", "regfft.cuh", "common.cuh", "internal.cuh"]
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
@@ -353,6 +354,16 @@ def gpu_arm(args):
         del I
         torch.cuda.synchronize()
         plan.reconstruct_host(T, I_host, f_host, z_host, s_host)      # first call sets up the pipeline
+        # host link bandwidth for context: one pinned host->device copy of the inputs
+        probe = torch.empty(I_host.shape, dtype=torch.float32, device=device)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record()
+        probe.copy_(I_host, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        h2d_gbs = I_host.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+        del probe
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -366,7 +377,8 @@ def gpu_arm(args):
         e2e = {"value": world * T * H * H * args.e2e_steps / (ems / 1e3) / 1e6, "unit": "Mpx/s",
                "h2d_bytes_per_step": int(I_host.numel() * 4),
                "d2h_bytes_per_step": int(f_host.numel() * 4 + z_host.numel() * 4 + s_host.numel() * 4),
-               "steps": args.e2e_steps, "api": "apic_reconstruct_host (pinned host buffers)"}
+               "steps": args.e2e_steps, "api": "apic_reconstruct_host (pinned host buffers)",
+               "h2d_gbs_measured": h2d_gbs}
         del I_host, f_host, z_host, s_host
 
     # ---- roofline of the darkfield kernel (algorithmic flops / live event time)
@@ -380,9 +392,11 @@ def gpu_arm(args):
     if os.path.exists(TRAFFIC):
         with open(TRAFFIC) as fh:
             tr = json.load(fh)
-        if tr.get("source_sha") == source_sha() and tr.get("tile") == n and tr.get("tiles") == T:
+        tol = args.df_tol if args.df_tol > 0 else DEFAULT_DF_TOL
+        if (tr.get("source_sha") == source_sha() and tr.get("tile") == n and tr.get("tiles") == T
+                and abs(tr.get("df_tol", 0) - tol) < 1e-12 and not args.df_iters):
             traffic = tr.get("dram_bytes_per_launch")
-    roofline = {"bound": "alu", "kernel": "k_darkfield", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+    roofline = {"bound": "alu", "kernel": "k_darkfield_reg", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_kind": "derived FP32 CUDA-core peak (152 SMs x 128 lanes x 2 x 2.07 GHz)",
                 "launch_ms": df_ms, "cg_iterations_per_launch": iters, "solves_per_launch": solves,
