@@ -177,7 +177,7 @@ apic_status upload(apic_plan* plan) {
     std::vector<DevDF> dfs;
     std::vector<int> ux, uy, up, ua, px, py, pp, pa, qx, qy, rp;
     std::vector<unsigned> qmask;
-    int maxN = 1, maxM = 1, band_u = 1, band_q = 1;
+    int maxN = 1, maxM = 1, band_u = 1, band_p = 1, band_q = 1;
     const int mr = H.mr;
     for (const auto& d : H.df) {
         if (!d.used) continue;
@@ -224,7 +224,8 @@ apic_status upload(apic_plan* plan) {
         e.prp = push_rp(d.P_y, e.py0, e.py1);
         maxN = std::max(maxN, e.N);
         maxM = std::max(maxM, e.M);
-        band_u = std::max(band_u, std::max(e.uy1 - e.uy0 + 1, e.py1 - e.py0 + 1));
+        band_u = std::max(band_u, e.uy1 - e.uy0 + 1);
+        band_p = std::max(band_p, e.py1 - e.py0 + 1);
         band_q = std::max(band_q, e.qy1 - e.qy0 + 1);
         e.qmask_off = (int)qmask.size();
         if (mr > 0) {   // Q membership per band row on the register grid
@@ -242,6 +243,7 @@ apic_status upload(apic_plan* plan) {
     D.max_M = maxM;
     D.mr = mr;
     D.band_u = band_u;
+    D.band_p = band_p;
     D.band_q = band_q;
     if (qmask.empty()) qmask.push_back(0u);
     const size_t o_df = A.add(dfs);
@@ -330,7 +332,7 @@ apic_status configure(apic_plan* plan) {
         }
     }
     if (D.mr > 0 && !(plan->params.flags & APIC_LEGACY_KERNELS)) {
-        const size_t smem = dfr_smem_bytes(D.mr / 16, D.h / 16, std::max(D.band_q, D.band_u), D.max_N);
+        const size_t smem = dfr_smem_bytes(D.mr / 16, D.h / 16, D.band_u, D.band_q, D.max_N);
         int dev_max = 0;
         cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
         if (smem <= (size_t)dev_max) {

@@ -25,7 +25,7 @@ struct DevPlan {
     int h, w, H, W, n_bf, n_df, n_img;
     int npup, nap, nrows, m, n_used;
     int mr;                          // register-FFT correlation grid (16 B), 0 if unsupported
-    int band_u, band_q;              // largest U/P and Q row bands of the used images
+    int band_u, band_p, band_q;      // largest U, P and Q row bands of the used images
     int max_N, max_M;
     float Rx, Ry;
     int pup_ax, pup_ay;
@@ -112,7 +112,7 @@ cudaError_t launch_sim(const DevPlan& P, const Launch& L, int n_tiles, const flo
 size_t df_scratch_bytes(const DevPlan& P);
 
 // register-FFT darkfield kernel (m = 16 B, n = 16 BN)
-size_t dfr_smem_bytes(int B, int BN, int max_band, int max_N);
+size_t dfr_smem_bytes(int B, int BN, int band_u, int band_q, int max_N);
 size_t dfr_scratch_bytes(const DevPlan& P);
 int configure_dfr(int B, int BN, size_t smem);
 cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,

@@ -13,10 +13,13 @@
 //     R3 rows of U: forward along x, gather w on U, <d, w>
 //   then x += alpha d, s -= alpha w, and d = s + beta d (folded into the next
 //   R1). Transforms FP32; inner products, step lengths and the solution FP64.
-// GU / GQ are band-row grids (only rows holding U, P or Q points) and the known
-// field p is stored column-major, all in the block's scratch (L2-resident).
-// One block per tile (persistent); images of a tile are sequential. Each pass
-// is a separate (non-inlined) function so registers are allocated per pass.
+// GU / GQ are band-row grids (only rows holding U or Q points). GU lives in
+// shared memory (row stride m + 1, so the column passes are conflict free); GQ,
+// the column-major known field p, b on Q and the FP64 solution live in the
+// block's global scratch (L2-resident). The setup transforms of each image
+// reuse the shared-memory space of GU. One block per tile (persistent); images
+// of a tile are sequential. Each pass is a separate (non-inlined) function so
+// registers are allocated per pass.
 #include <math.h>
 
 #include <algorithm>
@@ -118,9 +121,9 @@ struct MidTimesField {  // o *= p / m^2 or conj(p) / m^2 (p loaded by the caller
 
 // ---- passes
 
-// rows of a band: scatter val(e) at x = px[e], inverse transform along x, store rows of G
+// rows of a band: scatter val(e) at x = px[e], inverse transform along x, store rows of G (row stride ld)
 template <int B, class Val>
-__device__ __noinline__ void pass_rows_in(HW w, const float2* tw, float2* G, int nrows, const int* rp,
+__device__ __noinline__ void pass_rows_in(HW w, const float2* tw, float2* G, int ld, int nrows, const int* rp,
                                           const int* px, Val val) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
@@ -136,7 +139,7 @@ __device__ __noinline__ void pass_rows_in(HW w, const float2* tw, float2* G, int
         __syncwarp(w.mask);
         fft_alpha<B, true>(v, o, h, tw);
         if (w.t < B) {
-            float2* row = G + (size_t)b * m;
+            float2* row = G + (size_t)b * ld;
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) row[w.t + B * k1] = o[k1];
         }
@@ -145,13 +148,13 @@ __device__ __noinline__ void pass_rows_in(HW w, const float2* tw, float2* G, int
 
 // rows of a band of G: forward transform along x; returns sum of out(e, value) over this lane's points
 template <int B, class Out>
-__device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float2* G, int nrows, const int* rp,
-                                             const int* px, Out out) {
+__device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float2* G, int ld, int nrows,
+                                             const int* rp, const int* px, Out out) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
     double acc = 0.0;
     for (int b = w.hw; b < nrows; b += kHW) {
-        const float2* row = G + (size_t)b * m;
+        const float2* row = G + (size_t)b * ld;
         float2 v[B], o[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
@@ -167,13 +170,14 @@ __device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float
     return acc;
 }
 
-// columns: rows yi0.. (ni of them) of Gi are the input, the rest zero; inverse along
-// y, mid, forward along y; rows yo0.. (no) stored to Go. Each half-warp reads and
-// writes its own columns straight from the (L2-resident) grids; the known-field
-// values of the column are loaded up front with the inputs. Ends with __syncthreads.
+// columns: rows yi0.. (ni of them) of Gi (row stride ldi) are the input, the rest
+// zero; inverse along y, mid, forward along y; rows yo0.. (no) stored to Go (row
+// stride ldo). Each half-warp reads and writes its own columns, so Gi and Go may
+// be the same grid; the known-field values of the column are loaded up front
+// with the inputs. Ends with __syncthreads.
 template <int B, class Mid>
-__device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi, int yi0, int ni, float2* Go,
-                                       int yo0, int no, Mid mid) {
+__device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi, int ldi, int yi0, int ni,
+                                       float2* Go, int ldo, int yo0, int no, Mid mid) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
     for (int x = w.hw; x < m; x += kHW) {
@@ -187,7 +191,7 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi,
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             const int bb = sfreq(w.t + 16 * j, m) - yi0;
-            v[j] = (bb >= 0 && bb < ni) ? Gi[(size_t)bb * m + x] : make_float2(0.f, 0.f);
+            v[j] = (bb >= 0 && bb < ni) ? Gi[(size_t)bb * ldi + x] : make_float2(0.f, 0.f);
         }
         fft_alpha<B, true>(v, o, h, tw);
         if (w.t < B) mid(o, x, w.t, pf);
@@ -195,7 +199,7 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi,
 #pragma unroll
         for (int k1 = 0; k1 < B; ++k1) {
             const int bb = sfreq(w.t + 16 * k1, m) - yo0;
-            if (bb >= 0 && bb < no) Go[(size_t)bb * m + x] = v[k1];
+            if (bb >= 0 && bb < no) Go[(size_t)bb * ldo + x] = v[k1];
         }
     }
     __syncthreads();
@@ -332,29 +336,49 @@ __device__ __noinline__ void pass_rows_rhs(HW w, const float2* tw, float2* GQ, i
 
 }  // namespace
 
-template <int B, int BN>
-struct DFLayout {
-    static constexpr int hws = HWSize<B>::value > HWSize<BN>::value ? HWSize<B>::value : HWSize<BN>::value;
+// Shared memory of one block (bytes, 16-aligned offsets):
+//   [0, gu)        half-warp areas of the m-grid passes
+//   [gu, c)        GU, band_u rows of m + 1 complex values
+//   [0, c)         during the setup transforms of an image: half-warp areas of
+//                  the n-grid passes, then the column stage (aliases the above)
+//   [c, total)     CG vectors d, s, w; step twiddles of m and n; reduction slots
+struct DFRSmem {
+    size_t gu, stage, c, total;
 };
 
-size_t dfr_smem_bytes(int B, int BN, int max_band, int max_N) {
-    const int hws = std::max(std::max(17 * B, 16 * (B + 1)), std::max(17 * BN, 16 * (BN + 1)));
-    size_t b = ((size_t)kHW * hws * sizeof(float2) + 15) & ~(size_t)15;   // half-warp areas
-    const size_t stage_c = (size_t)max_band * kStageLd * sizeof(float2);
-    const size_t stage_f = (size_t)(16 * BN) * kStageLd * sizeof(float);
-    b += (std::max(stage_c, stage_f) + 15) & ~(size_t)15;                  // column stage
-    b += (size_t)max_N * (sizeof(double2) + 3 * sizeof(float2));           // x, d, s, w
-    b += (size_t)2 * (16 * B + 16 * BN) * sizeof(float2);                   // step twiddles
-    b += 64 * sizeof(double);
-    return (b + 15) & ~(size_t)15;
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ inline DFRSmem dfr_smem_layout(int B, int BN, int band_u, int band_q, int max_N) {
+    const int m = 16 * B, n = 16 * BN;
+    const int hws_m = 17 * B > 16 * (B + 1) ? 17 * B : 16 * (B + 1);
+    const int hws_n = 17 * BN > 16 * (BN + 1) ? 17 * BN : 16 * (BN + 1);
+    DFRSmem L;
+    L.gu = align16((size_t)kHW * hws_m * sizeof(float2));
+    const size_t gu_end = L.gu + align16((size_t)band_u * (m + 1) * sizeof(float2));
+    L.stage = align16((size_t)kHW * hws_n * sizeof(float2));
+    const size_t stage_c = (size_t)band_q * kStageLd * sizeof(float2);
+    const size_t stage_f = (size_t)n * kStageLd * sizeof(float);
+    const size_t stage_end = L.stage + align16(stage_c > stage_f ? stage_c : stage_f);
+    L.c = gu_end > stage_end ? gu_end : stage_end;
+    size_t t = L.c + (size_t)3 * max_N * sizeof(float2);                   // d, s, w
+    t += (size_t)2 * (m + n) * sizeof(float2);                            // step twiddles
+    t = align16(t) + 64 * sizeof(double);                                 // reductions
+    L.total = align16(t);
+    return L;
 }
 
+size_t dfr_smem_bytes(int B, int BN, int band_u, int band_q, int max_N) {
+    return dfr_smem_layout(B, BN, band_u, band_q, max_N).total;
+}
+
+// Global scratch of one block: FP64 solution x, GQ (Q or P band rows), the
+// known field / image rows, b on Q.
 size_t dfr_scratch_bytes(const DevPlan& P) {
     const int m = P.mr, n = P.h;
-    size_t s = (size_t)P.band_u * m * sizeof(float2);                        // GU
-    s += (size_t)P.band_q * m * sizeof(float2);                              // GQ
-    s += std::max((size_t)m * m, (size_t)P.band_q * n) * sizeof(float2);     // PF / F(I) rows
-    s += (size_t)P.max_M * sizeof(float2);                                   // b on Q
+    size_t s = (size_t)P.max_N * sizeof(double2);                                  // x
+    s += (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m * sizeof(float2);  // GQ
+    s += std::max((size_t)m * m, (size_t)P.band_q * n) * sizeof(float2);           // PF / F(I) rows
+    s += (size_t)P.max_M * sizeof(float2);                                         // b on Q
     return (s + 255) & ~(size_t)255;
 }
 
@@ -363,38 +387,36 @@ __global__ void __launch_bounds__(kDFThreads, 1)
 k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
                 float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
                 int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
-    constexpr int m = 16 * B, n = 16 * BN, HWS = DFLayout<B, BN>::hws;
+    constexpr int m = 16 * B, n = 16 * BN, LDU = m + 1;
+    constexpr int HWM = HWSize<B>::value, HWN = HWSize<BN>::value;
     extern __shared__ float4 smem4[];
-    char* sp_ = reinterpret_cast<char*>(smem4);
-    float2* hw_area = reinterpret_cast<float2*>(sp_);
-    sp_ += ((size_t)kHW * HWS * sizeof(float2) + 15) & ~(size_t)15;
-    const size_t bytes_c = (size_t)(P.band_q > P.band_u ? P.band_q : P.band_u) * kStageLd * sizeof(float2);
-    const size_t bytes_f = (size_t)n * kStageLd * sizeof(float);
-    float2* stage = reinterpret_cast<float2*>(sp_);
-    sp_ += ((bytes_c > bytes_f ? bytes_c : bytes_f) + 15) & ~(size_t)15;
-    double2* xv = reinterpret_cast<double2*>(sp_);
-    sp_ += (size_t)P.max_N * sizeof(double2);
-    float2* dv = reinterpret_cast<float2*>(sp_);
+    char* sbase = reinterpret_cast<char*>(smem4);
+    const DFRSmem SL = dfr_smem_layout(B, BN, P.band_u, P.band_q, P.max_N);
+    float2* GU = reinterpret_cast<float2*>(sbase + SL.gu);
+    float2* stage = reinterpret_cast<float2*>(sbase + SL.stage);
+    float2* dv = reinterpret_cast<float2*>(sbase + SL.c);
     float2* sv = dv + P.max_N;
     float2* wv = sv + P.max_N;
     float2* tw_m = wv + P.max_N;
     float2* tw_n = tw_m + 2 * m;
-    double* red = reinterpret_cast<double*>(tw_n + 2 * n);
+    double* red = reinterpret_cast<double*>(sbase + align16(SL.c + (size_t)3 * P.max_N * sizeof(float2) +
+                                                            (size_t)2 * (m + n) * sizeof(float2)));
 
     make_step_twiddles(tw_m, P.tw_r, B);
     make_step_twiddles(tw_n, P.tw_n, BN);
     __syncthreads();
 
-    HW w;
-    w.hw = threadIdx.x >> 4;
-    w.t = threadIdx.x & 15;
-    w.mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
-    w.hs = hw_area + w.hw * HWS;
+    HW w, wn;                        // m-grid passes / image (n-grid) setup passes
+    w.hw = wn.hw = threadIdx.x >> 4;
+    w.t = wn.t = threadIdx.x & 15;
+    w.mask = wn.mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
+    w.hs = reinterpret_cast<float2*>(sbase) + w.hw * HWM;
+    wn.hs = reinterpret_cast<float2*>(sbase) + w.hw * HWN;
 
     char* base = scratch + (size_t)blockIdx.x * per_block;
-    float2* GU = reinterpret_cast<float2*>(base);
-    float2* GQ = GU + (size_t)P.band_u * m;
-    float2* PF = GQ + (size_t)P.band_q * m;          // column-major known field, or F(I) rows
+    double2* xv = reinterpret_cast<double2*>(base);
+    float2* GQ = reinterpret_cast<float2*>(xv + P.max_N);
+    float2* PF = GQ + (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m;   // column-major p, or F(I) rows
     float2* bq = PF + (size_t)max(m * m, P.band_q * n);
     const float inv_m2 = 1.f / (float)(m * m);
 
@@ -412,18 +434,19 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             const unsigned* qmask = P.d_qmask + D.qmask_off;
             const float* img = I + ((size_t)tile * P.n_img + D.led) * n * n;
 
-            // b = F(I_j) on Q
-            pass_image_cols<BN>(w, tw_n, stage, img, PF, qy0, nQ);
-            pass_image_rows<BN>(w, tw_n, PF, nQ, qrp, P.dQ_x + q_off, bq);
-            // known field p (column-major in PF), b -= P*P, rows of b inverse along x
-            pass_rows_in<B>(w, tw_m, GU, nP, prp, P.dP_x + p_off,
+            // b = F(I_j) on Q (setup transforms in the shared space of GU)
+            pass_image_cols<BN>(wn, tw_n, stage, img, PF, qy0, nQ);
+            pass_image_rows<BN>(wn, tw_n, PF, nQ, qrp, P.dQ_x + q_off, bq);
+            // known field p (column-major in PF; its band rows staged in GQ), b -= P*P,
+            // rows of b inverse along x
+            pass_rows_in<B>(w, tw_m, GQ, m, nP, prp, P.dP_x + p_off,
                             ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
             __syncthreads();
-            pass_cols<B>(w, tw_m, GU, py0, nP, GQ, qy0, nQ, MidKnownField<B>{PF});
+            pass_cols<B>(w, tw_m, GQ, m, py0, nP, GQ, m, qy0, nQ, MidKnownField<B>{PF});
             pass_rows_rhs<B>(w, tw_m, GQ, nQ, qrp, P.dQ_x + q_off, bq);
             // s = d = C^H b
-            pass_cols<B>(w, tw_m, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
-            const double g0 = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutStart{sv, dv, xv});
+            pass_cols<B>(w, tw_m, GQ, m, qy0, nQ, GU, LDU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
+            const double g0 = pass_rows_out<B>(w, tw_m, GU, LDU, nU, urp, P.dU_x + u_off, OutStart{sv, dv, xv});
             int par = 0;
             const double gamma0 = block_sum2(g0, red, par);
 
@@ -434,12 +457,12 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             int it = 0;
             float bf = 0.f;                  // first direction: d = s
             for (; it < iters && !conv; ++it) {
-                pass_rows_in<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, ValNextDir{sv, dv, bf});
+                pass_rows_in<B>(w, tw_m, GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{sv, dv, bf});
                 __syncthreads();
-                pass_cols<B>(w, tw_m, GU, uy0, nU, GQ, qy0, nQ, MidTimesField<B, true>{PF, inv_m2});
+                pass_cols<B>(w, tw_m, GU, LDU, uy0, nU, GQ, m, qy0, nQ, MidTimesField<B, true>{PF, inv_m2});
                 pass_rows_mask<B>(w, tw_m, GQ, nQ, qmask);
-                pass_cols<B>(w, tw_m, GQ, qy0, nQ, GU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
-                const double dw = pass_rows_out<B>(w, tw_m, GU, nU, urp, P.dU_x + u_off, OutDot{wv, dv});
+                pass_cols<B>(w, tw_m, GQ, m, qy0, nQ, GU, LDU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
+                const double dw = pass_rows_out<B>(w, tw_m, GU, LDU, nU, urp, P.dU_x + u_off, OutDot{wv, dv});
                 const double delta = block_sum2(dw, red, par);
                 if (!(delta > 0)) break;
                 const double alpha = gamma / delta;
