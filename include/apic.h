@@ -302,6 +302,39 @@ apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* d_object,
                           float* d_intensity, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Whole-slide tiling. The paper reconstructs a slide patch by patch
+ * (Sec. 2.3, 3.2). No tile is ragged here: windows of the plan's tile size step
+ * by `stride` (1..tile) over a slide_h x slide_w camera image, and the last
+ * window of each row and column moves inward to end at the slide edge, so one
+ * plan serves the whole slide. Consecutive windows split their overlap at its
+ * middle: window k owns the slide pixels [oy0, oy1) x [ox0, ox1), and the owned
+ * rectangles cover the slide exactly once.
+ * Window records: int32 [6] = y0, x0, oy0, ox0, oy1, ox1 (slide pixels).
+ * ------------------------------------------------------------------------ */
+
+/* Windows in row-major order into h_windows [capacity][6] (host memory);
+ * *n_windows receives their number (h_windows NULL: count only). Host only.
+ * Errors: APIC_EINVAL (slide smaller than a tile, stride outside [1, tile],
+ * capacity below the count). */
+apic_status apic_slide_windows(int slide_h, int slide_w, int tile, int stride, int32_t* h_windows,
+                               int capacity, int* n_windows);
+
+/* Cut d_windows [n_tiles][6] (device) out of d_slide [n_img][slide_h][slide_w]
+ * float32 into d_intensity [n_tiles][n_img][h][w] (the batch layout). A window
+ * that leaves the slide gives a NaN stack, which the reconstruction flags
+ * APIC_TILE_BADINPUT. */
+apic_status apic_cut_tiles(apic_plan* plan, int n_tiles, const float* d_slide, int slide_h, int slide_w,
+                           const int32_t* d_windows, float* d_intensity, void* stream);
+
+/* Write the owned part of each tile's field d_field [n_tiles][u h][u w]
+ * complex64 into d_slide_field [u slide_h][u slide_w] complex64; other pixels
+ * are left untouched. Each tile keeps its own global phase (the paper's
+ * cross-tile registration, Sec. 2.5, is not part of this library). */
+apic_status apic_paste_fields(apic_plan* plan, int n_tiles, const float* d_field,
+                              const int32_t* d_windows, int slide_h, int slide_w,
+                              float* d_slide_field, void* stream);
+
+/* ------------------------------------------------------------------------
  * Learned aberration network. The paper has no counterpart: its aberration
  * estimate is the closed-form solve of Eq. 10 alone. This small CNN predicts
  * the field-dependent Noll coefficients 4..15 of a tile from the magnitudes of

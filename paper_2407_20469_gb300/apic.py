@@ -34,6 +34,7 @@ EXPORTS = [
     "apic_pupil", "apic_simulate", "apic_net_param_count", "apic_net_feature_count", "apic_net_create",
     "apic_net_destroy", "apic_net_set_params", "apic_net_get_params", "apic_net_get_grads", "apic_net_forward",
     "apic_net_backward", "apic_net_adamw", "apic_net_activation", "apic_features", "apic_reconstruct_learned",
+    "apic_slide_windows", "apic_cut_tiles", "apic_paste_fields",
 ]
 
 
@@ -103,6 +104,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_net_activation": (i32, [vp, i32, C.POINTER(C.c_float), sz]),
         "apic_features": (i32, [vp, i32, vp, vp, vp]),
         "apic_reconstruct_learned": (i32, [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "apic_slide_windows": (i32, [i32, i32, i32, i32, C.POINTER(C.c_int32), i32, C.POINTER(C.c_int)]),
+        "apic_cut_tiles": (i32, [vp, i32, vp, i32, i32, vp, vp, vp]),
+        "apic_paste_fields": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -140,6 +144,17 @@ def _stream(stream) -> int | None:
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def slide_windows(slide_h: int, slide_w: int, tile: int, stride: int) -> np.ndarray:
+    """Windows [n, 6] int32 (y0, x0, oy0, ox0, oy1, ox1) covering a slide (apic_slide_windows)."""
+    lib = load()
+    n = C.c_int(0)
+    _check(lib.apic_slide_windows(slide_h, slide_w, tile, stride, None, 0, C.byref(n)), "apic_slide_windows")
+    out = np.zeros((n.value, 6), dtype=np.int32)
+    _check(lib.apic_slide_windows(slide_h, slide_w, tile, stride, out.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  n.value, C.byref(n)), "apic_slide_windows")
+    return out
 
 
 class Plan:
@@ -268,6 +283,14 @@ class Plan:
     def simulate(self, n_tiles, obj, zernike, photons, seed, intensity, stream=None):
         _check(load().apic_simulate(self.handle, n_tiles, _ptr(obj), _ptr(zernike), float(photons), int(seed),
                                     _ptr(intensity), _stream(stream)), "apic_simulate")
+
+    def cut_tiles(self, n_tiles, slide, slide_h, slide_w, windows, intensity, stream=None):
+        _check(load().apic_cut_tiles(self.handle, n_tiles, _ptr(slide), slide_h, slide_w, _ptr(windows),
+                                     _ptr(intensity), _stream(stream)), "apic_cut_tiles")
+
+    def paste_fields(self, n_tiles, field, windows, slide_h, slide_w, slide_field, stream=None):
+        _check(load().apic_paste_fields(self.handle, n_tiles, _ptr(field), _ptr(windows), slide_h, slide_w,
+                                        _ptr(slide_field), _stream(stream)), "apic_paste_fields")
 
     def features(self, n_tiles, intensity, feat, stream=None):
         """Network input features [n_tiles][64][64][8] of the first 8 images of each stack."""

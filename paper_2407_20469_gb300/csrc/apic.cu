@@ -943,6 +943,29 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
     return APIC_OK;
 }
 
+apic_status apic_cut_tiles(apic_plan* plan, int n_tiles, const float* slide, int slide_h, int slide_w,
+                           const int32_t* windows, float* I, void* stream) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!slide || !windows || !I) return fail(APIC_EINVAL, "NULL slide, windows or output");
+    if (slide_h < plan->dev.h || slide_w < plan->dev.w) return fail(APIC_EINVAL, "slide smaller than a tile");
+    if (n_tiles == 0) return APIC_OK;
+    APIC_TRY_LAUNCH(launch_cut_tiles(plan->dev, n_tiles, slide, slide_h, slide_w, windows, I, (cudaStream_t)stream));
+    return APIC_OK;
+}
+
+apic_status apic_paste_fields(apic_plan* plan, int n_tiles, const float* field, const int32_t* windows, int slide_h,
+                              int slide_w, float* slide_field, void* stream) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!field || !windows || !slide_field) return fail(APIC_EINVAL, "NULL field, windows or output");
+    if (slide_h < plan->dev.h || slide_w < plan->dev.w) return fail(APIC_EINVAL, "slide smaller than a tile");
+    if (n_tiles == 0) return APIC_OK;
+    APIC_TRY_LAUNCH(launch_paste_fields(plan->dev, n_tiles, (const float2*)field, windows, slide_h, slide_w,
+                                        (float2*)slide_field, (cudaStream_t)stream));
+    return APIC_OK;
+}
+
 apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* obj, const float* zern, float photons,
                           uint64_t seed, float* I, void* stream) {
     apic_status s = check_plan(plan, n_tiles);

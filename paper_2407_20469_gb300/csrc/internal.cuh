@@ -129,6 +129,11 @@ cudaError_t net_predict(struct ::apic_net* n, int B, const float* feat, const fl
                         cudaStream_t st);
 int net_max_batch(const struct ::apic_net* n);
 long long net_launches(const struct ::apic_net* n);
+// Whole-slide tiling (kernels_slide.cu): windows [tiles][6] = y0, x0, oy0, ox0, oy1, ox1.
+cudaError_t launch_cut_tiles(const DevPlan& P, int n_tiles, const float* slide, int Hs, int Ws, const int32_t* win,
+                             float* out, cudaStream_t st);
+cudaError_t launch_paste_fields(const DevPlan& P, int n_tiles, const float2* field, const int32_t* win, int Hs,
+                                int Ws, float2* slide, cudaStream_t st);
 // Records the message returned by apic_last_error (apic.cu).
 int record_error(int status, const char* msg);
 

@@ -1,0 +1,82 @@
+"""Whole-slide tiling on the GPU: cutting and pasting are exact copies, and a
+slide laid out from independently simulated tiles reconstructs exactly as the
+tiles do in one batch, through uneven batches."""
+import numpy as np
+import pytest
+
+from paper_2407_20469_gb300 import apic, learn, slide, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def plan():
+    from paper_2407_20469_gb300 import build
+    build.build()
+    return apic.Plan.from_illumination(64, synth.illumination(), max_tiles=8)
+
+
+def test_cut_tiles_is_exact_and_rejects_windows_outside(plan):
+    rng = np.random.default_rng(3)
+    Hs, Ws, n_img = 150, 211, 24
+    s = rng.random((n_img, Hs, Ws), dtype=np.float32)
+    win = apic.slide_windows(Hs, Ws, 64, 48)
+    bad = win[:1].copy()
+    bad[0, 1] = Ws - 63                                   # one column beyond the slide
+    allw = np.concatenate([win, bad])
+    out = torch.empty((len(allw), n_img, 64, 64), dtype=torch.float32, device="cuda")
+    plan.cut_tiles(len(allw), torch.as_tensor(s, device="cuda"), Hs, Ws, torch.as_tensor(allw, device="cuda"), out)
+    got = out.cpu().numpy()
+    for k, r in enumerate(win):
+        assert np.array_equal(got[k], s[:, r[0]:r[0] + 64, r[1]:r[1] + 64])
+    assert np.all(np.isnan(got[-1]))
+
+
+def test_paste_fields_writes_owned_parts_exactly(plan):
+    rng = np.random.default_rng(4)
+    Hs, Ws = 150, 211
+    win = apic.slide_windows(Hs, Ws, 64, 40)
+    f = rng.standard_normal((len(win), 128, 256)).astype(np.float32)
+    out = torch.full((2 * Hs, 4 * Ws), 7.0, dtype=torch.float32, device="cuda")
+    plan.paste_fields(len(win), torch.as_tensor(f, device="cuda"), torch.as_tensor(win, device="cuda"), Hs, Ws, out)
+    exp = np.full((2 * Hs, 4 * Ws), 7.0, dtype=np.float32)
+    for k, (y0, x0, oy0, ox0, oy1, ox1) in enumerate(win):
+        tile = f[k].reshape(128, 128, 2)
+        exp.reshape(2 * Hs, 2 * Ws, 2)[2 * oy0:2 * oy1, 2 * ox0:2 * ox1] = \
+            tile[2 * (oy0 - y0):2 * (oy1 - y0), 2 * (ox0 - x0):2 * (ox1 - x0)]
+    got = out.cpu().numpy()
+    assert np.array_equal(got, exp)                       # owned parts cover everything once
+
+
+def test_slide_of_tiles_matches_the_batch(plan):
+    rows, cols, n = 2, 3, 64
+    uv, zern, blank = learn.draw_tiles(rows * cols, 8, learn.field_table())
+    I = learn.simulate(plan, zern, blank, 8)                         # [6, 24, 64, 64]
+    s = I.reshape(rows, cols, 24, n, n).permute(2, 0, 3, 1, 4).reshape(24, rows * n, cols * n).contiguous()
+    out, z, st, win = slide.reconstruct_slide(plan, s, rows * n, cols * n, stride=n, batch=4)
+    H = plan.info.out_h
+    f_ref = torch.empty((rows * cols, H, 2 * H), dtype=torch.float32, device="cuda")
+    z_ref = torch.empty((rows * cols, 15), dtype=torch.float32, device="cuda")
+    plan.reconstruct_batch(rows * cols, I, f_ref, z_ref)
+    torch.cuda.synchronize()
+    assert np.array_equal(win[:, :2], np.array([[r * n, c * n] for r in range(rows) for c in range(cols)]))
+    assert np.all(st.cpu().numpy() == 0)
+    assert torch.equal(z, z_ref)
+    exp = f_ref.reshape(rows, cols, H, H, 2).permute(0, 2, 1, 3, 4).reshape(rows * H, cols * H * 2)
+    assert torch.equal(out, exp)
+
+
+def test_ragged_slide_through_the_learned_path(plan):
+    rng = np.random.default_rng(5)
+    Hs, Ws = 100, 150                                      # not multiples of the tile
+    s = torch.as_tensor(rng.random((24, Hs, Ws), dtype=np.float32) + 0.5, device="cuda")
+    net = apic.Net(8)
+    net.set_params(learn.init_params(2))
+    out, z, st, win = slide.reconstruct_slide(plan, s, Hs, Ws, stride=56, batch=3, net=net,
+                                              mode=apic.APIC_NET_WARM | apic.APIC_NET_REPLACE)
+    torch.cuda.synchronize()
+    assert len(win) == 6                                   # 2 x 3 windows, the last of each axis moved inward
+    assert torch.isfinite(out).all() and torch.isfinite(z).all()
+    assert not np.any(st.cpu().numpy() & apic.APIC_TILE_BADINPUT)
