@@ -301,6 +301,21 @@ apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* d_object,
                           const float* d_zernike, float photons, uint64_t seed,
                           float* d_intensity, void* stream);
 
+/*
+ * Autotuner (the paper has no counterpart). Times, on the caller's sample
+ * d_intensity [n_tiles][n_img][h][w] (1 <= n_tiles <= max_tiles; a full wave
+ * of the darkfield grid, e.g. one tile per SM, gives representative numbers),
+ * the register-FFT and the shared-memory Stockham variants of the
+ * Kramers-Kronig and darkfield stages (best of two runs after a warm-up, CUDA
+ * events) and keeps the faster variant of each for the plan's later calls.
+ * h_ms [n_ms] (may be NULL): milliseconds of KK register, KK Stockham,
+ * darkfield register, darkfield Stockham (-1 where a variant does not apply).
+ * Synchronous; uses the plan's workspace, so it must not overlap other calls
+ * on the plan.
+ */
+apic_status apic_plan_autotune(apic_plan* plan, int n_tiles, const float* d_intensity, double* h_ms,
+                               int n_ms);
+
 /* ------------------------------------------------------------------------
  * Whole-slide tiling. The paper reconstructs a slide patch by patch
  * (Sec. 2.3, 3.2). No tile is ragged here: windows of the plan's tile size step

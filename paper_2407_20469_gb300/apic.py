@@ -34,7 +34,7 @@ EXPORTS = [
     "apic_pupil", "apic_simulate", "apic_net_param_count", "apic_net_feature_count", "apic_net_create",
     "apic_net_destroy", "apic_net_set_params", "apic_net_get_params", "apic_net_get_grads", "apic_net_forward",
     "apic_net_backward", "apic_net_adamw", "apic_net_activation", "apic_features", "apic_reconstruct_learned",
-    "apic_slide_windows", "apic_cut_tiles", "apic_paste_fields",
+    "apic_slide_windows", "apic_cut_tiles", "apic_paste_fields", "apic_plan_autotune",
 ]
 
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_net_activation": (i32, [vp, i32, C.POINTER(C.c_float), sz]),
         "apic_features": (i32, [vp, i32, vp, vp, vp]),
         "apic_reconstruct_learned": (i32, [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "apic_plan_autotune": (i32, [vp, i32, vp, C.POINTER(C.c_double), i32]),
         "apic_slide_windows": (i32, [i32, i32, i32, i32, C.POINTER(C.c_int32), i32, C.POINTER(C.c_int)]),
         "apic_cut_tiles": (i32, [vp, i32, vp, i32, i32, vp, vp, vp]),
         "apic_paste_fields": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
@@ -283,6 +284,14 @@ class Plan:
     def simulate(self, n_tiles, obj, zernike, photons, seed, intensity, stream=None):
         _check(load().apic_simulate(self.handle, n_tiles, _ptr(obj), _ptr(zernike), float(photons), int(seed),
                                     _ptr(intensity), _stream(stream)), "apic_simulate")
+
+    def autotune(self, n_tiles, intensity) -> dict:
+        """Times the register and Stockham variants of the transform stages on a sample; keeps the faster."""
+        ms = np.full(4, -1.0)
+        _check(load().apic_plan_autotune(self.handle, n_tiles, _ptr(intensity),
+                                         ms.ctypes.data_as(C.POINTER(C.c_double)), 4), "apic_plan_autotune")
+        return {"kk_register": ms[0], "kk_stockham": ms[1], "darkfield_register": ms[2],
+                "darkfield_stockham": ms[3]}
 
     def cut_tiles(self, n_tiles, slide, slide_h, slide_w, windows, intensity, stream=None):
         _check(load().apic_cut_tiles(self.handle, n_tiles, _ptr(slide), slide_h, slide_w, _ptr(windows),

@@ -106,6 +106,7 @@ struct apic_plan {
         float* d_zern[2] = {};
         int32_t* d_status[2] = {};
     } io;
+    bool kkr_ok = false, dfr_ok = false;   // register kernels available for this geometry
     bool use_kkr = false;        // register-FFT Kramers-Kronig kernel
     size_t smem_kkr = 0;
     int grid_kkr = 0;
@@ -318,27 +319,28 @@ apic_status configure(apic_plan* plan) {
         return fail(APIC_ECUDA, "kernel configuration (shared memory / occupancy) failed");
     }
     const int sms = plan->sms;
-    plan->use_reg = false;
-    plan->use_kkr = false;
-    if (D.h == D.w && (D.h == 64 || D.h == 128 || D.h == 256) && !(plan->params.flags & APIC_LEGACY_KERNELS)) {
+    // register-FFT kernels where the sizes allow them (the default), the
+    // shared-memory Stockham kernels otherwise or when asked for
+    plan->kkr_ok = plan->dfr_ok = false;
+    if (D.h == D.w && (D.h == 64 || D.h == 128 || D.h == 256)) {
         const size_t smem = kkr_smem_bytes(D.h / 16);
         const int occ = configure_kkr(D.h / 16, smem);
         if (occ > 0) {
-            plan->use_kkr = true;
+            plan->kkr_ok = true;
             plan->smem_kkr = smem;
             plan->grid_kkr = sms * occ;
         } else {
             cudaGetLastError();
         }
     }
-    if (D.mr > 0 && !(plan->params.flags & APIC_LEGACY_KERNELS)) {
+    if (D.mr > 0) {
         const size_t smem = dfr_smem_bytes(D.mr / 16, D.h / 16, D.band_u, D.band_q, D.max_N);
         int dev_max = 0;
         cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
         if (smem <= (size_t)dev_max) {
             const int occ = configure_dfr(D.mr / 16, D.h / 16, smem);
             if (occ > 0) {
-                plan->use_reg = true;
+                plan->dfr_ok = true;
                 plan->smem_dfr = smem;
                 plan->grid_dfr = sms * occ;
             } else {
@@ -346,6 +348,9 @@ apic_status configure(apic_plan* plan) {
             }
         }
     }
+    const bool legacy = (plan->params.flags & APIC_LEGACY_KERNELS) != 0;
+    plan->use_kkr = plan->kkr_ok && !legacy;
+    plan->use_reg = plan->dfr_ok && !legacy;
     L.grid_kk = sms * o_kk;
     L.grid_ab = sms * std::min(o_ab, 2);
     L.grid_df = sms * std::min(o_df, 2);
@@ -446,7 +451,7 @@ struct StageTimer {
 // allocated on the first learned call.
 apic_status learned_buffers(apic_plan* p) {
     if (p->feat) return APIC_OK;
-    if (!p->use_kkr) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (!p->kkr_ok) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
     if (p->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
     apic_status s;
     if ((s = dmalloc(p, (void**)&p->feat, (size_t)p->max_tiles * feature_floats() * sizeof(float))) != APIC_OK)
@@ -869,7 +874,7 @@ apic_status apic_features(apic_plan* plan, int n_tiles, const float* I, float* f
     apic_status s = check_stage(plan, n_tiles);
     if (s != APIC_OK) return s;
     if (!I || !feat) return fail(APIC_EINVAL, "NULL intensity or features");
-    if (!plan->use_kkr) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (!plan->kkr_ok) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
     if (plan->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
     if (n_tiles == 0) return APIC_OK;
     APIC_TRY_LAUNCH(launch_features(plan->dev, plan->grid_kkr, n_tiles, I, feat, plan->kk_scratch,
@@ -940,6 +945,91 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
     }
     APIC_TRY_CUDA(cudaStreamSynchronize(io.s_out));
     APIC_TRY_CUDA(cudaStreamSynchronize(io.s_comp));
+    return APIC_OK;
+}
+
+apic_status apic_plan_autotune(apic_plan* plan, int n_tiles, const float* I, double* h_ms, int n_ms) {
+    apic_status s = check_stage(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!I || n_tiles < 1) return fail(APIC_EINVAL, "autotuning needs at least one sample tile");
+    APIC_TRY_CUDA(cudaDeviceSynchronize());
+    cudaStream_t st = nullptr;
+    APIC_TRY_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double ms[4] = {-1.0, -1.0, -1.0, -1.0};   // KK register / Stockham, darkfield register / Stockham
+    const DevPlan& D = plan->dev;
+    int32_t* stt = plan->status;
+    auto timed = [&](auto&& launch, double& out) -> cudaError_t {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {       // first run warms up, best of the other two
+            cudaEventRecord(e0, st);
+            cudaError_t e = launch();
+            if (e != cudaSuccess) return e;
+            cudaEventRecord(e1, st);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) best = std::min(best, t);
+        }
+        out = best;
+        return cudaSuccess;
+    };
+    cudaError_t err = launch_background(D, n_tiles, I, plan->c2, stt, plan->bg_thresh2, st);
+    // Kramers-Kronig variants (the scratch covers both grids)
+    for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+        if (v == 0 && !plan->kkr_ok) continue;
+        plan->use_kkr = v == 0;
+        err = timed([&] { return launch_kk_any(plan, 0, n_tiles, I, plan->xdisc, plan->kk_scratch, stt, st); },
+                    ms[v]);
+    }
+    if (err == cudaSuccess) plan->use_kkr = plan->kkr_ok && !(ms[1] >= 0 && ms[1] < ms[0]);
+    // inputs of the darkfield stage
+    if (err == cudaSuccess) err = launch_kk_any(plan, 0, n_tiles, I, plan->xdisc, plan->kk_scratch, stt, st);
+    if (err == cudaSuccess)
+        err = launch_aberration(D, plan->L, n_tiles, plan->xdisc, plan->zern, plan->beta_scratch, plan->ab_passes,
+                                stt, st);
+    if (err == cudaSuccess) err = launch_phase(D, n_tiles, plan->zern, plan->phi, st);
+    if (err == cudaSuccess) err = launch_stitch(D, n_tiles, plan->xdisc, plan->phi, plan->spec, stt, st);
+    // darkfield variants, each with its own scratch; the solve is idempotent on the
+    // stitched spectrum, so repeated runs see the same system
+    const bool had_reg = plan->use_reg;
+    void* scratch[2] = {nullptr, nullptr};
+    size_t per_block[2] = {dfr_scratch_bytes(D), df_scratch_bytes(D)};
+    scratch[had_reg ? 0 : 1] = plan->df_scratch;
+    for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+        if (v == 0 && !plan->dfr_ok) continue;
+        if (!scratch[v]) {
+            const size_t bytes = (size_t)(v == 0 ? plan->grid_dfr : plan->L.grid_df) * per_block[v];
+            if ((s = dmalloc(plan, &scratch[v], bytes)) != APIC_OK) break;
+        }
+        plan->use_reg = v == 0;
+        plan->df_scratch = scratch[v];
+        plan->df_per_block = per_block[v];
+        err = timed([&] { return launch_df(plan, n_tiles, I, plan->spec, stt, st); }, ms[2 + v]);
+    }
+    if (s == APIC_OK && err == cudaSuccess) {
+        const int pick = plan->dfr_ok && !(ms[3] >= 0 && ms[3] < ms[2]) ? 0 : 1;
+        plan->use_reg = pick == 0;
+        plan->df_scratch = scratch[pick];
+        plan->df_per_block = per_block[pick];
+        void* loser = scratch[1 - pick];
+        if (loser) {
+            cudaFree(loser);
+            plan->allocs.erase(std::find(plan->allocs.begin(), plan->allocs.end(), loser));
+        }
+    } else {   // keep the plan's original darkfield selection
+        plan->use_reg = had_reg;
+        plan->df_scratch = scratch[had_reg ? 0 : 1];
+        plan->df_per_block = per_block[had_reg ? 0 : 1];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (s != APIC_OK) return s;
+    if (err != cudaSuccess) return cuda_fail(err, "apic_plan_autotune");
+    for (int i = 0; i < n_ms && i < 4; ++i) h_ms[i] = ms[i];
     return APIC_OK;
 }
 

@@ -376,3 +376,25 @@ def test_plans_sharing_kernels_coexist():
     res = oracle_tile(I[0], n)
     assert rel_l2(as_complex(field)[0], res.field) < FIELD_TOL
     small.close()
+
+
+@pytest.mark.parametrize("flags", [0, apic.APIC_LEGACY_KERNELS])
+def test_autotune_keeps_the_faster_variants_and_the_results(flags):
+    n = 128
+    I, _, _ = make_tiles(n, 3, seed=55)
+    plan = new_plan(n, max_tiles=3, flags=flags)
+    H = plan.info.out_h
+    f0 = torch.zeros((3, H, 2 * H), dtype=torch.float32, device="cuda")
+    f1 = torch.zeros_like(f0)
+    z = torch.zeros((3, 15), dtype=torch.float32, device="cuda")
+    plan.reconstruct_batch(3, dev(I), f0, z)
+    ms = plan.autotune(3, dev(I))
+    print(ms)
+    assert all(v > 0 for v in ms.values())             # all four variants apply at 128 x 128
+    plan.reconstruct_batch(3, dev(I), f1, z)
+    torch.cuda.synchronize()
+    a, b = as_complex(f0), as_complex(f1)
+    for t in range(3):
+        assert rel_l2(b[t], a[t]) < 2e-4                   # the variants solve the same problems
+    res = oracle_tile(I[0], n)
+    assert rel_l2(b[0], res.field) < FIELD_TOL
