@@ -13,6 +13,8 @@ namespace apic {
 // ---------------------------------------------------------------- background
 // Per tile: mean over the NA-matching images of var(I)/mean(I)^2; flags
 // tiles below the threshold and stacks with negative or non-finite values.
+// Each thread sums its own pixels in FP32 (a few hundred values), the block
+// combines the partial sums in FP64; the darkfield images are only checked.
 __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles, const float* __restrict__ I,
                                                          float* __restrict__ c2, int32_t* __restrict__ status,
                                                          float thresh2, int learned) {
@@ -23,24 +25,30 @@ __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles,
     const float* T = I + (size_t)tile * P.n_img * npix;
     double acc = 0;
     int bad = 0;
+    auto invalid = [](float4 v) {
+        return !(v.x >= 0.f && v.x < INFINITY) || !(v.y >= 0.f && v.y < INFINITY) ||
+               !(v.z >= 0.f && v.z < INFINITY) || !(v.w >= 0.f && v.w < INFINITY);
+    };
     for (int i = 0; i < P.n_img; ++i) {
-        double s = 0, s2 = 0;
         const float4* T4 = reinterpret_cast<const float4*>(T + i * npix);
-        for (size_t k = threadIdx.x; k < npix / 4; k += blockDim.x) {
-            const float4 v = T4[k];
-            bad |= !(v.x >= 0.f && v.x < INFINITY) || !(v.y >= 0.f && v.y < INFINITY) ||
-                   !(v.z >= 0.f && v.z < INFINITY) || !(v.w >= 0.f && v.w < INFINITY);
-            if (i < P.n_bf) {
-                s += (double)v.x + v.y + v.z + v.w;
-                s2 += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
-            }
-        }
+        const int nq = (int)(npix / 4);
         if (i < P.n_bf) {
-            s = block_sum(s, red);
-            s2 = block_sum(s2, red);
-            const double mean = s / npix;
-            const double var = s2 / npix - mean * mean;
+            float s = 0.f, s2 = 0.f;
+#pragma unroll 4
+            for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+                const float4 v = T4[k];
+                bad |= invalid(v);
+                s += (v.x + v.y) + (v.z + v.w);
+                s2 += (v.x * v.x + v.y * v.y) + (v.z * v.z + v.w * v.w);
+            }
+            const double st = block_sum((double)s, red);
+            const double st2 = block_sum((double)s2, red);
+            const double mean = st / npix;
+            const double var = st2 / npix - mean * mean;
             acc += mean > 0 ? var / (mean * mean) : 0.0;
+        } else {
+#pragma unroll 4
+            for (int k = threadIdx.x; k < nq; k += blockDim.x) bad |= invalid(T4[k]);
         }
     }
     const int anybad = __syncthreads_or(bad);
