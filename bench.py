@@ -363,13 +363,20 @@ def gpu_arm(args):
         c1.record()
         torch.cuda.synchronize()
         h2d_gbs = I_host.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+        c0.record()
+        f_host.copy_(probe.view(-1)[:f_host.numel()].view(f_host.shape), non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        d2h_gbs = f_host.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
         del probe
         if world > 1:
             dist.barrier()
-        t0 = time.perf_counter()
+        step_ms = []
         for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
             plan.reconstruct_host(T, I_host, f_host, z_host, s_host)
-        ems = (time.perf_counter() - t0) * 1e3
+            step_ms.append((time.perf_counter() - t0) * 1e3)
+        ems = sum(step_ms)
         if world > 1:
             t = torch.tensor([ems], dtype=torch.float64, device=device)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -378,7 +385,8 @@ def gpu_arm(args):
                "h2d_bytes_per_step": int(I_host.numel() * 4),
                "d2h_bytes_per_step": int(f_host.numel() * 4 + z_host.numel() * 4 + s_host.numel() * 4),
                "steps": args.e2e_steps, "api": "apic_reconstruct_host (pinned host buffers)",
-               "h2d_gbs_measured": h2d_gbs}
+               "h2d_gbs_measured": h2d_gbs, "d2h_gbs_measured": d2h_gbs,
+               "step_ms": [round(v, 2) for v in step_ms]}
         del I_host, f_host, z_host, s_host
 
     # ---- roofline of the darkfield kernel (algorithmic flops / live event time)
