@@ -6,8 +6,10 @@
 // transforms one row or column at a time:
 //   P1 rows: log(max(I, 1e-6 mean I)), forward transform along x
 //   P2 cols: forward along y, half-plane mask of Eq. 5, inverse along y
-//   P3 rows: inverse along x, / n^2, exp (Eq. 6), forward along x
-//   P4 cols: forward along y, / n^2 (Fourier-series coefficients, Eq. 7)
+//   P3 rows: inverse along x, / n^2, exp (Eq. 6), forward along x; only the
+//            columns the gather needs (the pupil box shifted by -k_i) are kept
+//   P4 cols: those columns forward along y, / n^2 (Fourier-series
+//            coefficients, Eq. 7), rows of the shifted pupil box kept
 // then the values at K = k_p - k_i for the pupil points k_p are gathered.
 // log, exp and sincos are the hardware approximations (__logf, __expf,
 // __sincosf): their errors (a few 1e-7 relative for the log-intensities and
@@ -103,7 +105,11 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
             for (int k1 = 0; k1 < BN; ++k1) G[(size_t)(t + 16 * k1) * n + x] = v[k1];
         }
         __syncthreads();
-        // P3: rows, inverse along x, exp, forward along x
+        // only the spectrum at K = k_p - k_i (|k_p| within the pupil box) is gathered:
+        // columns Kx in [kx0, kx0 + nbx), rows Ky in [ky0, ky0 + nby)
+        const int kx0 = -P.pup_ax - kix, nbx = 2 * P.pup_ax + 1;
+        const int ky0 = -P.pup_ay - kiy, nby = 2 * P.pup_ay + 1;
+        // P3: rows, inverse along x, exp, forward along x; the band columns are stored
         for (int r = hw; r < n; r += kKKHW) {
             float2* gr = G + (size_t)r * n;
             float2 v[BN], o[16];
@@ -122,18 +128,26 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
             }
             fft_beta<BN, false>(o, v, h, tw);
 #pragma unroll
-            for (int k1 = 0; k1 < BN; ++k1) gr[t + 16 * k1] = v[k1];
+            for (int k1 = 0; k1 < BN; ++k1) {
+                const int x = t + 16 * k1;
+                if ((unsigned)(sfreq_kk(x, n) - kx0 + n) % (unsigned)n < (unsigned)nbx) gr[x] = v[k1];
+            }
         }
         __syncthreads();
-        // P4: columns, forward along y, series normalisation
-        for (int x = hw; x < n; x += kKKHW) {
+        // P4: band columns, forward along y, series normalisation, band rows stored
+        for (int c = hw; c < nbx; c += kKKHW) {
+            const int x = freq_index(kx0 + c, n);
             float2 v[BN], o[16];
 #pragma unroll
             for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * n + x];
             fft_alpha<BN, false>(v, o, h, tw);
             if (t < BN) {
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) G[(size_t)(t + BN * k1) * n + x] = cscale(o[k1], inv_n2);
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const int y = t + BN * k1;
+                    if ((unsigned)(sfreq_kk(y, n) - ky0 + n) % (unsigned)n < (unsigned)nby)
+                        G[(size_t)y * n + x] = cscale(o[k1], inv_n2);
+                }
             }
         }
         __syncthreads();
