@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-assisted timing")
+    ap.add_argument("--images", choices=["8+16", "8+24"], default="8+16",
+                    help="illumination set (8+24: rings at NA 0.29 / 0.34 / 0.40)")
     ap.add_argument("--seed", type=int, default=2407)
     ap.add_argument("--df-tol", type=float, default=0.0, help="CGLS tolerance (0: library default)")
     ap.add_argument("--df-iters", type=int, default=0, help="CGLS iteration cap (0: library default)")
@@ -229,6 +231,13 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
+def workload_name(T, n, H, images):
+    if (T, n, images) == (512, 256, "8+16"):
+        return WORKLOAD
+    return (f"{T} tiles x {n}x{n} low-res ({H}x{H} output), {images} images, quadratic field-dependent "
+            f"Zernike, Poisson 1e4 photons/px")
+
+
 def learned_timing(args, plan, ill, T, n, H, I, field, zern, status, device):
     """Mpx/s of apic_reconstruct_learned (APIC_NET_WARM) with a briefly trained network."""
     import torch
@@ -281,7 +290,7 @@ def gpu_arm(args):
     device = torch.device("cuda", torch.cuda.current_device())
 
     n, T = args.tile, args.tiles
-    ill = synth.illumination()
+    ill = synth.illumination_8_24() if args.images == "8+24" else synth.illumination()
     plan = apic.Plan.from_illumination(n, ill, max_tiles=T, df_tol=args.df_tol, df_iters=args.df_iters)
     info = plan.info
     H = info.out_h
@@ -415,7 +424,8 @@ def gpu_arm(args):
         "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "tiles_per_gpu": T, "tile": n, "output": H, "images": n_img,
+        "config": {"workload": workload_name(T, n, H, args.images), "tiles_per_gpu": T, "tile": n, "output": H,
+                   "images": n_img,
                    "l2": "inputs_larger_than_l2 (3.2 GB intensities per step)", "launch": "direct C-ABI calls",
                    "tiles_per_s": world * T * args.steps / (ms / 1e3),
                    "df_tol": args.df_tol or "library default", "fft_m": info.fft_m,

@@ -521,7 +521,9 @@ bool nalloc(apic_net* n, T** p, size_t count) {
     return true;
 }
 
-int split_for(long long K) { return (int)std::max(1LL, std::min(128LL, K / 2048)); }
+// split-K factor of a weight-gradient GEMM: ~256 pixels per block, so even the small
+// late layers spread over a few thousand blocks
+int split_for(long long K) { return (int)std::max(1LL, std::min(512LL, K / 256)); }
 
 }  // namespace
 
