@@ -110,6 +110,9 @@ struct apic_plan {
     bool use_kkr = false;        // register-FFT Kramers-Kronig kernel
     size_t smem_kkr = 0;
     int grid_kkr = 0;
+    // second stream for the last partial darkfield wave of a batch (see reconstruct)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float* feat = nullptr;                       // learned path: features, network coefficients
     float* c_net = nullptr;
     unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
@@ -375,13 +378,20 @@ apic_status alloc_workspace(apic_plan* p) {
     if ((s = dmalloc(p, (void**)&p->kk_scratch, kk_blocks * D.h * D.h * sizeof(float2))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->beta_scratch, (size_t)p->L.grid_ab * D.nrows * sizeof(float))) != APIC_OK)
         return s;
+    // darkfield scratch for two waves of blocks: a batch's last partial wave runs
+    // beside the full waves (reconstruct) on blocks of its own
     if (p->use_reg) {
         p->df_per_block = dfr_scratch_bytes(D);
-        if ((s = dmalloc(p, &p->df_scratch, (size_t)p->grid_dfr * p->df_per_block)) != APIC_OK) return s;
+        if ((s = dmalloc(p, &p->df_scratch, 2 * (size_t)p->grid_dfr * p->df_per_block)) != APIC_OK) return s;
     } else {
         p->df_per_block = df_scratch_bytes(D);
-        if ((s = dmalloc(p, &p->df_scratch, (size_t)p->L.grid_df * p->df_per_block)) != APIC_OK) return s;
+        if ((s = dmalloc(p, &p->df_scratch, 2 * (size_t)p->L.grid_df * p->df_per_block)) != APIC_OK) return s;
     }
+    int least = 0, greatest = 0;
+    APIC_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    APIC_TRY_CUDA(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, greatest));
+    APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     return APIC_OK;
 }
 
@@ -395,12 +405,23 @@ cudaError_t launch_kk_any(apic_plan* p, int blocks, int n_tiles, const float* I,
                           I, xdisc, scratch, status, st);
 }
 
-cudaError_t launch_df(apic_plan* p, int n_tiles, const float* I, float2* spec, int32_t* status, cudaStream_t st) {
+// Darkfield blocks of one full wave (the grid of the selected kernel).
+int df_wave(const apic_plan* p) { return std::max(1, p->use_reg ? p->grid_dfr : p->L.grid_df); }
+
+// Darkfield stage on the tiles whose phase table starts at phi; `second` selects the
+// second wave of scratch blocks (for a launch that runs beside another one).
+cudaError_t launch_df_on(apic_plan* p, int n_tiles, const float* I, const float* phi, float2* spec, int32_t* status,
+                         bool second, cudaStream_t st) {
+    char* scratch = (char*)p->df_scratch + (second ? (size_t)df_wave(p) * p->df_per_block : 0);
     if (p->use_reg)
-        return launch_darkfield_reg(p->dev, p->grid_dfr, p->smem_dfr, n_tiles, I, p->phi, spec, p->df_scratch,
+        return launch_darkfield_reg(p->dev, p->grid_dfr, p->smem_dfr, n_tiles, I, phi, spec, scratch,
                                     p->df_per_block, p->df_iters, p->df_tol, status, p->d_counters, st);
-    return launch_darkfield(p->dev, p->L, n_tiles, I, p->phi, spec, p->df_scratch, p->df_per_block, p->df_iters,
-                            p->df_tol, status, p->d_counters, st);
+    return launch_darkfield(p->dev, p->L, n_tiles, I, phi, spec, scratch, p->df_per_block, p->df_iters, p->df_tol,
+                            status, p->d_counters, st);
+}
+
+cudaError_t launch_df(apic_plan* p, int n_tiles, const float* I, float2* spec, int32_t* status, cudaStream_t st) {
+    return launch_df_on(p, n_tiles, I, p->phi, spec, status, false, st);
 }
 
 apic_status check_plan(const apic_plan* plan, int n_tiles) {
@@ -463,13 +484,24 @@ apic_status learned_buffers(apic_plan* p) {
 
 // Background, Kramers-Kronig, aberration (learned when `net`), stitching,
 // darkfield, synthesis and pupil over chunks of max_tiles tiles.
+//
+// The darkfield stage runs one tile per block, so a chunk of nt tiles takes
+// ceil(nt / W) block rounds (W = blocks of a full wave) and its last partial
+// round leaves SMs idle. When nt is not a multiple of W, the r = nt mod W
+// trailing tiles go first: their earlier stages run, their darkfield solves
+// start on a high-priority second stream (own scratch blocks), and meanwhile
+// the earlier stages of the other nt - r tiles run on the remaining SMs,
+// followed by their darkfield launch; synthesis waits for both. Every tile
+// gets exactly the computation of the plain order.
 apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, const float* I, const float* uv,
                         float* field, float* zern, float* pupil, int32_t* status, cudaStream_t st) {
     const DevPlan& D = plan->dev;
     const Launch& L = plan->L;
     const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
     const bool replace = net && (mode & APIC_NET_REPLACE);
+    const bool warm = net && (mode & APIC_NET_WARM);
     const float thresh2 = replace ? plan->bg_c2 : plan->bg_thresh2;
+    const int W = df_wave(plan);
     StageTimer tm(plan, st);
     for (int t0 = 0; t0 < n_tiles; t0 += plan->max_tiles) {
         const int nt = std::min(plan->max_tiles, n_tiles - t0);
@@ -477,14 +509,37 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
         const float* It = I + (size_t)t0 * in_tile;
         int32_t* stt = status ? status + t0 : plan->status;
         float* zt = zern + (size_t)t0 * APIC_N_ZERNIKE;
-        // with several chunks a stage's interval spans from its first start to its last stop
+        const int r = (D.n_used > 0 && nt > W) ? nt % W : 0;      // tiles of the last partial wave
+        const int m0 = nt - r;                                      // tiles of the full waves
+        // earlier stages of tiles [a, a + k) of the chunk; in the split order this runs
+        // for the partial wave (a = m0) and then for the full waves (a = 0), so a stage's
+        // interval starts with the first call and ends with the call for a = 0
+        bool pre_first = true;
+        auto pre_df = [&](int a, int k) -> apic_status {
+            if (k == 0) return APIC_OK;
+            const bool mark0 = first && pre_first, mark1 = last && a == 0;
+            pre_first = false;
+            float2* xd = plan->xdisc + (size_t)a * D.n_bf * D.npup;
+            float* ph = plan->phi + (size_t)a * D.npup;
+            if (mark0) tm.mark(1, 0);
+            APIC_TRY_LAUNCH(launch_kk_any(plan, 0, k, It + (size_t)a * in_tile, xd, plan->kk_scratch, stt + a, st));
+            if (mark1) tm.mark(1, 1);
+            if (mark0) tm.mark(2, 0);
+            APIC_TRY_LAUNCH(launch_aberration(D, L, k, xd, zt + (size_t)a * APIC_N_ZERNIKE, plan->beta_scratch,
+                                              plan->ab_passes, stt + a, st,
+                                              net ? plan->c_net + (size_t)a * APIC_N_ZERNIKE : nullptr, warm ? 1 : 0));
+            if (mark1) tm.mark(2, 1);
+            if (mark0) tm.mark(3, 0);
+            APIC_TRY_LAUNCH(launch_phase(D, k, zt + (size_t)a * APIC_N_ZERNIKE, ph, st));
+            APIC_TRY_LAUNCH(launch_stitch(D, k, xd, ph, plan->spec + (size_t)a * D.nap, stt + a, st));
+            if (mark1) tm.mark(3, 1);
+            return APIC_OK;
+        };
+        // with several chunks a stage's interval spans from its first start to its last stop;
+        // in the split order the intervals of the stages before the darkfield overlap it
         if (first) tm.mark(0, 0);
         APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
         if (last) tm.mark(0, 1);
-        if (first) tm.mark(1, 0);
-        APIC_TRY_LAUNCH(launch_kk_any(plan, 0, nt, It, plan->xdisc, plan->kk_scratch, stt, st));
-        if (last) tm.mark(1, 1);
-        if (first) tm.mark(2, 0);
         if (net) {
             APIC_TRY_LAUNCH(launch_features(D, plan->grid_kkr, nt, It, plan->feat, plan->kk_scratch, st));
             const int nb = net_max_batch(net);
@@ -496,16 +551,26 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                 plan->launches += net_launches(net) - before;
             }
         }
-        APIC_TRY_LAUNCH(launch_aberration(D, L, nt, plan->xdisc, zt, plan->beta_scratch, plan->ab_passes, stt, st,
-                                          net ? plan->c_net : nullptr, net && (mode & APIC_NET_WARM) ? 1 : 0));
-        if (last) tm.mark(2, 1);
-        if (first) tm.mark(3, 0);
-        APIC_TRY_LAUNCH(launch_phase(D, nt, zt, plan->phi, st));
-        APIC_TRY_LAUNCH(launch_stitch(D, nt, plan->xdisc, plan->phi, plan->spec, stt, st));
-        if (last) tm.mark(3, 1);
-        if (first) tm.mark(4, 0);
-        APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
-        if (last) tm.mark(4, 1);
+        apic_status s;
+        if (r > 0) {
+            // last partial wave first: its darkfield starts beside the others' earlier stages
+            if ((s = pre_df(m0, r)) != APIC_OK) return s;
+            APIC_TRY_CUDA(cudaEventRecord(plan->ev_fork, st));
+            if (first) tm.mark(4, 0);
+            APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
+            APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)m0 * in_tile, plan->phi + (size_t)m0 * D.npup,
+                                         plan->spec + (size_t)m0 * D.nap, stt + m0, true, plan->side));
+            APIC_TRY_CUDA(cudaEventRecord(plan->ev_join, plan->side));
+            if ((s = pre_df(0, m0)) != APIC_OK) return s;
+            APIC_TRY_LAUNCH(launch_df_on(plan, m0, It, plan->phi, plan->spec, stt, false, st));
+            APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_join, 0));
+            if (last) tm.mark(4, 1);
+        } else {
+            if ((s = pre_df(0, nt)) != APIC_OK) return s;
+            if (first) tm.mark(4, 0);
+            APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
+            if (last) tm.mark(4, 1);
+        }
         if (first) tm.mark(5, 0);
         APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, (float2*)field + (size_t)t0 * out_tile, stt, st));
         if (last) tm.mark(5, 1);
@@ -618,6 +683,9 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         cudaDeviceSynchronize();
         for (void* p : plan->allocs) cudaFree(p);
         for (auto e : plan->events) cudaEventDestroy(e);
+        if (plan->side) cudaStreamDestroy(plan->side);
+        if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+        if (plan->ev_join) cudaEventDestroy(plan->ev_join);
         if (plan->io.ready) {
             for (int b = 0; b < 2; ++b) {
                 cudaEventDestroy(plan->io.in_done[b]);
@@ -897,7 +965,7 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
     // chunk sizes follow the darkfield grid (one tile per block): the first chunk
     // is one full wave so computation starts after a short copy, the rest go in
     // chunks of up to four waves; the total number of waves matches one batch.
-    const int wave = std::max(1, plan->use_reg ? plan->grid_dfr : plan->L.grid_df);
+    const int wave = df_wave(plan);
     const int max_chunk = std::max(1, std::min(plan->max_tiles, 4 * wave));
     if (!io.ready) {
         io.chunk = max_chunk;
@@ -1001,7 +1069,7 @@ apic_status apic_plan_autotune(apic_plan* plan, int n_tiles, const float* I, dou
     for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
         if (v == 0 && !plan->dfr_ok) continue;
         if (!scratch[v]) {
-            const size_t bytes = (size_t)(v == 0 ? plan->grid_dfr : plan->L.grid_df) * per_block[v];
+            const size_t bytes = 2 * (size_t)(v == 0 ? plan->grid_dfr : plan->L.grid_df) * per_block[v];
             if ((s = dmalloc(plan, &scratch[v], bytes)) != APIC_OK) break;
         }
         plan->use_reg = v == 0;

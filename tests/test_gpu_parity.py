@@ -398,3 +398,31 @@ def test_autotune_keeps_the_faster_variants_and_the_results(flags):
         assert rel_l2(b[t], a[t]) < 2e-4                   # the variants solve the same problems
     res = oracle_tile(I[0], n)
     assert rel_l2(b[0], res.field) < FIELD_TOL
+
+
+def test_partial_wave_runs_beside_the_full_waves_bit_exactly():
+    """1000 tiles in one call (the last partial darkfield wave runs on a second
+    stream beside the other tiles' earlier stages) equal ten calls of 100 tiles
+    (no partial wave split), bit for bit."""
+    n, T = 64, 1000
+    plan = new_plan(n, max_tiles=T)
+    rng = np.random.default_rng(12)
+    zern = torch.as_tensor(np.resize(rng.uniform(-0.5, 0.5, (16, 15)).astype(np.float32), (T, 15)), device="cuda")
+    zern[:, :3] = 0
+    from paper_2407_20469_gb300 import learn
+    obj = learn.device_objects(T, 2 * n, 21, "cuda")
+    I = torch.empty((T, 24, n, n), dtype=torch.float32, device="cuda")
+    plan.simulate(T, obj, zern, 1e4, 21, I)
+    H = plan.info.out_h
+    f1 = torch.empty((T, H, 2 * H), dtype=torch.float32, device="cuda")
+    f2 = torch.empty_like(f1)
+    z1 = torch.empty((T, 15), dtype=torch.float32, device="cuda")
+    z2 = torch.empty_like(z1)
+    s1 = torch.empty(T, dtype=torch.int32, device="cuda")
+    s2 = torch.empty_like(s1)
+    plan.reconstruct_batch(T, I, f1, z1, None, s1)
+    for t0 in range(0, T, 100):
+        plan.reconstruct_batch(100, I[t0:t0 + 100], f2[t0:t0 + 100], z2[t0:t0 + 100], None, s2[t0:t0 + 100])
+    torch.cuda.synchronize()
+    assert torch.equal(s1, s2) and torch.equal(z1, z2) and torch.equal(f1, f2)
+    assert torch.isfinite(f1).all()
