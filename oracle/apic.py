@@ -39,6 +39,26 @@ def wrap(a):
 
 
 # ----------------------------------------------------------------------------
+# 0. Background test (Sec. 3.2)
+# ----------------------------------------------------------------------------
+
+def background_contrast2(I_bf: np.ndarray) -> float:
+    """Squared RMS contrast of a tile: the mean over its NA-matching images of
+    var(I) / mean(I)^2 (population variance over the pixels).
+
+    Sec. 3.2 skips patches without sample by a threshold on their variation;
+    the statistic is read as this normalised variance, compared with the square
+    of the contrast threshold (2 %).
+    """
+    I = np.asarray(I_bf, dtype=np.float64)
+    out = 0.0
+    for img in I:
+        mu = img.mean()
+        out += ((img - mu) ** 2).mean() / mu ** 2 if mu > 0 else 0.0
+    return float(out / len(I))
+
+
+# ----------------------------------------------------------------------------
 # 1. Kramers-Kronig recovery (Eq. 4-7)
 # ----------------------------------------------------------------------------
 

@@ -426,3 +426,25 @@ def test_partial_wave_runs_beside_the_full_waves_bit_exactly():
     torch.cuda.synchronize()
     assert torch.equal(s1, s2) and torch.equal(z1, z2) and torch.equal(f1, f2)
     assert torch.isfinite(f1).all()
+
+
+def test_background_statistic_matches_oracle():
+    """Per-tile squared contrast (Sec. 3.2 background test) against the oracle's
+    definition, on ordinary and near-blank tiles; the flag follows the threshold."""
+    from paper_2407_20469_gb300 import learn
+    n, T = 128, 12
+    plan = new_plan(n, max_tiles=T, bg_contrast=0.02)
+    uv, zern, blank = learn.draw_tiles(T, 31, learn.field_table())
+    blank[::2] = True
+    I = learn.simulate(plan, zern, blank, 31)
+    c2 = torch.empty(T, dtype=torch.float32, device="cuda")
+    st = torch.empty(T, dtype=torch.int32, device="cuda")
+    plan.background(T, I, c2, st)
+    torch.cuda.synchronize()
+    Ih = I.cpu().numpy()
+    got, s = c2.cpu().numpy(), st.cpu().numpy()
+    for t in range(T):
+        ref = oapic.background_contrast2(Ih[t, :8])
+        assert abs(got[t] - ref) <= 1e-6 + 1e-4 * ref, (t, got[t], ref)
+        assert bool(s[t] & apic.APIC_TILE_BACKGROUND) == (ref < 0.02 ** 2)
+    assert (s & apic.APIC_TILE_BACKGROUND).any() and not (s & apic.APIC_TILE_BACKGROUND).all()

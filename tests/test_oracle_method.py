@@ -291,3 +291,18 @@ def test_synthetic_aperture_resolution_matches_paper_formula():
     assert abs(res_um - theory) / theory < 0.02
     # the paper prints 761 nm for 522 nm / (0.44 + 0.25); the ratio itself is 756.5 nm
     assert abs(theory * 1000 - paper["printed_theory_nm"]) / paper["printed_theory_nm"] < 0.01
+
+
+def test_background_contrast_closed_forms():
+    """var / mean^2 of I = m (1 + a cos(2 pi k x / n)) over whole periods is a^2 / 2;
+    a constant image has 0; the statistic is scale invariant and averages images."""
+    from oracle import apic as oapic
+    n = 32
+    x = np.arange(n)
+    a = 0.3
+    I1 = 5.0 * (1.0 + a * np.cos(2 * np.pi * 3 * x / n))[None, :] * np.ones((n, 1))
+    I2 = np.full((n, n), 2.0)
+    assert abs(oapic.background_contrast2(I1[None]) - a * a / 2) < 1e-15
+    assert oapic.background_contrast2(I2[None]) == 0.0
+    assert abs(oapic.background_contrast2(np.stack([I1, I2])) - a * a / 4) < 1e-15
+    assert abs(oapic.background_contrast2((7 * I1)[None]) - a * a / 2) < 1e-14
