@@ -13,10 +13,10 @@
 //     R3 rows of U: forward along x, gather w on U, <d, w>
 //   then x += alpha d, s -= alpha w, and d = s + beta d (folded into the next
 //   R1). Transforms FP32; inner products, step lengths and the solution FP64.
-// GU / GQ are band-row grids (only rows holding U or Q points). GU lives in
-// shared memory (row stride m + 1, so the column passes are conflict free); GQ,
-// the column-major known field p, b on Q and the FP64 solution live in the
-// block's global scratch (L2-resident). The setup transforms of each image
+// GU / GQ are band-row grids (only rows holding U or Q points). GU and the CG
+// vectors (FP64 solution included) live in shared memory (GU with row stride
+// m + 1, so the column passes are conflict free); GQ, the column-major known
+// field p and b on Q live in the block's global scratch (L2-resident). The setup transforms of each image
 // reuse the shared-memory space of GU. One block per tile (persistent); images
 // of a tile are sequential. Each pass is a separate (non-inlined) function so
 // registers are allocated per pass.
@@ -344,9 +344,10 @@ __device__ __noinline__ void pass_rows_rhs(HW w, const float2* tw, float2* GQ, i
 //   [gu, c)        GU, band_u rows of m + 1 complex values
 //   [0, c)         during the setup transforms of an image: half-warp areas of
 //                  the n-grid passes, then the column stage (aliases the above)
+//   [x, c)         FP64 solution x
 //   [c, total)     CG vectors d, s, w; step twiddles of m and n; reduction slots
 struct DFRSmem {
-    size_t gu, stage, c, total;
+    size_t gu, stage, x, c, total;
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -362,7 +363,8 @@ __host__ __device__ inline DFRSmem dfr_smem_layout(int B, int BN, int band_u, in
     const size_t stage_c = (size_t)band_q * kStageLd * sizeof(float2);
     const size_t stage_f = (size_t)n * kStageLd * sizeof(float);
     const size_t stage_end = L.stage + align16(stage_c > stage_f ? stage_c : stage_f);
-    L.c = gu_end > stage_end ? gu_end : stage_end;
+    L.x = gu_end > stage_end ? gu_end : stage_end;
+    L.c = L.x + align16((size_t)max_N * sizeof(double2));
     size_t t = L.c + (size_t)3 * max_N * sizeof(float2);                   // d, s, w
     t += (size_t)2 * (m + n) * sizeof(float2);                            // step twiddles
     t = align16(t) + 64 * sizeof(double);                                 // reductions
@@ -374,12 +376,11 @@ size_t dfr_smem_bytes(int B, int BN, int band_u, int band_q, int max_N) {
     return dfr_smem_layout(B, BN, band_u, band_q, max_N).total;
 }
 
-// Global scratch of one block: FP64 solution x, GQ (Q or P band rows), the
-// known field / image rows, b on Q.
+// Global scratch of one block: GQ (Q or P band rows), the known field / image
+// rows, b on Q.
 size_t dfr_scratch_bytes(const DevPlan& P) {
     const int m = P.mr, n = P.h;
-    size_t s = (size_t)P.max_N * sizeof(double2);                                  // x
-    s += (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m * sizeof(float2);  // GQ
+    size_t s = (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m * sizeof(float2);  // GQ
     s += std::max((size_t)m * m, (size_t)P.band_q * n) * sizeof(float2);           // PF / F(I) rows
     s += (size_t)P.max_M * sizeof(float2);                                         // b on Q
     return (s + 255) & ~(size_t)255;
@@ -416,9 +417,9 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
     w.hs = reinterpret_cast<float2*>(sbase) + w.hw * HWM;
     wn.hs = reinterpret_cast<float2*>(sbase) + w.hw * HWN;
 
+    double2* xv = reinterpret_cast<double2*>(sbase + SL.x);
     char* base = scratch + (size_t)blockIdx.x * per_block;
-    double2* xv = reinterpret_cast<double2*>(base);
-    float2* GQ = reinterpret_cast<float2*>(xv + P.max_N);
+    float2* GQ = reinterpret_cast<float2*>(base);
     float2* PF = GQ + (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m;   // column-major p, or F(I) rows
     float2* bq = PF + (size_t)max(m * m, P.band_q * n);
     const float inv_m2 = 1.f / (float)(m * m);
