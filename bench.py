@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--impl", choices=["apic", "reference"], default="apic")
     ap.add_argument("--tiles", type=int, default=512)
     ap.add_argument("--tile", type=int, default=256)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-assisted timing")
     ap.add_argument("--images", choices=["8+16", "8+24"], default="8+16",
