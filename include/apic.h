@@ -169,6 +169,11 @@ apic_status apic_plan_df_set(const apic_plan* plan, int index, int which, int32_
  * aberration solve (Eq. 8-10), correction and stitching, darkfield extension
  * (Eq. 11-13), inverse transform. The global phase of the field is the
  * phase gauge of Eq. 5 (mean phase of the recovered fields set to zero).
+ * Batches above max_tiles are processed in chunks. When a chunk is not a
+ * whole number of darkfield waves (one tile per block), its last partial
+ * wave's darkfield solves run on a second stream the plan owns, forked from
+ * and joined back to `stream` (stream capture follows the fork); results are
+ * identical to the plain order.
  */
 apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* d_intensity,
                                    float* d_field, float* d_zernike, float* d_pupil,
