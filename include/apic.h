@@ -394,7 +394,7 @@ apic_status apic_net_get_params(const apic_net* net, float* h_params, size_t cou
 /* Gradients of the last apic_net_backward, same layout. Synchronous. */
 apic_status apic_net_get_grads(const apic_net* net, float* h_grads, size_t count);
 
-/* Forward pass: d_feat [batch][64][64][8], d_uv [batch][2] (NULL: zeros),
+/* Forward pass: d_feat [batch][64][64][8] (16-byte aligned), d_uv [batch][2] (NULL: zeros),
  * d_out [batch][15] (Noll 1..3 written as 0; NULL: kept internally). The
  * features must stay valid until the matching apic_net_backward. */
 apic_status apic_net_forward(apic_net* net, int batch, const float* d_feat, const float* d_uv,

@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -39,23 +40,38 @@ constexpr int kOut = 12;
 constexpr int kC0 = 8, kC1 = 32, kC2 = 64, kC3 = 128, kC4 = 256;
 constexpr int kHin = kC4 + 2;
 
+// FP32 parameters W_l [rows][taps + 1] back to back (off, ld); the BF16 copy the
+// GEMMs read has its rows padded to a multiple of 8 values (offp, ldp) so that
+// 16-byte vector loads stay aligned.
 struct Layout {
-    size_t off[6];
+    size_t off[6], offp[6];
     int rows[6], taps[6];
-    size_t total;
+    size_t total, total_pad;
     Layout() {
         const int r[6] = {kC1, kC2, kC3, kC4, kHidden, kOut};
         const int t[6] = {9 * kC0, 9 * kC1, 9 * kC2, 9 * kC3, kHin, kHidden};
-        size_t o = 0;
+        size_t o = 0, op = 0;
         for (int l = 0; l < 6; ++l) {
             off[l] = o;
+            offp[l] = op;
             rows[l] = r[l];
             taps[l] = t[l];
             o += (size_t)r[l] * (t[l] + 1);
+            op += (size_t)r[l] * ((t[l] + 1 + 7) / 8 * 8);
         }
         total = o;
+        total_pad = op;
     }
-    int ld(int l) const { return taps[l] + 1; }
+    __host__ __device__ int ld(int l) const { return taps[l] + 1; }
+    __host__ __device__ int ldp(int l) const { return (taps[l] + 1 + 7) / 8 * 8; }
+    // index in the padded copy of flat parameter i
+    __device__ size_t padded(size_t i) const {
+        int l = 5;
+        while (l > 0 && i < off[l]) --l;
+        const size_t q = i - off[l];
+        const size_t r = q / (size_t)ld(l), c = q - r * (size_t)ld(l);
+        return offp[l] + r * (size_t)ldp(l) + c;
+    }
 };
 
 // ------------------------------------------------------------------ features
@@ -141,6 +157,61 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Staging of 16 consecutive k of one A row (m fixed) or one B column (n fixed)
+// into 16 BF16 values of shared memory (16-byte aligned). Loaders whose data is
+// contiguous along k provide segA / segB with vector loads; the others go
+// through their element loaders.
+template <class F, class = void>
+struct HasSegA : std::false_type {};
+template <class F>
+struct HasSegA<F, std::void_t<decltype(std::declval<const F&>().segA(0, 0, 0, (__nv_bfloat16*)nullptr))>>
+    : std::true_type {};
+template <class F, class = void>
+struct HasSegB : std::false_type {};
+template <class F>
+struct HasSegB<F, std::void_t<decltype(std::declval<const F&>().segB(0, 0, 0, (__nv_bfloat16*)nullptr))>>
+    : std::true_type {};
+
+__device__ __forceinline__ void zero16(__nv_bfloat16* dst) {
+    reinterpret_cast<uint4*>(dst)[0] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(dst)[1] = make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const unsigned*>(&h);
+}
+
+// 8 floats (two float4, 16-byte aligned source) -> 8 BF16 (one uint4)
+__device__ __forceinline__ uint4 f8_to_bf16(const float* src) {
+    const float4 a = reinterpret_cast<const float4*>(src)[0], b = reinterpret_cast<const float4*>(src)[1];
+    return make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
+}
+
+template <class F>
+__device__ __forceinline__ void stage_a(const F& f, bool valid, int m, int k0, int kend, __nv_bfloat16* dst) {
+    if (!valid) {
+        zero16(dst);
+    } else if constexpr (HasSegA<F>::value) {
+        f.segA(m, k0, kend, dst);
+    } else {
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) dst[c] = __float2bfloat16(k0 + c < kend ? f(m, k0 + c) : 0.f);
+    }
+}
+
+template <class F>
+__device__ __forceinline__ void stage_b(const F& f, bool valid, int n, int k0, int kend, __nv_bfloat16* dst) {
+    if (!valid) {
+        zero16(dst);
+    } else if constexpr (HasSegB<F>::value) {
+        f.segB(k0, kend, n, dst);
+    } else {
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) dst[c] = __float2bfloat16(k0 + c < kend ? f(k0 + c, n) : 0.f);
+    }
+}
+
 template <class LA, class LB, class EP>
 __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, int k_split, LA la, LB lb, EP ep) {
     __shared__ __align__(16) __nv_bfloat16 As[kBM * kLD];
@@ -161,13 +232,8 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, int k_split, 
     const int sr = threadIdx.x >> 1, sc = (threadIdx.x & 1) * 16;
     const int am = m0 + sr, bn = n0 + sr;
     for (int k0 = kb; k0 < ke; k0 += kBK) {
-#pragma unroll 4
-        for (int c = 0; c < 16; ++c) {
-            const int k = k0 + sc + c;
-            const bool kin = k < ke;
-            As[sr * kLD + sc + c] = __float2bfloat16(am < M && kin ? la(am, k) : 0.f);
-            Bs[sr * kLD + sc + c] = __float2bfloat16(bn < N && kin ? lb(k, bn) : 0.f);
-        }
+        stage_a(la, am < M, am, k0 + sc, ke, As + sr * kLD + sc);
+        stage_b(lb, bn < N, bn, k0 + sc, ke, Bs + sr * kLD + sc);
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kBK; kk += 16) {
@@ -238,6 +304,40 @@ struct ConvIn {
         if ((unsigned)yy >= (unsigned)H || (unsigned)xx >= (unsigned)H) return 0.f;
         return to_f(x[(((size_t)b * H + yy) * H + xx) * C + c]);
     }
+    // address of channel c of tap s at output pixel m, or NULL in the padding
+    __device__ const T* tap(int m, int s, int c) const {
+        const int dy = s / 3, dx = s - 3 * dy;
+        const int q = m / H, xx = m - q * H + dx - 1;
+        const int b = q / H, yy = q - b * H + dy - 1;
+        if ((unsigned)yy >= (unsigned)H || (unsigned)xx >= (unsigned)H) return nullptr;
+        return x + (((size_t)b * H + yy) * H + xx) * C + c;
+    }
+    // 16 consecutive taps of a row: one tap's 16 channels (C % 16 == 0, BF16
+    // maps) or two taps' 8 channels (C == 8, FP32 input); vector loads
+    __device__ void segA(int m, int k0, int kend, __nv_bfloat16* dst) const {
+        if (k0 + 16 <= kend && k0 + 16 <= 9 * C) {
+            if constexpr (std::is_same<T, __nv_bfloat16>::value && C % 16 == 0) {
+                const int s = k0 / C;
+                const T* p = tap(m, s, k0 - s * C);
+                if (p) {
+                    reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(p)[0];
+                    reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(p)[1];
+                } else {
+                    zero16(dst);
+                }
+                return;
+            } else if constexpr (std::is_same<T, float>::value && C == 8) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const T* p = tap(m, k0 / 8 + h, 0);
+                    reinterpret_cast<uint4*>(dst)[h] = p ? f8_to_bf16(p) : make_uint4(0, 0, 0, 0);
+                }
+                return;
+            }
+        }
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) dst[c] = __float2bfloat16(k0 + c < kend ? (*this)(m, k0 + c) : 0.f);
+    }
 };
 // (co, pixel) of the pre-activation gradient dz = dr * [r > 0]
 template <int C>
@@ -263,20 +363,64 @@ struct DzShift {
         const size_t i = (((size_t)b * H + yy) * H + xx) * Co + co;
         return __bfloat162float(r[i]) > 0.f ? g[i] : 0.f;
     }
+    // 16 consecutive output channels of one tap (Co % 16 == 0): vector loads of
+    // the gradient and of the activation that masks it
+    __device__ void segA(int m, int k0, int kend, __nv_bfloat16* dst) const {
+        static_assert(Co % 16 == 0, "16 channels per segment");
+        if (k0 + 16 <= kend) {
+            const int s = k0 / Co, co = k0 - s * Co, dy = s / 3, dx = s - 3 * dy;
+            const int q = m / H, xx = m - q * H - dx + 1;
+            const int b = q / H, yy = q - b * H - dy + 1;
+            if ((unsigned)yy >= (unsigned)H || (unsigned)xx >= (unsigned)H) {
+                zero16(dst);
+                return;
+            }
+            const size_t i = (((size_t)b * H + yy) * H + xx) * Co + co;
+            const float4* g4 = reinterpret_cast<const float4*>(g + i);
+            const uint4* r4 = reinterpret_cast<const uint4*>(r + i);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint4 rv = r4[h];
+                const __nv_bfloat16* rb = reinterpret_cast<const __nv_bfloat16*>(&rv);
+                const float4 a = g4[2 * h], c = g4[2 * h + 1];
+                const float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+                unsigned w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    w[e] = pack_bf16(__bfloat162float(rb[2 * e]) > 0.f ? v[2 * e] : 0.f,
+                                     __bfloat162float(rb[2 * e + 1]) > 0.f ? v[2 * e + 1] : 0.f);
+                reinterpret_cast<uint4*>(dst)[h] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            return;
+        }
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) dst[c] = __float2bfloat16(k0 + c < kend ? (*this)(m, k0 + c) : 0.f);
+    }
 };
 // (k = (dy, dx, co), n = ci) -> W[co][(dy, dx, ci)]
 template <int Ci, int Co>
 struct WFlip {
     const __nv_bfloat16* w;
+    int ld;
     __device__ float operator()(int k, int n) const {
         const int co = k % Co, s = k / Co;
-        return __bfloat162float(w[(size_t)co * (9 * Ci + 1) + s * Ci + n]);
+        return __bfloat162float(w[(size_t)co * ld + s * Ci + n]);
     }
 };
-struct WT {                 // B(k, n) = W[n][k]
+struct WT {                 // B(k, n) = W[n][k]; rows padded to multiples of 8
     const __nv_bfloat16* w;
     int ld;
     __device__ float operator()(int k, int n) const { return __bfloat162float(w[(size_t)n * ld + k]); }
+    __device__ void segB(int k0, int kend, int n, __nv_bfloat16* dst) const {
+        const __nv_bfloat16* p = w + (size_t)n * ld + k0;
+        if (k0 + 16 <= kend) {
+            reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(p)[0];
+            reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(p)[1];
+            return;
+        }
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) dst[c] = k0 + c < kend ? p[c] : __float2bfloat16(0.f);
+    }
 };
 struct WN {                 // B(k, n) = W[k][n]
     const __nv_bfloat16* w;
@@ -287,6 +431,16 @@ struct Mat {                // (r, c) -> p[r][c]
     const float* p;
     int ld;
     __device__ float operator()(int r, int c) const { return p[(size_t)r * ld + c]; }
+    __device__ void segA(int r, int k0, int kend, __nv_bfloat16* dst) const {
+        const float* q = p + (size_t)r * ld + k0;
+        if (k0 + 16 <= kend && (ld & 3) == 0) {
+            reinterpret_cast<uint4*>(dst)[0] = f8_to_bf16(q);
+            reinterpret_cast<uint4*>(dst)[1] = f8_to_bf16(q + 8);
+            return;
+        }
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) dst[c] = __float2bfloat16(k0 + c < kend ? q[c] : 0.f);
+    }
 };
 struct MatT {               // (r, c) -> p[c][r]
     const float* p;
@@ -419,15 +573,15 @@ __global__ void k_relu_mask(float* __restrict__ g, const float* __restrict__ h, 
         if (!(h[i] > 0.f)) g[i] = 0.f;
 }
 
-__global__ void k_cast_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+__global__ void k_cast_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n, Layout L) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = __float2bfloat16(src[i]);
+        dst[L.padded(i)] = __float2bfloat16(src[i]);
 }
 
 // AdamW with bias-corrected moments and decoupled weight decay; refreshes the bf16 copy.
 __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                         float* __restrict__ v, __nv_bfloat16* __restrict__ pbf, size_t n, float lr, float b1, float b2,
-                        float eps, float wd, float c1, float c2) {
+                        float eps, float wd, float c1, float c2, Layout L) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -436,7 +590,7 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
         v[i] = vi;
         const float pi = p[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
         p[i] = pi;
-        pbf[i] = __float2bfloat16(pi);
+        pbf[L.padded(i)] = __float2bfloat16(pi);
     }
 }
 
@@ -543,26 +697,26 @@ cudaError_t net_predict(apic_net* n, int B, const float* feat, const float* uv, 
                                                                            C);                                    \
     ++*nl;                                                                                                       \
     NET_STEP(cudaGetLastError());
-    NET_STEP(gemm(B * 64 * 64, kC1, 9 * kC0, 1, ConvIn<64, kC0, float>{feat}, WT{n->wbf + L.off[0], L.ld(0)},
+    NET_STEP(gemm(B * 64 * 64, kC1, 9 * kC0, 1, ConvIn<64, kC0, float>{feat}, WT{n->wbf + L.offp[0], L.ldp(0)},
                   EpConv{n->r[0], n->params + L.off[0] + L.taps[0], L.ld(0), kC1}, st, nl));
     NET_POOL(0, 64, kC1);
     NET_STEP(gemm(B * 32 * 32, kC2, 9 * kC1, 1, ConvIn<32, kC1, __nv_bfloat16>{n->pool[0]},
-                  WT{n->wbf + L.off[1], L.ld(1)}, EpConv{n->r[1], n->params + L.off[1] + L.taps[1], L.ld(1), kC2}, st,
+                  WT{n->wbf + L.offp[1], L.ldp(1)}, EpConv{n->r[1], n->params + L.off[1] + L.taps[1], L.ld(1), kC2}, st,
                   nl));
     NET_POOL(1, 32, kC2);
     NET_STEP(gemm(B * 16 * 16, kC3, 9 * kC2, 1, ConvIn<16, kC2, __nv_bfloat16>{n->pool[1]},
-                  WT{n->wbf + L.off[2], L.ld(2)}, EpConv{n->r[2], n->params + L.off[2] + L.taps[2], L.ld(2), kC3}, st,
+                  WT{n->wbf + L.offp[2], L.ldp(2)}, EpConv{n->r[2], n->params + L.off[2] + L.taps[2], L.ld(2), kC3}, st,
                   nl));
     NET_POOL(2, 16, kC3);
     NET_STEP(gemm(B * 8 * 8, kC4, 9 * kC3, 1, ConvIn<8, kC3, __nv_bfloat16>{n->pool[2]},
-                  WT{n->wbf + L.off[3], L.ld(3)}, EpConv{n->r[3], n->params + L.off[3] + L.taps[3], L.ld(3), kC4}, st,
+                  WT{n->wbf + L.offp[3], L.ldp(3)}, EpConv{n->r[3], n->params + L.off[3] + L.taps[3], L.ld(3), kC4}, st,
                   nl));
     k_gap_concat<<<B, 256, 0, st>>>(n->r[3], uv, n->hin, 64, kC4);
     ++*nl;
     NET_STEP(cudaGetLastError());
-    NET_STEP(gemm(B, kHidden, kHin, 1, Mat{n->hin, kHin}, WT{n->wbf + L.off[4], L.ld(4)},
+    NET_STEP(gemm(B, kHidden, kHin, 1, Mat{n->hin, kHin}, WT{n->wbf + L.offp[4], L.ldp(4)},
                   EpDense{n->h4, n->params + L.off[4] + L.taps[4], L.ld(4), kHidden, true}, st, nl));
-    NET_STEP(gemm(B, kOut, kHidden, 1, Mat{n->h4, kHidden}, WT{n->wbf + L.off[5], L.ld(5)},
+    NET_STEP(gemm(B, kOut, kHidden, 1, Mat{n->h4, kHidden}, WT{n->wbf + L.offp[5], L.ldp(5)},
                   EpDense{n->y, n->params + L.off[5] + L.taps[5], L.ld(5), kOut, false}, st, nl));
     if (out15) {
         k_pack_out<<<(B * APIC_N_ZERNIKE + 255) / 256, 256, 0, st>>>(n->y, out15, B);
@@ -593,7 +747,7 @@ apic_status apic_net_create(int max_batch, apic_net** out) {
     n->max_batch = max_batch;
     const size_t P = n->L.total, B = (size_t)max_batch;
     bool ok = nalloc(n, &n->params, P) && nalloc(n, &n->grads, P) && nalloc(n, &n->m, P) && nalloc(n, &n->v, P) &&
-              nalloc(n, &n->wbf, P);
+              nalloc(n, &n->wbf, n->L.total_pad);
     const int C[4] = {kC1, kC2, kC3, kC4};
     int H = kCrop;
     for (int l = 0; l < 4 && ok; ++l) {
@@ -612,7 +766,7 @@ apic_status apic_net_create(int max_batch, apic_net** out) {
     }
     if (cudaMemset(n->params, 0, P * 4) != cudaSuccess || cudaMemset(n->grads, 0, P * 4) != cudaSuccess ||
         cudaMemset(n->m, 0, P * 4) != cudaSuccess || cudaMemset(n->v, 0, P * 4) != cudaSuccess ||
-        cudaMemset(n->wbf, 0, P * 2) != cudaSuccess) {
+        cudaMemset(n->wbf, 0, n->L.total_pad * 2) != cudaSuccess) {
         cudaGetLastError();
         apic_net_destroy(n);
         return net_fail(APIC_ECUDA, "network initialisation failed");
@@ -633,7 +787,7 @@ apic_status apic_net_set_params(apic_net* n, const float* h, size_t count) {
     if (!n || !h || count != n->L.total) return net_fail(APIC_EINVAL, "expected apic_net_param_count() floats");
     NET_TRY(cudaDeviceSynchronize());
     NET_TRY(cudaMemcpy(n->params, h, count * 4, cudaMemcpyHostToDevice));
-    k_cast_bf16<<<blocks_for(count), 256>>>(n->params, n->wbf, count);
+    k_cast_bf16<<<blocks_for(count), 256>>>(n->params, n->wbf, count, n->L);
     NET_TRY(cudaGetLastError());
     NET_TRY(cudaMemset(n->m, 0, count * 4));
     NET_TRY(cudaMemset(n->v, 0, count * 4));
@@ -659,6 +813,7 @@ apic_status apic_net_forward(apic_net* n, int batch, const float* feat, const fl
                              void* stream) {
     if (!n || !feat) return net_fail(APIC_EINVAL, "NULL network or features");
     if (batch < 1 || batch > n->max_batch) return net_fail(APIC_EINVAL, "batch must be in [1, max_batch]");
+    if (reinterpret_cast<uintptr_t>(feat) & 15) return net_fail(APIC_EINVAL, "features must be 16-byte aligned");
     NET_TRY(net_predict(n, batch, feat, uv, out15, (cudaStream_t)stream));
     return APIC_OK;
 }
@@ -677,7 +832,7 @@ apic_status apic_net_backward(apic_net* n, const float* target15, float* loss, v
     // dense 256 -> 12
     NET_TRY(gemm(kOut, L.ld(5), B, split_for(B), MatT{n->g_y, kOut}, MatBias{n->h4, kHidden, kHidden},
                  EpAtomic{n->grads + L.off[5], L.ld(5)}, st, nl));
-    NET_TRY(gemm(B, kHidden, kOut, 1, Mat{n->g_y, kOut}, WN{n->wbf + L.off[5], L.ld(5)}, EpStore{n->g_h4, kHidden},
+    NET_TRY(gemm(B, kHidden, kOut, 1, Mat{n->g_y, kOut}, WN{n->wbf + L.offp[5], L.ldp(5)}, EpStore{n->g_h4, kHidden},
                  st, nl));
     k_relu_mask<<<blocks_for((size_t)B * kHidden), 256, 0, st>>>(n->g_h4, n->h4, (size_t)B * kHidden);
     ++*nl;
@@ -685,7 +840,7 @@ apic_status apic_net_backward(apic_net* n, const float* target15, float* loss, v
     // dense 258 -> 256
     NET_TRY(gemm(kHidden, L.ld(4), B, split_for(B), MatT{n->g_h4, kHidden}, MatBias{n->hin, kHin, kHin},
                  EpAtomic{n->grads + L.off[4], L.ld(4)}, st, nl));
-    NET_TRY(gemm(B, kHin, kHidden, 1, Mat{n->g_h4, kHidden}, WN{n->wbf + L.off[4], L.ld(4)}, EpStore{n->g_hin, kHin},
+    NET_TRY(gemm(B, kHin, kHidden, 1, Mat{n->g_h4, kHidden}, WN{n->wbf + L.offp[4], L.ldp(4)}, EpStore{n->g_hin, kHin},
                  st, nl));
     // global mean
     k_gap_back<<<blocks_for((size_t)B * 64 * kC4), 256, 0, st>>>(n->g_hin, n->g_r[3], B, 64, kC4);
@@ -694,7 +849,7 @@ apic_status apic_net_backward(apic_net* n, const float* target15, float* loss, v
     // conv 128 -> 256 on 8 x 8
     NET_TRY(gemm(kC4, L.ld(3), B * 64, split_for(B * 64LL), ReluGradT<kC4>{n->g_r[3], n->r[3]},
                  ConvIn<8, kC3, __nv_bfloat16>{n->pool[2]}, EpAtomic{n->grads + L.off[3], L.ld(3)}, st, nl));
-    NET_TRY(gemm(B * 64, kC3, 9 * kC4, 1, DzShift<8, kC4>{n->g_r[3], n->r[3]}, WFlip<kC3, kC4>{n->wbf + L.off[3]},
+    NET_TRY(gemm(B * 64, kC3, 9 * kC4, 1, DzShift<8, kC4>{n->g_r[3], n->r[3]}, WFlip<kC3, kC4>{n->wbf + L.offp[3], L.ldp(3)},
                  EpStore{n->g_pool[2], kC3}, st, nl));
     k_maxpool_back<<<blocks_for((size_t)B * 64 * kC3), 256, 0, st>>>(n->g_pool[2], n->arg[2], n->g_r[2], B, 16, kC3);
     ++*nl;
@@ -702,7 +857,7 @@ apic_status apic_net_backward(apic_net* n, const float* target15, float* loss, v
     // conv 64 -> 128 on 16 x 16
     NET_TRY(gemm(kC3, L.ld(2), B * 256, split_for(B * 256LL), ReluGradT<kC3>{n->g_r[2], n->r[2]},
                  ConvIn<16, kC2, __nv_bfloat16>{n->pool[1]}, EpAtomic{n->grads + L.off[2], L.ld(2)}, st, nl));
-    NET_TRY(gemm(B * 256, kC2, 9 * kC3, 1, DzShift<16, kC3>{n->g_r[2], n->r[2]}, WFlip<kC2, kC3>{n->wbf + L.off[2]},
+    NET_TRY(gemm(B * 256, kC2, 9 * kC3, 1, DzShift<16, kC3>{n->g_r[2], n->r[2]}, WFlip<kC2, kC3>{n->wbf + L.offp[2], L.ldp(2)},
                  EpStore{n->g_pool[1], kC2}, st, nl));
     k_maxpool_back<<<blocks_for((size_t)B * 256 * kC2), 256, 0, st>>>(n->g_pool[1], n->arg[1], n->g_r[1], B, 32,
                                                                      kC2);
@@ -711,7 +866,7 @@ apic_status apic_net_backward(apic_net* n, const float* target15, float* loss, v
     // conv 32 -> 64 on 32 x 32
     NET_TRY(gemm(kC2, L.ld(1), B * 1024, split_for(B * 1024LL), ReluGradT<kC2>{n->g_r[1], n->r[1]},
                  ConvIn<32, kC1, __nv_bfloat16>{n->pool[0]}, EpAtomic{n->grads + L.off[1], L.ld(1)}, st, nl));
-    NET_TRY(gemm(B * 1024, kC1, 9 * kC2, 1, DzShift<32, kC2>{n->g_r[1], n->r[1]}, WFlip<kC1, kC2>{n->wbf + L.off[1]},
+    NET_TRY(gemm(B * 1024, kC1, 9 * kC2, 1, DzShift<32, kC2>{n->g_r[1], n->r[1]}, WFlip<kC1, kC2>{n->wbf + L.offp[1], L.ldp(1)},
                  EpStore{n->g_pool[0], kC1}, st, nl));
     k_maxpool_back<<<blocks_for((size_t)B * 1024 * kC1), 256, 0, st>>>(n->g_pool[0], n->arg[0], n->g_r[0], B, 64,
                                                                       kC1);
@@ -731,7 +886,7 @@ apic_status apic_net_adamw(apic_net* n, float lr, float beta1, float beta2, floa
     const size_t P = n->L.total;
     const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
     k_adamw<<<blocks_for(P), 256, 0, (cudaStream_t)stream>>>(n->params, n->grads, n->m, n->v, n->wbf, P, lr, beta1,
-                                                              beta2, eps, weight_decay, c1, c2);
+                                                              beta2, eps, weight_decay, c1, c2, n->L);
     ++n->launches;
     NET_TRY(cudaGetLastError());
     return APIC_OK;
