@@ -360,7 +360,8 @@ apic_status apic_paste_fields(apic_plan* plan, int n_tiles, const float* d_field
  * the field-dependent Noll coefficients 4..15 of a tile from the magnitudes of
  * its NA-matching intensity spectra and its position, replaces the solve on
  * low-contrast tiles (where Eq. 10 is ill-conditioned) and warm-starts it
- * elsewhere; the closed-form solve stays the fallback and the judge.
+ * elsewhere; the closed-form solve stays the fallback and decides, by its
+ * residual, which of the two solutions a solved tile keeps.
  *
  * Input features, per tile: feat [64][64][8] float32 (NHWC), channel i =
  *   log(|F(I_i)(kx, ky)| / |F(I_i)(0, 0)| + 1e-4) at [ky + 32][kx + 32],

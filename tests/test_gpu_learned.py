@@ -5,7 +5,7 @@ simulated tiles whose coefficients follow a fixed field-dependent table plus
 a per-tile defocus offset, 30 % of them near-blank. On fresh tiles from the
 same slide model the closed-form-only reconstruction is compared with the
 learned one (warm start on solved tiles, replacement on low-contrast tiles),
-both judged against the true coefficients.
+both compared with the true coefficients.
 """
 import time
 
@@ -89,6 +89,6 @@ def test_learned_reconstruction_beats_closed_form_on_background(trained):
     # replacement: much better than the ill-conditioned closed form on background tiles
     assert np.median(e_l[blank]) < 0.5 * np.median(e_cf[blank])
     assert np.median(e_l[blank]) < 0.25
-    # warm start: the residual judge keeps the closed-form quality elsewhere
+    # warm start: the residual comparison keeps the closed-form quality elsewhere
     assert np.median(e_l[fg]) <= np.median(e_cf[fg]) + 0.01
     assert np.all(np.isfinite(z_l))
