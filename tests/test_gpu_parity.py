@@ -448,3 +448,29 @@ def test_background_statistic_matches_oracle():
         assert abs(got[t] - ref) <= 1e-6 + 1e-4 * ref, (t, got[t], ref)
         assert bool(s[t] & apic.APIC_TILE_BACKGROUND) == (ref < 0.02 ** 2)
     assert (s & apic.APIC_TILE_BACKGROUND).any() and not (s & apic.APIC_TILE_BACKGROUND).all()
+
+
+def test_reconstruct_host_with_partial_waves_matches_device_path():
+    """The host-buffer pipeline over chunks that contain partial darkfield waves
+    (second stream forked from its compute stream) returns the device result bit
+    for bit."""
+    n, T = 64, 1000
+    plan = new_plan(n, max_tiles=T)
+    from paper_2407_20469_gb300 import learn
+    zern = torch.zeros((T, 15), dtype=torch.float32, device="cuda")
+    zern[:, 3:] = torch.as_tensor(np.resize(np.linspace(-0.4, 0.4, 12, dtype=np.float32), (T, 12)), device="cuda")
+    obj = learn.device_objects(T, 2 * n, 33, "cuda")
+    I = torch.empty((T, 24, n, n), dtype=torch.float32, device="cuda")
+    plan.simulate(T, obj, zern, 1e4, 33, I)
+    H = plan.info.out_h
+    f_d = torch.empty((T, H, 2 * H), dtype=torch.float32, device="cuda")
+    z_d = torch.empty((T, 15), dtype=torch.float32, device="cuda")
+    s_d = torch.empty(T, dtype=torch.int32, device="cuda")
+    plan.reconstruct_batch(T, I, f_d, z_d, None, s_d)
+    Ih = I.cpu().pin_memory()
+    f_h = torch.empty(f_d.shape, dtype=torch.float32).pin_memory()
+    z_h = torch.empty(z_d.shape, dtype=torch.float32).pin_memory()
+    s_h = torch.empty(s_d.shape, dtype=torch.int32).pin_memory()
+    plan.reconstruct_host(T, Ih, f_h, z_h, s_h)
+    torch.cuda.synchronize()
+    assert torch.equal(s_h, s_d.cpu()) and torch.equal(z_h, z_d.cpu()) and torch.equal(f_h, f_d.cpu())
