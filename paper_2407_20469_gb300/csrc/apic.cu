@@ -112,7 +112,7 @@ struct apic_plan {
     int grid_kkr = 0;
     // second stream for the last partial darkfield wave of a batch (see reconstruct)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr, ev_pre = nullptr;
     float* feat = nullptr;                       // learned path: features, network coefficients
     float* c_net = nullptr;
     unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
@@ -392,6 +392,8 @@ apic_status alloc_workspace(apic_plan* p) {
     APIC_TRY_CUDA(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, greatest));
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_tail, cudaEventDisableTiming));
+    APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_pre, cudaEventDisableTiming));
     return APIC_OK;
 }
 
@@ -408,15 +410,19 @@ cudaError_t launch_kk_any(apic_plan* p, int blocks, int n_tiles, const float* I,
 // Darkfield blocks of one full wave (the grid of the selected kernel).
 int df_wave(const apic_plan* p) { return std::max(1, p->use_reg ? p->grid_dfr : p->L.grid_df); }
 
-// Darkfield stage on the tiles whose phase table starts at phi; `second` selects the
-// second wave of scratch blocks (for a launch that runs beside another one).
+// Darkfield stage on the tiles whose phase table starts at phi, on `grid` blocks
+// (<= 0: a full wave); `second` selects the second wave of scratch blocks (for a
+// launch that runs beside another one).
 cudaError_t launch_df_on(apic_plan* p, int n_tiles, const float* I, const float* phi, float2* spec, int32_t* status,
-                         bool second, cudaStream_t st) {
+                         bool second, cudaStream_t st, int grid = 0) {
     char* scratch = (char*)p->df_scratch + (second ? (size_t)df_wave(p) * p->df_per_block : 0);
+    const int g = grid > 0 ? std::min(grid, df_wave(p)) : df_wave(p);
     if (p->use_reg)
-        return launch_darkfield_reg(p->dev, p->grid_dfr, p->smem_dfr, n_tiles, I, phi, spec, scratch,
-                                    p->df_per_block, p->df_iters, p->df_tol, status, p->d_counters, st);
-    return launch_darkfield(p->dev, p->L, n_tiles, I, phi, spec, scratch, p->df_per_block, p->df_iters, p->df_tol,
+        return launch_darkfield_reg(p->dev, g, p->smem_dfr, n_tiles, I, phi, spec, scratch, p->df_per_block,
+                                    p->df_iters, p->df_tol, status, p->d_counters, st);
+    Launch L = p->L;
+    L.grid_df = g;
+    return launch_darkfield(p->dev, L, n_tiles, I, phi, spec, scratch, p->df_per_block, p->df_iters, p->df_tol,
                             status, p->d_counters, st);
 }
 
@@ -490,8 +496,11 @@ apic_status learned_buffers(apic_plan* p) {
 // round leaves SMs idle. When nt is not a multiple of W, the r = nt mod W
 // trailing tiles go first: their earlier stages run, their darkfield solves
 // start on a high-priority second stream (own scratch blocks), and meanwhile
-// the earlier stages of the other nt - r tiles run on the remaining SMs,
-// followed by their darkfield launch; synthesis waits for both. Every tile
+// the earlier stages of the other tiles run on the remaining SMs. Those tiles
+// then go to two launches sized so that each block takes the same number of
+// tiles: W - r blocks on the caller's stream (they start right away) and r
+// blocks on the second stream (they start where the partial wave ends); the
+// first group's synthesis runs while the second group finishes. Every tile
 // gets exactly the computation of the plain order.
 apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, const float* I, const float* uv,
                         float* field, float* zern, float* pupil, int32_t* status, cudaStream_t st) {
@@ -535,45 +544,78 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             if (mark1) tm.mark(3, 1);
             return APIC_OK;
         };
-        // with several chunks a stage's interval spans from its first start to its last stop;
-        // in the split order the intervals of the stages before the darkfield overlap it
-        if (first) tm.mark(0, 0);
-        APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
-        if (last) tm.mark(0, 1);
-        if (net) {
-            APIC_TRY_LAUNCH(launch_features(D, plan->grid_kkr, nt, It, plan->feat, plan->kk_scratch, st));
+        // network coefficients of tiles [a, a + k) of the chunk (learned path)
+        auto learned_part = [&](int a, int k) -> apic_status {
+            if (!net || k == 0) return APIC_OK;
+            float* feat = plan->feat + (size_t)a * feature_floats();
+            APIC_TRY_LAUNCH(launch_features(D, plan->grid_kkr, k, It + (size_t)a * in_tile, feat, plan->kk_scratch,
+                                            st));
             const int nb = net_max_batch(net);
-            for (int b0 = 0; b0 < nt; b0 += nb) {
-                const int bn = std::min(nb, nt - b0);
+            for (int b0 = 0; b0 < k; b0 += nb) {
+                const int bn = std::min(nb, k - b0);
                 const long long before = net_launches(net);
-                APIC_TRY_CUDA(net_predict(net, bn, plan->feat + (size_t)b0 * feature_floats(),
-                                          uv + (size_t)(t0 + b0) * 2, plan->c_net + (size_t)b0 * APIC_N_ZERNIKE, st));
+                APIC_TRY_CUDA(net_predict(net, bn, feat + (size_t)b0 * feature_floats(),
+                                          uv + (size_t)(t0 + a + b0) * 2,
+                                          plan->c_net + (size_t)(a + b0) * APIC_N_ZERNIKE, st));
                 plan->launches += net_launches(net) - before;
             }
-        }
+            return APIC_OK;
+        };
+        // with several chunks a stage's interval spans from its first start to its last stop;
+        // in the split order the intervals of the stages overlap
         apic_status s;
+        float2* fld = (float2*)field + (size_t)t0 * out_tile;
         if (r > 0) {
-            // last partial wave first: its darkfield starts beside the others' earlier stages
+            // Tiles of the full waves split into MA = [0, ma) on W - r blocks and
+            // MB = [ma, m0) on r blocks (k tiles per block each); T = [m0, nt) is the
+            // partial wave. Caller's stream: T's earlier stages, then (fork) the full
+            // waves' background and earlier stages, MA's darkfield, synthesis of MA and
+            // T. Second stream: T's darkfield, then MB's darkfield and synthesis (join).
+            const int k = m0 / W, ma = (W - r) * k;
+            if (first) tm.mark(0, 0);
+            APIC_TRY_LAUNCH(launch_background(D, r, It + (size_t)m0 * in_tile, plan->c2 + m0, stt + m0, thresh2, st,
+                                              replace ? 1 : 0));
+            if ((s = learned_part(m0, r)) != APIC_OK) return s;
             if ((s = pre_df(m0, r)) != APIC_OK) return s;
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_fork, st));
             if (first) tm.mark(4, 0);
             APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
             APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)m0 * in_tile, plan->phi + (size_t)m0 * D.npup,
-                                         plan->spec + (size_t)m0 * D.nap, stt + m0, true, plan->side));
-            APIC_TRY_CUDA(cudaEventRecord(plan->ev_join, plan->side));
+                                         plan->spec + (size_t)m0 * D.nap, stt + m0, true, plan->side, r));
+            APIC_TRY_CUDA(cudaEventRecord(plan->ev_tail, plan->side));
+            APIC_TRY_LAUNCH(launch_background(D, m0, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
+            if (last) tm.mark(0, 1);
+            if ((s = learned_part(0, m0)) != APIC_OK) return s;
             if ((s = pre_df(0, m0)) != APIC_OK) return s;
-            APIC_TRY_LAUNCH(launch_df_on(plan, m0, It, plan->phi, plan->spec, stt, false, st));
+            APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
+            APIC_TRY_LAUNCH(launch_df_on(plan, ma, It, plan->phi, plan->spec, stt, false, st, W - r));
+            APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_pre, 0));
+            APIC_TRY_LAUNCH(launch_df_on(plan, m0 - ma, It + (size_t)ma * in_tile, plan->phi + (size_t)ma * D.npup,
+                                         plan->spec + (size_t)ma * D.nap, stt + ma, true, plan->side, r));
+            APIC_TRY_LAUNCH(launch_synthesize(D, L, m0 - ma, plan->spec + (size_t)ma * D.nap,
+                                              fld + (size_t)ma * out_tile, stt + ma, plan->side));
+            APIC_TRY_CUDA(cudaEventRecord(plan->ev_join, plan->side));
+            APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_tail, 0));
+            if (first) tm.mark(5, 0);
+            APIC_TRY_LAUNCH(launch_synthesize(D, L, ma, plan->spec, fld, stt, st));
+            APIC_TRY_LAUNCH(launch_synthesize(D, L, r, plan->spec + (size_t)m0 * D.nap, fld + (size_t)m0 * out_tile,
+                                              stt + m0, st));
             APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_join, 0));
             if (last) tm.mark(4, 1);
+            if (last) tm.mark(5, 1);
         } else {
+            if (first) tm.mark(0, 0);
+            APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
+            if (last) tm.mark(0, 1);
+            if ((s = learned_part(0, nt)) != APIC_OK) return s;
             if ((s = pre_df(0, nt)) != APIC_OK) return s;
             if (first) tm.mark(4, 0);
             APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
             if (last) tm.mark(4, 1);
+            if (first) tm.mark(5, 0);
+            APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, fld, stt, st));
+            if (last) tm.mark(5, 1);
         }
-        if (first) tm.mark(5, 0);
-        APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, (float2*)field + (size_t)t0 * out_tile, stt, st));
-        if (last) tm.mark(5, 1);
         if (first) tm.mark(6, 0);
         if (pupil)
             APIC_TRY_LAUNCH(launch_pupil(D, nt, plan->phi, (float2*)pupil + (size_t)t0 * D.h * D.w, stt, st));
@@ -686,6 +728,8 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         if (plan->side) cudaStreamDestroy(plan->side);
         if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
         if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+        if (plan->ev_tail) cudaEventDestroy(plan->ev_tail);
+        if (plan->ev_pre) cudaEventDestroy(plan->ev_pre);
         if (plan->io.ready) {
             for (int b = 0; b < 2; ++b) {
                 cudaEventDestroy(plan->io.in_done[b]);
