@@ -101,6 +101,7 @@ struct apic_plan {
         int chunk = 0;
         cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
         cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
+        cudaEvent_t in_tail = nullptr, early = nullptr;   // one-chunk order
         float* d_in[2] = {};
         float* d_field[2] = {};
         float* d_zern[2] = {};
@@ -488,6 +489,23 @@ apic_status learned_buffers(apic_plan* p) {
     return APIC_OK;
 }
 
+// Where the host pipeline joins the order of one chunk (reconstruct): wait_main
+// is waited on before the first stage of the full waves' tiles, early_done is
+// recorded once the fields of tiles [0, ma) and [m0, nt) are synthesized.
+struct SplitHooks {
+    cudaEvent_t wait_main = nullptr;
+    cudaEvent_t early_done = nullptr;
+};
+
+// Partial-wave geometry of a chunk of nt tiles: r trailing tiles (0: no split),
+// m0 = nt - r, and ma, the full waves' tiles that go to the W - r blocks.
+void split_geometry(const apic_plan* p, int nt, int& r, int& m0, int& ma) {
+    const int W = df_wave(p);
+    r = (p->dev.n_used > 0 && nt > W) ? nt % W : 0;
+    m0 = nt - r;
+    ma = r > 0 ? (W - r) * (m0 / W) : m0;
+}
+
 // Background, Kramers-Kronig, aberration (learned when `net`), stitching,
 // darkfield, synthesis and pupil over chunks of max_tiles tiles.
 //
@@ -503,7 +521,8 @@ apic_status learned_buffers(apic_plan* p) {
 // first group's synthesis runs while the second group finishes. Every tile
 // gets exactly the computation of the plain order.
 apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, const float* I, const float* uv,
-                        float* field, float* zern, float* pupil, int32_t* status, cudaStream_t st) {
+                        float* field, float* zern, float* pupil, int32_t* status, cudaStream_t st,
+                        const SplitHooks* hk = nullptr) {
     const DevPlan& D = plan->dev;
     const Launch& L = plan->L;
     const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
@@ -518,8 +537,8 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
         const float* It = I + (size_t)t0 * in_tile;
         int32_t* stt = status ? status + t0 : plan->status;
         float* zt = zern + (size_t)t0 * APIC_N_ZERNIKE;
-        const int r = (D.n_used > 0 && nt > W) ? nt % W : 0;      // tiles of the last partial wave
-        const int m0 = nt - r;                                      // tiles of the full waves
+        int r = 0, m0 = nt, ma = nt;     // partial-wave tiles, full-wave tiles, their first group
+        split_geometry(plan, nt, r, m0, ma);
         // earlier stages of tiles [a, a + k) of the chunk; in the split order this runs
         // for the partial wave (a = m0) and then for the full waves (a = 0), so a stage's
         // interval starts with the first call and ends with the call for a = 0
@@ -571,7 +590,6 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             // partial wave. Caller's stream: T's earlier stages, then (fork) the full
             // waves' background and earlier stages, MA's darkfield, synthesis of MA and
             // T. Second stream: T's darkfield, then MB's darkfield and synthesis (join).
-            const int k = m0 / W, ma = (W - r) * k;
             if (first) tm.mark(0, 0);
             APIC_TRY_LAUNCH(launch_background(D, r, It + (size_t)m0 * in_tile, plan->c2 + m0, stt + m0, thresh2, st,
                                               replace ? 1 : 0));
@@ -583,6 +601,7 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)m0 * in_tile, plan->phi + (size_t)m0 * D.npup,
                                          plan->spec + (size_t)m0 * D.nap, stt + m0, true, plan->side, r));
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_tail, plan->side));
+            if (hk && hk->wait_main) APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
             APIC_TRY_LAUNCH(launch_background(D, m0, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
             if (last) tm.mark(0, 1);
             if ((s = learned_part(0, m0)) != APIC_OK) return s;
@@ -600,10 +619,12 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             APIC_TRY_LAUNCH(launch_synthesize(D, L, ma, plan->spec, fld, stt, st));
             APIC_TRY_LAUNCH(launch_synthesize(D, L, r, plan->spec + (size_t)m0 * D.nap, fld + (size_t)m0 * out_tile,
                                               stt + m0, st));
+            if (hk && hk->early_done) APIC_TRY_CUDA(cudaEventRecord(hk->early_done, st));
             APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_join, 0));
             if (last) tm.mark(4, 1);
             if (last) tm.mark(5, 1);
         } else {
+            if (hk && hk->wait_main) APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
             if (first) tm.mark(0, 0);
             APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
             if (last) tm.mark(0, 1);
@@ -614,6 +635,7 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             if (last) tm.mark(4, 1);
             if (first) tm.mark(5, 0);
             APIC_TRY_LAUNCH(launch_synthesize(D, L, nt, plan->spec, fld, stt, st));
+            if (hk && hk->early_done) APIC_TRY_CUDA(cudaEventRecord(hk->early_done, st));
             if (last) tm.mark(5, 1);
         }
         if (first) tm.mark(6, 0);
@@ -736,6 +758,8 @@ apic_status apic_plan_destroy(apic_plan* plan) {
                 cudaEventDestroy(plan->io.comp_done[b]);
                 cudaEventDestroy(plan->io.out_done[b]);
             }
+            cudaEventDestroy(plan->io.in_tail);
+            cudaEventDestroy(plan->io.early);
             cudaStreamDestroy(plan->io.s_in);
             cudaStreamDestroy(plan->io.s_comp);
             cudaStreamDestroy(plan->io.s_out);
@@ -1017,6 +1041,8 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
         APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_in, cudaStreamNonBlocking));
         APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_comp, cudaStreamNonBlocking));
         APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_out, cudaStreamNonBlocking));
+        APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.in_tail, cudaEventDisableTiming));
+        APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.early, cudaEventDisableTiming));
         for (int b = 0; b < 2; ++b) {
             APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.in_done[b], cudaEventDisableTiming));
             APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.comp_done[b], cudaEventDisableTiming));
@@ -1027,6 +1053,50 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
             if ((s = dmalloc(plan, (void**)&io.d_status[b], C * sizeof(int32_t))) != APIC_OK) return s;
         }
         io.ready = true;
+    }
+    if (n_tiles <= io.chunk) {
+        // One chunk, copies woven into its order: the partial darkfield wave's
+        // inputs go first and its stages start while the other inputs copy; the
+        // fields of the tiles synthesized early copy out while the last darkfield
+        // group finishes.
+        int r = 0, m0 = n_tiles, ma = n_tiles;
+        split_geometry(plan, n_tiles, r, m0, ma);
+        float* dI = io.d_in[0];
+        float* dF = io.d_field[0];
+        const size_t fbytes = out_tile * sizeof(float2);
+        if (r > 0) {
+            APIC_TRY_CUDA(cudaMemcpyAsync(dI + (size_t)m0 * in_tile, h_I + (size_t)m0 * in_tile,
+                                          (size_t)r * in_tile * sizeof(float), cudaMemcpyHostToDevice, io.s_in));
+            APIC_TRY_CUDA(cudaEventRecord(io.in_tail, io.s_in));
+        }
+        APIC_TRY_CUDA(cudaMemcpyAsync(dI, h_I, (size_t)m0 * in_tile * sizeof(float), cudaMemcpyHostToDevice,
+                                      io.s_in));
+        APIC_TRY_CUDA(cudaEventRecord(io.in_done[0], io.s_in));
+        APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_comp, r > 0 ? io.in_tail : io.in_done[0], 0));
+        SplitHooks hk;
+        hk.wait_main = r > 0 ? io.in_done[0] : nullptr;
+        hk.early_done = io.early;
+        s = reconstruct(plan, nullptr, 0, n_tiles, dI, nullptr, dF, io.d_zern[0], nullptr, io.d_status[0], io.s_comp,
+                        &hk);
+        if (s != APIC_OK) return s;
+        APIC_TRY_CUDA(cudaEventRecord(io.comp_done[0], io.s_comp));
+        APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.early, 0));
+        APIC_TRY_CUDA(cudaMemcpyAsync(h_field, dF, (size_t)ma * fbytes, cudaMemcpyDeviceToHost, io.s_out));
+        if (r > 0)
+            APIC_TRY_CUDA(cudaMemcpyAsync(h_field + (size_t)m0 * out_tile * 2, dF + (size_t)m0 * out_tile * 2,
+                                          (size_t)r * fbytes, cudaMemcpyDeviceToHost, io.s_out));
+        APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.comp_done[0], 0));
+        if (m0 > ma)
+            APIC_TRY_CUDA(cudaMemcpyAsync(h_field + (size_t)ma * out_tile * 2, dF + (size_t)ma * out_tile * 2,
+                                          (size_t)(m0 - ma) * fbytes, cudaMemcpyDeviceToHost, io.s_out));
+        APIC_TRY_CUDA(cudaMemcpyAsync(h_zern, io.d_zern[0], (size_t)n_tiles * APIC_N_ZERNIKE * sizeof(float),
+                                      cudaMemcpyDeviceToHost, io.s_out));
+        if (h_status)
+            APIC_TRY_CUDA(cudaMemcpyAsync(h_status, io.d_status[0], (size_t)n_tiles * sizeof(int32_t),
+                                          cudaMemcpyDeviceToHost, io.s_out));
+        APIC_TRY_CUDA(cudaStreamSynchronize(io.s_out));
+        APIC_TRY_CUDA(cudaStreamSynchronize(io.s_comp));
+        return APIC_OK;
     }
     int k = 0;
     for (int t0 = 0, nt = 0; t0 < n_tiles; t0 += nt, ++k) {

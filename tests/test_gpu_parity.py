@@ -474,3 +474,30 @@ def test_reconstruct_host_with_partial_waves_matches_device_path():
     plan.reconstruct_host(T, Ih, f_h, z_h, s_h)
     torch.cuda.synchronize()
     assert torch.equal(s_h, s_d.cpu()) and torch.equal(z_h, z_d.cpu()) and torch.equal(f_h, f_d.cpu())
+
+
+def test_reconstruct_host_one_chunk_split_matches_device_path():
+    """One chunk (n_tiles <= the pipeline chunk) with a partial darkfield wave: the
+    inputs copy in two parts and the fields out in two parts around the split
+    order; the result equals the device path bit for bit."""
+    n, T = 64, 500
+    plan = new_plan(n, max_tiles=T)
+    from paper_2407_20469_gb300 import learn
+    zern = torch.zeros((T, 15), dtype=torch.float32, device="cuda")
+    zern[:, 3:] = torch.as_tensor(np.resize(np.linspace(0.3, -0.3, 12, dtype=np.float32), (T, 12)), device="cuda")
+    obj = learn.device_objects(T, 2 * n, 44, "cuda")
+    I = torch.empty((T, 24, n, n), dtype=torch.float32, device="cuda")
+    plan.simulate(T, obj, zern, 1e4, 44, I)
+    H = plan.info.out_h
+    f_d = torch.empty((T, H, 2 * H), dtype=torch.float32, device="cuda")
+    z_d = torch.empty((T, 15), dtype=torch.float32, device="cuda")
+    s_d = torch.empty(T, dtype=torch.int32, device="cuda")
+    plan.reconstruct_batch(T, I, f_d, z_d, None, s_d)
+    Ih = I.cpu().pin_memory()
+    f_h = torch.full(f_d.shape, 5.0, dtype=torch.float32).pin_memory()
+    z_h = torch.empty(z_d.shape, dtype=torch.float32).pin_memory()
+    s_h = torch.empty(s_d.shape, dtype=torch.int32).pin_memory()
+    for _ in range(2):                                   # twice: buffers and events reused
+        plan.reconstruct_host(T, Ih, f_h, z_h, s_h)
+        torch.cuda.synchronize()
+        assert torch.equal(s_h, s_d.cpu()) and torch.equal(z_h, z_d.cpu()) and torch.equal(f_h, f_d.cpu())
