@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-assisted timing")
+    ap.add_argument("--per-tile", type=int, default=32,
+                    help="tiles timed one call at a time for the unbatched comparison (0: skip)")
     ap.add_argument("--images", choices=["8+16", "8+24"], default="8+16",
                     help="illumination set (8+24: rings at NA 0.29 / 0.34 / 0.40)")
     ap.add_argument("--seed", type=int, default=2407)
@@ -344,6 +346,24 @@ def gpu_arm(args):
         ms = float(t.item())
     status_np = status.cpu().numpy()
 
+    # ---- the same library called one tile at a time (no batching, no persistence
+    # across tiles): what the batched launch buys on this workload
+    per_tile = None
+    if args.per_tile > 0:
+        k = min(args.per_tile, T)
+        plan.reconstruct_batch(1, I[0:1], field[0:1], zern[0:1], None, status[0:1])
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for t in range(k):
+            plan.reconstruct_batch(1, I[t:t + 1], field[t:t + 1], zern[t:t + 1], None, status[t:t + 1])
+        c1.record(stream)
+        torch.cuda.synchronize()
+        pt_ms = c0.elapsed_time(c1)
+        pt_value = k * H * H / (pt_ms / 1e3) / 1e6
+        per_tile = {"value": pt_value, "unit": "Mpx/s", "tiles": k, "ms_per_tile": pt_ms / k,
+                    "batched_over_per_tile": None}
+
     # ---- learned-assisted reconstruction on the same inputs: a network trained
     # here for a few seconds on simulated tiles, warm-starting the aberration
     # solve (features + network forward + second refinement inside the timing)
@@ -434,6 +454,9 @@ def gpu_arm(args):
     }
     if learned is not None:
         line["learned"] = learned
+    if per_tile is not None:
+        per_tile["batched_over_per_tile"] = value / per_tile["value"]
+        line["per_tile_calls"] = per_tile
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         I1, g1, k1, ill1 = oracle_tile_sample(n, args.seed)
         res, secs = run_oracle(I1, g1, k1, ill1.n_bf)
