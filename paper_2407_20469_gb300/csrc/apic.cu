@@ -752,18 +752,17 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         if (plan->ev_join) cudaEventDestroy(plan->ev_join);
         if (plan->ev_tail) cudaEventDestroy(plan->ev_tail);
         if (plan->ev_pre) cudaEventDestroy(plan->ev_pre);
-        if (plan->io.ready) {
-            for (int b = 0; b < 2; ++b) {
-                cudaEventDestroy(plan->io.in_done[b]);
-                cudaEventDestroy(plan->io.comp_done[b]);
-                cudaEventDestroy(plan->io.out_done[b]);
-            }
-            cudaEventDestroy(plan->io.in_tail);
-            cudaEventDestroy(plan->io.early);
-            cudaStreamDestroy(plan->io.s_in);
-            cudaStreamDestroy(plan->io.s_comp);
-            cudaStreamDestroy(plan->io.s_out);
+        auto& io = plan->io;
+        for (int b = 0; b < 2; ++b) {
+            if (io.in_done[b]) cudaEventDestroy(io.in_done[b]);
+            if (io.comp_done[b]) cudaEventDestroy(io.comp_done[b]);
+            if (io.out_done[b]) cudaEventDestroy(io.out_done[b]);
         }
+        if (io.in_tail) cudaEventDestroy(io.in_tail);
+        if (io.early) cudaEventDestroy(io.early);
+        if (io.s_in) cudaStreamDestroy(io.s_in);
+        if (io.s_comp) cudaStreamDestroy(io.s_comp);
+        if (io.s_out) cudaStreamDestroy(io.s_out);
     }
     delete plan;
     return APIC_OK;
@@ -1036,21 +1035,34 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
     const int wave = df_wave(plan);
     const int max_chunk = std::max(1, std::min(plan->max_tiles, 4 * wave));
     if (!io.ready) {
+        // each object is made once: a set-up that failed part way resumes where it stopped
         io.chunk = max_chunk;
         const size_t C = (size_t)io.chunk;
-        APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_in, cudaStreamNonBlocking));
-        APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_comp, cudaStreamNonBlocking));
-        APIC_TRY_CUDA(cudaStreamCreateWithFlags(&io.s_out, cudaStreamNonBlocking));
-        APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.in_tail, cudaEventDisableTiming));
-        APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.early, cudaEventDisableTiming));
+        auto stream = [](cudaStream_t& x) {
+            return x ? cudaSuccess : cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+        };
+        auto event = [](cudaEvent_t& x) {
+            return x ? cudaSuccess : cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        };
+        APIC_TRY_CUDA(stream(io.s_in));
+        APIC_TRY_CUDA(stream(io.s_comp));
+        APIC_TRY_CUDA(stream(io.s_out));
+        APIC_TRY_CUDA(event(io.in_tail));
+        APIC_TRY_CUDA(event(io.early));
         for (int b = 0; b < 2; ++b) {
-            APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.in_done[b], cudaEventDisableTiming));
-            APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.comp_done[b], cudaEventDisableTiming));
-            APIC_TRY_CUDA(cudaEventCreateWithFlags(&io.out_done[b], cudaEventDisableTiming));
-            if ((s = dmalloc(plan, (void**)&io.d_in[b], C * in_tile * sizeof(float))) != APIC_OK) return s;
-            if ((s = dmalloc(plan, (void**)&io.d_field[b], C * out_tile * sizeof(float2))) != APIC_OK) return s;
-            if ((s = dmalloc(plan, (void**)&io.d_zern[b], C * APIC_N_ZERNIKE * sizeof(float))) != APIC_OK) return s;
-            if ((s = dmalloc(plan, (void**)&io.d_status[b], C * sizeof(int32_t))) != APIC_OK) return s;
+            APIC_TRY_CUDA(event(io.in_done[b]));
+            APIC_TRY_CUDA(event(io.comp_done[b]));
+            APIC_TRY_CUDA(event(io.out_done[b]));
+            if (!io.d_in[b] && (s = dmalloc(plan, (void**)&io.d_in[b], C * in_tile * sizeof(float))) != APIC_OK)
+                return s;
+            if (!io.d_field[b] &&
+                (s = dmalloc(plan, (void**)&io.d_field[b], C * out_tile * sizeof(float2))) != APIC_OK)
+                return s;
+            if (!io.d_zern[b] &&
+                (s = dmalloc(plan, (void**)&io.d_zern[b], C * APIC_N_ZERNIKE * sizeof(float))) != APIC_OK)
+                return s;
+            if (!io.d_status[b] && (s = dmalloc(plan, (void**)&io.d_status[b], C * sizeof(int32_t))) != APIC_OK)
+                return s;
         }
         io.ready = true;
     }
