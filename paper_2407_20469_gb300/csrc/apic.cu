@@ -193,30 +193,64 @@ apic_status upload(apic_plan* plan) {
         e.N = (int)d.U_x.size();
         e.M = (int)d.Q_x.size();
         e.NP = (int)d.P_x.size();
+        // Solve frame: an image whose lag set is narrower along x than along y is
+        // solved transposed (x <-> y in every set and in the image), so the row
+        // bands the darkfield passes walk are the shorter ones. The problem is
+        // symmetric under the swap; points are re-sorted by their new rows.
+        auto extent = [](const std::vector<int>& v) {
+            return v.empty() ? 0 : *std::max_element(v.begin(), v.end()) - *std::min_element(v.begin(), v.end()) + 1;
+        };
+        const bool tr = extent(d.Q_x) < extent(d.Q_y);
+        e.tr = tr ? 1 : 0;
+        struct Set {
+            std::vector<int> x, y, pup, ap;
+        };
+        auto frame = [&](const std::vector<int>& xs, const std::vector<int>& ys, const std::vector<int>* pup,
+                         const std::vector<int>* ap) {
+            const std::vector<int>& fx = tr ? ys : xs;
+            const std::vector<int>& fy = tr ? xs : ys;
+            std::vector<size_t> idx(xs.size());
+            for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+            if (tr)
+                std::stable_sort(idx.begin(), idx.end(), [&](size_t i, size_t j) {
+                    return fy[i] != fy[j] ? fy[i] < fy[j] : fx[i] < fx[j];
+                });
+            Set S;
+            for (size_t i : idx) {
+                S.x.push_back(fx[i]);
+                S.y.push_back(fy[i]);
+                if (pup) S.pup.push_back((*pup)[i]);
+                if (ap) S.ap.push_back((*ap)[i]);
+            }
+            return S;
+        };
+        const Set Us = frame(d.U_x, d.U_y, &d.U_pup, &d.U_ap);
+        const Set Ps = frame(d.P_x, d.P_y, &d.P_pup, &d.P_ap);
+        const Set Qs = frame(d.Q_x, d.Q_y, nullptr, nullptr);
         e.u_off = (int)ux.size();
         e.p_off = (int)px.size();
         e.q_off = (int)qx.size();
-        ux.insert(ux.end(), d.U_x.begin(), d.U_x.end());
-        uy.insert(uy.end(), d.U_y.begin(), d.U_y.end());
-        up.insert(up.end(), d.U_pup.begin(), d.U_pup.end());
-        ua.insert(ua.end(), d.U_ap.begin(), d.U_ap.end());
-        px.insert(px.end(), d.P_x.begin(), d.P_x.end());
-        py.insert(py.end(), d.P_y.begin(), d.P_y.end());
-        pp.insert(pp.end(), d.P_pup.begin(), d.P_pup.end());
-        pa.insert(pa.end(), d.P_ap.begin(), d.P_ap.end());
-        qx.insert(qx.end(), d.Q_x.begin(), d.Q_x.end());
-        qy.insert(qy.end(), d.Q_y.begin(), d.Q_y.end());
+        ux.insert(ux.end(), Us.x.begin(), Us.x.end());
+        uy.insert(uy.end(), Us.y.begin(), Us.y.end());
+        up.insert(up.end(), Us.pup.begin(), Us.pup.end());
+        ua.insert(ua.end(), Us.ap.begin(), Us.ap.end());
+        px.insert(px.end(), Ps.x.begin(), Ps.x.end());
+        py.insert(py.end(), Ps.y.begin(), Ps.y.end());
+        pp.insert(pp.end(), Ps.pup.begin(), Ps.pup.end());
+        pa.insert(pa.end(), Ps.ap.begin(), Ps.ap.end());
+        qx.insert(qx.end(), Qs.x.begin(), Qs.x.end());
+        qy.insert(qy.end(), Qs.y.begin(), Qs.y.end());
         auto band = [](const std::vector<int>& ys, int& y0, int& y1) {
             y0 = *std::min_element(ys.begin(), ys.end());
             y1 = *std::max_element(ys.begin(), ys.end());
         };
-        band(d.U_y, e.uy0, e.uy1);
-        band(d.Q_y, e.qy0, e.qy1);
-        if (d.P_y.empty()) {
+        band(Us.y, e.uy0, e.uy1);
+        band(Qs.y, e.qy0, e.qy1);
+        if (Ps.y.empty()) {
             e.py0 = 0;
             e.py1 = -1;
         } else {
-            band(d.P_y, e.py0, e.py1);
+            band(Ps.y, e.py0, e.py1);
         }
         auto push_rp = [&](const std::vector<int>& ys, int y0, int y1) {
             const int off = (int)rp.size();
@@ -224,9 +258,9 @@ apic_status upload(apic_plan* plan) {
             rp.insert(rp.end(), v.begin(), v.end());
             return off;
         };
-        e.urp = push_rp(d.U_y, e.uy0, e.uy1);
-        e.qrp = push_rp(d.Q_y, e.qy0, e.qy1);
-        e.prp = push_rp(d.P_y, e.py0, e.py1);
+        e.urp = push_rp(Us.y, e.uy0, e.uy1);
+        e.qrp = push_rp(Qs.y, e.qy0, e.qy1);
+        e.prp = push_rp(Ps.y, e.py0, e.py1);
         maxN = std::max(maxN, e.N);
         maxM = std::max(maxM, e.M);
         band_u = std::max(band_u, e.uy1 - e.uy0 + 1);
@@ -236,9 +270,9 @@ apic_status upload(apic_plan* plan) {
         if (mr > 0) {   // Q membership per band row on the register grid
             const int words = mr / 32;
             qmask.resize(qmask.size() + (size_t)(e.qy1 - e.qy0 + 1) * words, 0u);
-            for (size_t q = 0; q < d.Q_x.size(); ++q) {
-                const int xi = ((d.Q_x[q] % mr) + mr) % mr;
-                qmask[e.qmask_off + (size_t)(d.Q_y[q] - e.qy0) * words + (xi >> 5)] |= 1u << (xi & 31);
+            for (size_t q = 0; q < Qs.x.size(); ++q) {
+                const int xi = ((Qs.x[q] % mr) + mr) % mr;
+                qmask[e.qmask_off + (size_t)(Qs.y[q] - e.qy0) * words + (xi >> 5)] |= 1u << (xi & 31);
             }
         }
         dfs.push_back(e);

@@ -19,6 +19,7 @@ struct DevDF {
     int uy0, uy1, qy0, qy1, py0, py1;  // band of rows (signed y) of each set
     int urp, qrp, prp;               // offsets into the concatenated row-pointer array
     int qmask_off;                   // offset of the Q-membership bit rows (register grid)
+    int tr;                          // 1: solved transposed (point sets and image with x <-> y)
 };
 
 struct DevPlan {

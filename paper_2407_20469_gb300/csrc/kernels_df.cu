@@ -78,9 +78,16 @@ __global__ void __launch_bounds__(kThreads) k_darkfield(DevPlan P, int n_tiles, 
             {
                 const int S = cn.S, ld = cn.ld, nbq = D.qy1 - D.qy0 + 1;
                 for (int c0 = 0; c0 < n; c0 += S) {
-                    for (int t = threadIdx.x; t < S * n; t += blockDim.x) {
-                        const int y = t / S, q = t - y * S;
-                        cn.a[q * ld + y] = make_float2(img[(size_t)y * n + c0 + q], 0.f);
+                    if (D.tr) {   // the transposed image (solve frame with x <-> y)
+                        for (int t = threadIdx.x; t < S * n; t += blockDim.x) {
+                            const int q = t / n, y = t - q * n;
+                            cn.a[q * ld + y] = make_float2(img[(size_t)(c0 + q) * n + y], 0.f);
+                        }
+                    } else {
+                        for (int t = threadIdx.x; t < S * n; t += blockDim.x) {
+                            const int y = t / S, q = t - y * S;
+                            cn.a[q * ld + y] = make_float2(img[(size_t)y * n + c0 + q], 0.f);
+                        }
                     }
                     const float2* R = fft_chunk<false>(cn);
                     for (int t = threadIdx.x; t < nbq * S; t += blockDim.x) {

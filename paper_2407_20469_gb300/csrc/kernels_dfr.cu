@@ -234,19 +234,27 @@ __device__ __noinline__ void pass_rows_mask(HW w, const float2* tw, float2* G, i
     __syncthreads();
 }
 
-// columns of the real image (n = 16 BN): forward along y, rows qy0.. (nQ) stored to GX
-// (row length n). Chunks of 32 columns staged through shared memory for coalesced
-// image reads; half-warps 0..31 transform them. Ends with __syncthreads.
+// columns of the real image (n = 16 BN; with tr the transposed image): forward along
+// y, rows qy0.. (nQ) stored to GX (row length n). Chunks of 32 columns staged through
+// shared memory for coalesced image reads; half-warps 0..31 transform them. Ends with
+// __syncthreads.
 template <int BN>
 __device__ __noinline__ void pass_image_cols(HW w, const float2* tw, float2* stage, const float* img, float2* GX,
-                                             int qy0, int nQ) {
+                                             int qy0, int nQ, bool tr) {
     constexpr int n = 16 * BN;
     const HalfWarp h = w.h();
     float* stage_f = reinterpret_cast<float*>(stage);
     for (int c0 = 0; c0 < n; c0 += 32) {
-        for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
-            const int y = idx >> 5, c = idx & 31;
-            stage_f[y * kStageLd + c] = img[(size_t)y * n + c0 + c];
+        if (tr) {   // image read transposed: column c of the solve frame is image row c
+            for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+                const int c = idx / n, y = idx - c * n;
+                stage_f[y * kStageLd + c] = img[(size_t)(c0 + c) * n + y];
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+                const int y = idx >> 5, c = idx & 31;
+                stage_f[y * kStageLd + c] = img[(size_t)y * n + c0 + c];
+            }
         }
         __syncthreads();
         float2 v[BN], o[16];
@@ -439,7 +447,7 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             const float* img = I + ((size_t)tile * P.n_img + D.led) * n * n;
 
             // b = F(I_j) on Q (setup transforms in the shared space of GU)
-            pass_image_cols<BN>(wn, tw_n, stage, img, PF, qy0, nQ);
+            pass_image_cols<BN>(wn, tw_n, stage, img, PF, qy0, nQ, D.tr != 0);
             pass_image_rows<BN>(wn, tw_n, PF, nQ, qrp, P.dQ_x + q_off, bq);
             // known field p (column-major in PF; its band rows staged in GQ), b -= P*P,
             // rows of b inverse along x
