@@ -227,6 +227,24 @@ apic_status upload(apic_plan* plan) {
         const Set Us = frame(d.U_x, d.U_y, &d.U_pup, &d.U_ap);
         const Set Ps = frame(d.P_x, d.P_y, &d.P_pup, &d.P_ap);
         const Set Qs = frame(d.Q_x, d.Q_y, nullptr, nullptr);
+        // Column grid of the register solve: the shortest supported length L on which
+        // both correlations of Eq. 13 are exact along y. C u (U with P, read on Q) has
+        // no alias when no q - p - k (q in U, p in P, k in Q) is a nonzero multiple of
+        // L, C^H r (Q with P, read on U) when no k + p - q is; every band must also fit.
+        e.by = mr / 16;
+        if (mr == 192 && !Us.y.empty() && !Ps.y.empty() && !Qs.y.empty()) {
+            auto mm = [](const std::vector<int>& v) { return std::minmax_element(v.begin(), v.end()); };
+            const auto u = mm(Us.y), pp = mm(Ps.y), q = mm(Qs.y);
+            const int u0 = *u.first, u1 = *u.second, p0 = *pp.first, p1 = *pp.second, q0 = *q.first, q1 = *q.second;
+            const int need_c = std::max(std::abs(u0 - p1 - q1), std::abs(u1 - p0 - q0)) + 1;
+            const int need_ch = std::max(std::abs(q0 + p0 - u1), std::abs(q1 + p1 - u0)) + 1;
+            const int need = std::max({need_c, need_ch, u1 - u0 + 1, p1 - p0 + 1, q1 - q0 + 1});
+            for (int cand : {6, 8, 9, 12})
+                if (16 * cand >= need) {
+                    e.by = cand;
+                    break;
+                }
+        }
         e.u_off = (int)ux.size();
         e.p_off = (int)px.size();
         e.q_off = (int)qx.size();
@@ -291,6 +309,7 @@ apic_status upload(apic_plan* plan) {
     const size_t o_qx = A.add(qx), o_qy = A.add(qy), o_rp = A.add(rp);
     const size_t o_twn = A.add(twiddles(H.h)), o_twm = A.add(twiddles(H.m)), o_twN = A.add(twiddles(H.H));
     const size_t o_twr = A.add(twiddles(std::max(mr, 16)));
+    const size_t o_ty6 = A.add(twiddles(96)), o_ty8 = A.add(twiddles(128)), o_ty9 = A.add(twiddles(144));
     const size_t o_qm = A.add(qmask);
 
     void* base = nullptr;
@@ -337,6 +356,9 @@ apic_status upload(apic_plan* plan) {
     D.tw_m = (const float2*)(b + o_twm);
     D.tw_N = (const float2*)(b + o_twN);
     D.tw_r = (const float2*)(b + o_twr);
+    D.tw_y6 = (const float2*)(b + o_ty6);
+    D.tw_y8 = (const float2*)(b + o_ty8);
+    D.tw_y9 = (const float2*)(b + o_ty9);
     D.d_qmask = (const unsigned*)(b + o_qm);
     return APIC_OK;
 }

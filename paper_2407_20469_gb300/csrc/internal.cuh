@@ -20,6 +20,7 @@ struct DevDF {
     int urp, qrp, prp;               // offsets into the concatenated row-pointer array
     int qmask_off;                   // offset of the Q-membership bit rows (register grid)
     int tr;                          // 1: solved transposed (point sets and image with x <-> y)
+    int by;                          // column grid of the solve: 16 by points (register kernel)
 };
 
 struct DevPlan {
@@ -68,6 +69,9 @@ struct DevPlan {
     const float2* tw_m;
     const float2* tw_N;              // N = H = W
     const float2* tw_r;              // mr
+    const float2* tw_y6;             // 96, 128, 144: shorter column grids of the register darkfield
+    const float2* tw_y8;
+    const float2* tw_y9;
 };
 
 // Scratch sizes and grids decided at plan creation.

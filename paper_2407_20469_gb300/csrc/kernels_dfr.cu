@@ -42,6 +42,16 @@ constexpr int kStageLd = 33;           // column stage: 32 columns + 1 pad
 
 __device__ __forceinline__ int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
 
+// Row of a band starting at signed row y0 that lives at grid index i of an m-point
+// axis (band row r sits at index (y0 + r) mod m); >= the band size when none.
+// Needs |y0| < m.
+__device__ __forceinline__ int band_row(int i, int y0, int m) {
+    int r = i - y0;
+    if (r >= m) r -= m;
+    if (r < 0) r += m;
+    return r;
+}
+
 struct HW {
     int t, hw;
     unsigned mask;
@@ -94,16 +104,21 @@ struct OutDot {         // w = C^H C d; returns Re <d, w>
 
 // ---- per-column mid operations (lanes t < B; o[k1] is the value at y = t + B k1)
 template <int B>
-struct MidKnownField {  // store p column-major, replace by |p|^2
+struct MidStoreField {  // store p column-major (16 B per column)
     float2* PF;
     static constexpr bool kReadsField = false;
     __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&)[16]) const {
         float2* col = PF + (size_t)x * (16 * B);
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) {
-            col[t + B * k1] = o[k1];
-            o[k1] = make_float2(cabs2(o[k1]), 0.f);
-        }
+        for (int k1 = 0; k1 < 16; ++k1) col[t + B * k1] = o[k1];
+    }
+};
+struct MidAbs2 {        // replace p by |p|^2
+    float2* PF = nullptr;
+    static constexpr bool kReadsField = false;
+    __device__ void operator()(float2 (&o)[16], int, int, const float2 (&)[16]) const {
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) o[k1] = make_float2(cabs2(o[k1]), 0.f);
     }
 };
 template <int B, bool CONJ>
@@ -171,22 +186,24 @@ __device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float
     return acc;
 }
 
-// columns: rows yi0.. (ni of them) of Gi (row stride ldi) are the input, the rest
-// zero; inverse along y, mid, forward along y; rows yo0.. (no) stored to Go (row
-// stride ldo). Each half-warp reads and writes its own columns, so Gi and Go may
-// be the same grid; the known-field values of the column are loaded after the
-// first transform. Ends with __syncthreads.
+// columns x < ncols of a grid whose columns have 16 B points: band rows yi0..
+// (ni of them, row r of the band at grid row (yi0 + r) mod 16 B) of Gi (row stride
+// ldi) are the input, the rest zero; inverse along y, mid, forward along y; band
+// rows yo0.. (no) stored to Go (row stride ldo; no = 0: nothing stored, no forward
+// transform). Each half-warp reads and writes its own columns, so Gi and Go may be
+// the same grid; the known-field values of the column are loaded after the first
+// transform. Ends with __syncthreads.
 template <int B, class Mid>
-__device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi, int ldi, int yi0, int ni,
+__device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
                                        float2* Go, int ldo, int yo0, int no, Mid mid) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
-    for (int x = w.hw; x < m; x += kHW) {
+    for (int x = w.hw; x < ncols; x += kHW) {
         float2 v[B], o[16], pf[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            const int bb = sfreq(w.t + 16 * j, m) - yi0;
-            v[j] = (bb >= 0 && bb < ni) ? Gi[(size_t)bb * ldi + x] : make_float2(0.f, 0.f);
+            const int bb = band_row(w.t + 16 * j, yi0, m);
+            v[j] = bb < ni ? Gi[(size_t)bb * ldi + x] : make_float2(0.f, 0.f);
         }
         fft_alpha<B, true>(v, o, h, tw);
         // the known field of the column, loaded once the inputs are consumed (loading it
@@ -198,11 +215,13 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, const float2* Gi,
             for (int k1 = 0; k1 < 16; ++k1) pf[k1] = col[w.t + B * k1];
         }
         if (w.t < B) mid(o, x, w.t, pf);
-        fft_beta<B, false>(o, v, h, tw);
+        if (no > 0) {
+            fft_beta<B, false>(o, v, h, tw);
 #pragma unroll
-        for (int k1 = 0; k1 < B; ++k1) {
-            const int bb = sfreq(w.t + 16 * k1, m) - yo0;
-            if (bb >= 0 && bb < no) Go[(size_t)bb * ldo + x] = v[k1];
+            for (int k1 = 0; k1 < B; ++k1) {
+                const int bb = band_row(w.t + 16 * k1, yo0, m);
+                if (bb < no) Go[(size_t)bb * ldo + x] = v[k1];
+            }
         }
     }
     __syncthreads();
@@ -375,6 +394,7 @@ __host__ __device__ inline DFRSmem dfr_smem_layout(int B, int BN, int band_u, in
     L.c = L.x + align16((size_t)max_N * sizeof(double2));
     size_t t = L.c + (size_t)3 * max_N * sizeof(float2);                   // d, s, w
     t += (size_t)2 * (m + n) * sizeof(float2);                            // step twiddles
+    t += (size_t)2 * m * sizeof(float2);                                  // column-grid step twiddles
     t = align16(t) + 64 * sizeof(double);                                 // reductions
     L.total = align16(t);
     return L;
@@ -394,43 +414,141 @@ size_t dfr_scratch_bytes(const DevPlan& P) {
     return (s + 255) & ~(size_t)255;
 }
 
+// Per-block working set of the darkfield kernel.
+struct DFCtx {
+    HW w;
+    const float2* tw_m;     // step twiddles of the rows (16 B points)
+    float2* tw_y;           // step twiddles of the image's column grid (filled per image)
+    float2 *GU, *GQ, *PF, *bq;
+    float2 *dv, *sv, *wv;
+    double2* xv;
+    double* red;
+};
+
+__device__ __forceinline__ const float2* column_table(const DevPlan& P, int BY, int B) {
+    return BY == B ? P.tw_r : BY == 6 ? P.tw_y6 : BY == 8 ? P.tw_y8 : P.tw_y9;
+}
+
+// Solve of one darkfield image once b = F(I) on Q is in bq: rows on the 16 B
+// grid, columns on a 16 BY grid (BY <= B, chosen at plan time as the shortest on
+// which both correlations of Eq. 13 are free of aliasing). P * P, whose lags reach
+// further, is formed on the 16 B grid. Returns the CG iterations (negative: did
+// not converge).
+template <int B, int BY>
+__device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const DevDF& D, float2* sp, const float* ph,
+                                     int iters, float tol) {
+    constexpr int m = 16 * B, my = 16 * BY, LDU = m + 1;
+    const HW& w = c.w;
+    const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
+    const int uy0 = D.uy0, qy0 = D.qy0, py0 = D.py0;
+    const int N = D.N, nU = D.uy1 - uy0 + 1, nQ = D.qy1 - qy0 + 1, nP = D.py1 - py0 + 1;
+    const int *urp = P.d_rowptr + D.urp, *qrp = P.d_rowptr + D.qrp, *prp = P.d_rowptr + D.prp;
+    const unsigned* qmask = P.d_qmask + D.qmask_off;
+    const float2* twc = c.tw_m;
+    if (BY != B) {
+        make_step_twiddles(c.tw_y, column_table(P, BY, B), BY);
+        twc = c.tw_y;
+    }
+    // band rows of the known field P (Eq. 11) along x, staged in GQ
+    pass_rows_in<B>(w, c.tw_m, c.GQ, m, nP, prp, P.dP_x + p_off,
+                    ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
+    __syncthreads();
+    // p on the column grid (column-major in PF), then b -= P * P on Q (16 B grid), rows of b inverse along x
+    pass_cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF});
+    pass_cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
+    pass_rows_rhs<B>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
+    const float scale = 1.f / ((float)m * (float)my);
+    // s = d = C^H b
+    pass_cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
+    const double g0 = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
+    int par = 0;
+    const double gamma0 = block_sum2(g0, c.red, par);
+    // CGNR
+    double gamma = gamma0;
+    bool conv = !(gamma0 > 1e-300);
+    const double stop = (double)tol * (double)tol * gamma0;
+    int it = 0;
+    float bf = 0.f;                  // first direction: d = s
+    for (; it < iters && !conv; ++it) {
+        pass_rows_in<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{c.sv, c.dv, bf});
+        __syncthreads();
+        pass_cols<BY>(w, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ, MidTimesField<BY, true>{c.PF, scale});
+        pass_rows_mask<B>(w, c.tw_m, c.GQ, nQ, qmask);
+        pass_cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
+        const double dw = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
+        const double delta = block_sum2(dw, c.red, par);
+        if (!(delta > 0)) break;
+        const double alpha = gamma / delta;
+        const float af = (float)alpha;
+        double g2 = 0;
+        for (int e = threadIdx.x; e < N; e += blockDim.x) {
+            const float2 d = c.dv[e];
+            double2 x = c.xv[e];
+            x.x += alpha * d.x;
+            x.y += alpha * d.y;
+            c.xv[e] = x;
+            const float2 sv = csub(c.sv[e], cscale(c.wv[e], af));
+            c.sv[e] = sv;
+            g2 += (double)sv.x * sv.x + (double)sv.y * sv.y;
+        }
+        const double gnew = block_sum2(g2, c.red, par);
+        bf = (float)(gnew / gamma);
+        gamma = gnew;
+        conv = gnew <= stop;
+    }
+    // corrected unknown spectrum into the tile's spectrum
+    const int* Upup = P.dU_pup + u_off;
+    const int* Uap = P.dU_ap + u_off;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        float sn, cs;
+        sincosf(ph[Upup[e]], &sn, &cs);
+        const double2 x = c.xv[e];
+        sp[Uap[e]] = cmul(make_float2((float)x.x, (float)x.y), make_float2(cs, -sn));
+    }
+    __syncthreads();
+    return conv ? it : -1 - it;
+}
+
 template <int B, int BN>
 __global__ void __launch_bounds__(kDFThreads, 1)
 k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
                 float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
                 int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
-    constexpr int m = 16 * B, n = 16 * BN, LDU = m + 1;
+    constexpr int m = 16 * B, n = 16 * BN;
     constexpr int HWM = HWSize<B>::value, HWN = HWSize<BN>::value;
     extern __shared__ float4 smem4[];
     char* sbase = reinterpret_cast<char*>(smem4);
     const DFRSmem SL = dfr_smem_layout(B, BN, P.band_u, P.band_q, P.max_N);
-    float2* GU = reinterpret_cast<float2*>(sbase + SL.gu);
+    DFCtx c;
+    c.GU = reinterpret_cast<float2*>(sbase + SL.gu);
     float2* stage = reinterpret_cast<float2*>(sbase + SL.stage);
-    float2* dv = reinterpret_cast<float2*>(sbase + SL.c);
-    float2* sv = dv + P.max_N;
-    float2* wv = sv + P.max_N;
-    float2* tw_m = wv + P.max_N;
+    c.dv = reinterpret_cast<float2*>(sbase + SL.c);
+    c.sv = c.dv + P.max_N;
+    c.wv = c.sv + P.max_N;
+    float2* tw_m = c.wv + P.max_N;
     float2* tw_n = tw_m + 2 * m;
-    double* red = reinterpret_cast<double*>(sbase + align16(SL.c + (size_t)3 * P.max_N * sizeof(float2) +
-                                                            (size_t)2 * (m + n) * sizeof(float2)));
+    c.tw_y = tw_n + 2 * n;
+    c.red = reinterpret_cast<double*>(sbase + align16(SL.c + (size_t)3 * P.max_N * sizeof(float2) +
+                                                      (size_t)2 * (m + n) * sizeof(float2) +
+                                                      (size_t)2 * m * sizeof(float2)));
+    c.tw_m = tw_m;
 
     make_step_twiddles(tw_m, P.tw_r, B);
     make_step_twiddles(tw_n, P.tw_n, BN);
     __syncthreads();
 
-    HW w, wn;                        // m-grid passes / image (n-grid) setup passes
-    w.hw = wn.hw = threadIdx.x >> 4;
-    w.t = wn.t = threadIdx.x & 15;
-    w.mask = wn.mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
-    w.hs = reinterpret_cast<float2*>(sbase) + w.hw * HWM;
-    wn.hs = reinterpret_cast<float2*>(sbase) + w.hw * HWN;
+    HW wn;                           // image (n-grid) setup passes
+    c.w.hw = wn.hw = threadIdx.x >> 4;
+    c.w.t = wn.t = threadIdx.x & 15;
+    c.w.mask = wn.mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
+    c.w.hs = reinterpret_cast<float2*>(sbase) + c.w.hw * HWM;
+    wn.hs = reinterpret_cast<float2*>(sbase) + c.w.hw * HWN;
 
-    double2* xv = reinterpret_cast<double2*>(sbase + SL.x);
+    c.xv = reinterpret_cast<double2*>(sbase + SL.x);
     char* base = scratch + (size_t)blockIdx.x * per_block;
-    float2* GQ = reinterpret_cast<float2*>(base);
-    float2* PF = GQ + (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m;   // column-major p, or F(I) rows
-    float2* bq = PF + (size_t)max(m * m, P.band_q * n);
-    const float inv_m2 = 1.f / (float)(m * m);
+    c.GQ = reinterpret_cast<float2*>(base);
+    c.PF = c.GQ + (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m;   // column-major p, or F(I) rows
+    c.bq = c.PF + (size_t)max(m * m, P.band_q * n);
 
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
@@ -439,76 +557,27 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
         bool notconv = false;
         for (int di = 0; di < P.n_used; ++di) {
             const DevDF& D = P.df[di];
-            const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
-            const int uy0 = D.uy0, qy0 = D.qy0, py0 = D.py0;
-            const int N = D.N, nU = D.uy1 - uy0 + 1, nQ = D.qy1 - qy0 + 1, nP = D.py1 - py0 + 1;
-            const int *urp = P.d_rowptr + D.urp, *qrp = P.d_rowptr + D.qrp, *prp = P.d_rowptr + D.prp;
-            const unsigned* qmask = P.d_qmask + D.qmask_off;
+            const int nQ = D.qy1 - D.qy0 + 1;
             const float* img = I + ((size_t)tile * P.n_img + D.led) * n * n;
-
             // b = F(I_j) on Q (setup transforms in the shared space of GU)
-            pass_image_cols<BN>(wn, tw_n, stage, img, PF, qy0, nQ, D.tr != 0);
-            pass_image_rows<BN>(wn, tw_n, PF, nQ, qrp, P.dQ_x + q_off, bq);
-            // known field p (column-major in PF; its band rows staged in GQ), b -= P*P,
-            // rows of b inverse along x
-            pass_rows_in<B>(w, tw_m, GQ, m, nP, prp, P.dP_x + p_off,
-                            ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
-            __syncthreads();
-            pass_cols<B>(w, tw_m, GQ, m, py0, nP, GQ, m, qy0, nQ, MidKnownField<B>{PF});
-            pass_rows_rhs<B>(w, tw_m, GQ, nQ, qrp, P.dQ_x + q_off, bq);
-            // s = d = C^H b
-            pass_cols<B>(w, tw_m, GQ, m, qy0, nQ, GU, LDU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
-            const double g0 = pass_rows_out<B>(w, tw_m, GU, LDU, nU, urp, P.dU_x + u_off, OutStart{sv, dv, xv});
-            int par = 0;
-            const double gamma0 = block_sum2(g0, red, par);
-
-            // CGNR
-            double gamma = gamma0;
-            bool conv = !(gamma0 > 1e-300);
-            const double stop = (double)tol * (double)tol * gamma0;
-            int it = 0;
-            float bf = 0.f;                  // first direction: d = s
-            for (; it < iters && !conv; ++it) {
-                pass_rows_in<B>(w, tw_m, GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{sv, dv, bf});
-                __syncthreads();
-                pass_cols<B>(w, tw_m, GU, LDU, uy0, nU, GQ, m, qy0, nQ, MidTimesField<B, true>{PF, inv_m2});
-                pass_rows_mask<B>(w, tw_m, GQ, nQ, qmask);
-                pass_cols<B>(w, tw_m, GQ, m, qy0, nQ, GU, LDU, uy0, nU, MidTimesField<B, false>{PF, inv_m2});
-                const double dw = pass_rows_out<B>(w, tw_m, GU, LDU, nU, urp, P.dU_x + u_off, OutDot{wv, dv});
-                const double delta = block_sum2(dw, red, par);
-                if (!(delta > 0)) break;
-                const double alpha = gamma / delta;
-                const float af = (float)alpha;
-                double g2 = 0;
-                for (int e = threadIdx.x; e < N; e += blockDim.x) {
-                    const float2 d = dv[e];
-                    double2 x = xv[e];
-                    x.x += alpha * d.x;
-                    x.y += alpha * d.y;
-                    xv[e] = x;
-                    const float2 s = csub(sv[e], cscale(wv[e], af));
-                    sv[e] = s;
-                    g2 += (double)s.x * s.x + (double)s.y * s.y;
+            pass_image_cols<BN>(wn, tw_n, stage, img, c.PF, D.qy0, nQ, D.tr != 0);
+            pass_image_rows<BN>(wn, tw_n, c.PF, nQ, P.d_rowptr + D.qrp, P.dQ_x + D.q_off, c.bq);
+            int r;
+            if constexpr (B == 12) {
+                switch (D.by) {
+                    case 6: r = df_solve<B, 6>(c, P, D, sp, ph, iters, tol); break;
+                    case 8: r = df_solve<B, 8>(c, P, D, sp, ph, iters, tol); break;
+                    case 9: r = df_solve<B, 9>(c, P, D, sp, ph, iters, tol); break;
+                    default: r = df_solve<B, B>(c, P, D, sp, ph, iters, tol); break;
                 }
-                const double gnew = block_sum2(g2, red, par);
-                bf = (float)(gnew / gamma);
-                gamma = gnew;
-                conv = gnew <= stop;
+            } else {
+                r = df_solve<B, B>(c, P, D, sp, ph, iters, tol);
             }
-            if (!conv) notconv = true;
+            if (r < 0) notconv = true;
             if (threadIdx.x == 0 && counters) {
-                atomicAdd(counters + 1, (unsigned long long)it);
+                atomicAdd(counters + 1, (unsigned long long)(r < 0 ? -1 - r : r));
                 atomicAdd(counters + 2, 1ull);
             }
-            const int* Upup = P.dU_pup + u_off;
-            const int* Uap = P.dU_ap + u_off;
-            for (int e = threadIdx.x; e < N; e += blockDim.x) {
-                float sn, cs;
-                sincosf(ph[Upup[e]], &sn, &cs);
-                const double2 x = xv[e];
-                sp[Uap[e]] = cmul(make_float2((float)x.x, (float)x.y), make_float2(cs, -sn));
-            }
-            __syncthreads();
         }
         if (threadIdx.x == 0 && notconv && status) atomicOr(status + tile, APIC_TILE_NOTCONV);
     }
