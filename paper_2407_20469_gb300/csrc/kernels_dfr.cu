@@ -227,6 +227,62 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const 
     __syncthreads();
 }
 
+// pass_cols for short columns (2 B <= 16): each half-warp transforms the column pair
+// x, x + 1 together (fft_alpha2 / fft_beta2), so every lane works in the DFT_16 step
+// and each pass makes half as many round trips per half-warp. ncols is even.
+template <int B, class Mid>
+__device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
+                                        float2* Go, int ldo, int yo0, int no, Mid mid) {
+    constexpr int m = 16 * B;
+    const HalfWarp h = w.h();
+    const int side = w.t >= B ? 1 : 0;           // lanes t < 2 B: column x + side, point u
+    const int u = w.t - side * B;
+    for (int x = 2 * w.hw; x < ncols; x += 2 * kHW) {
+        float2 va[B], vb[B], o[16], pf[16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int bb = band_row(w.t + 16 * j, yi0, m);
+            if (bb < ni) {
+                const float2* g = Gi + (size_t)bb * ldi + x;
+                va[j] = g[0];
+                vb[j] = g[1];
+            } else {
+                va[j] = vb[j] = make_float2(0.f, 0.f);
+            }
+        }
+        fft_alpha2<B, true>(va, vb, o, h, tw);
+        if (Mid::kReadsField && w.t < 2 * B) {
+            const float2* col = mid.PF + (size_t)(x + side) * m;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) pf[k1] = col[u + B * k1];
+        }
+        if (w.t < 2 * B) mid(o, x + side, u, pf);
+        if (no > 0) {
+            fft_beta2<B, false>(o, va, vb, h, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < B; ++k1) {
+                const int bb = band_row(w.t + 16 * k1, yo0, m);
+                if (bb < no) {
+                    float2* g = Go + (size_t)bb * ldo + x;
+                    g[0] = va[k1];
+                    g[1] = vb[k1];
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// column pass on a 16 B grid: paired columns where two fit a half-warp
+template <int B, class Mid>
+__device__ __forceinline__ void cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
+                                     float2* Go, int ldo, int yo0, int no, Mid mid) {
+    if constexpr (2 * B <= 16)
+        pass_cols2<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
+    else
+        pass_cols<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
+}
+
 // rows of Q in place: forward along x, keep the Q lags, inverse along x. Ends with __syncthreads.
 template <int B>
 __device__ __noinline__ void pass_rows_mask(HW w, const float2* tw, float2* G, int nrows, const unsigned* qmask) {
@@ -379,10 +435,19 @@ struct DFRSmem {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+// Half-warp area of the m-grid passes: single transforms of 16 B points and, for
+// the column grids of 16 BY points with 2 BY <= 16 (BY = B for B <= 8; 6 or 8 on
+// the 192-point grid), column pairs.
+__host__ __device__ constexpr int hw_area_m(int B) {
+    const int pb = B == 12 ? 8 : (B <= 8 ? B : 0);
+    const int p = pb ? hw_pair_size(pb) : 0;
+    return hw_single_size(B) > p ? hw_single_size(B) : p;
+}
+
 __host__ __device__ inline DFRSmem dfr_smem_layout(int B, int BN, int band_u, int band_q, int max_N) {
     const int m = 16 * B, n = 16 * BN;
-    const int hws_m = 17 * B > 16 * (B + 1) ? 17 * B : 16 * (B + 1);
-    const int hws_n = 17 * BN > 16 * (BN + 1) ? 17 * BN : 16 * (BN + 1);
+    const int hws_m = hw_area_m(B);
+    const int hws_n = hw_single_size(BN);
     DFRSmem L;
     L.gu = align16((size_t)kHW * hws_m * sizeof(float2));
     const size_t gu_end = L.gu + align16((size_t)band_u * (m + 1) * sizeof(float2));
@@ -454,12 +519,12 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
                     ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
     __syncthreads();
     // p on the column grid (column-major in PF), then b -= P * P on Q (16 B grid), rows of b inverse along x
-    pass_cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF});
-    pass_cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
+    cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF});
+    cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
     pass_rows_rhs<B>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
     const float scale = 1.f / ((float)m * (float)my);
     // s = d = C^H b
-    pass_cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
+    cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
     const double g0 = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
     int par = 0;
     const double gamma0 = block_sum2(g0, c.red, par);
@@ -472,9 +537,9 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     for (; it < iters && !conv; ++it) {
         pass_rows_in<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{c.sv, c.dv, bf});
         __syncthreads();
-        pass_cols<BY>(w, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ, MidTimesField<BY, true>{c.PF, scale});
+        cols<BY>(w, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ, MidTimesField<BY, true>{c.PF, scale});
         pass_rows_mask<B>(w, c.tw_m, c.GQ, nQ, qmask);
-        pass_cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
+        cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
         const double dw = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
         const double delta = block_sum2(dw, c.red, par);
         if (!(delta > 0)) break;
@@ -515,7 +580,7 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
                 float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
                 int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
     constexpr int m = 16 * B, n = 16 * BN;
-    constexpr int HWM = HWSize<B>::value, HWN = HWSize<BN>::value;
+    constexpr int HWM = hw_area_m(B), HWN = HWSize<BN>::value;
     extern __shared__ float4 smem4[];
     char* sbase = reinterpret_cast<char*>(smem4);
     const DFRSmem SL = dfr_smem_layout(B, BN, P.band_u, P.band_q, P.max_N);

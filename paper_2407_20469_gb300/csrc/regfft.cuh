@@ -182,6 +182,7 @@ template <int B>
 struct HWSize {
     static constexpr int value = (17 * B > 16 * (B + 1) ? 17 * B : 16 * (B + 1));
 };
+__host__ __device__ constexpr int hw_single_size(int B) { return 17 * B > 16 * (B + 1) ? 17 * B : 16 * (B + 1); }
 
 __device__ __forceinline__ float2 tw_get(const float2* tw, int k, bool inv) {
     const float2 w = tw[k];
@@ -228,6 +229,62 @@ __device__ __forceinline__ void fft_beta(float2 (&o)[16], float2 (&v)[B], const 
 #pragma unroll
     for (int u = 0; u < B; ++u) v[u] = h.hs[h.t * (B + 1) + u];
     DFT<B, INV>::run(v);
+    __syncwarp(h.mask);
+}
+
+// ---- two transforms of length N = 16 B (2 B <= 16) per half-warp, columns a and b.
+// The single-column form leaves lanes t >= B idle in its DFT_16 step; here lanes
+// t < B carry column a there and lanes B <= t < 2 B column b. Same step twiddles.
+// Half-warp area: alpha 2 B rows of 17; beta two 16 x (B + 1) blocks, the second
+// shifted by 8 values so that the two columns' writes fall in different banks.
+__host__ __device__ constexpr int hw_pair_size(int B) {
+    return 34 * B > 32 * (B + 1) + 8 ? 34 * B : 32 * (B + 1) + 8;
+}
+
+// alpha2: va[j] = a[t + 16 j], vb[j] = b[t + 16 j] -> lane t < B: o[k1] = A[t + B k1],
+// lane B <= t < 2 B: o[k1] = B[t - B + B k1].
+template <int B, bool INV>
+__device__ __forceinline__ void fft_alpha2(float2 (&va)[B], float2 (&vb)[B], float2 (&o)[16], const HalfWarp& h,
+                                           const float2* tw) {
+    static_assert(2 * B <= 16, "alpha2 needs 2 B <= 16");
+    DFT<B, INV>::run(va);
+    DFT<B, INV>::run(vb);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) {
+        const float2 wt = tw_get(tw, k2 * 16 + h.t, INV);
+        h.hs[k2 * 17 + h.t] = cmul(va[k2], wt);
+        h.hs[(B + k2) * 17 + h.t] = cmul(vb[k2], wt);
+    }
+    __syncwarp(h.mask);
+    const int row = h.t < 2 * B ? h.t : 0;
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) o[n1] = h.hs[row * 17 + n1];
+    DFT<16, INV>::run(o);
+    __syncwarp(h.mask);
+}
+
+// beta2: lane t < 2 B holds o[j] = (t < B ? a : b)[u + B j], u = t mod B -> all
+// lanes: va[k1] = A[t + 16 k1], vb[k1] = B[t + 16 k1].
+template <int B, bool INV>
+__device__ __forceinline__ void fft_beta2(float2 (&o)[16], float2 (&va)[B], float2 (&vb)[B], const HalfWarp& h,
+                                          const float2* tw) {
+    static_assert(2 * B <= 16, "beta2 needs 2 B <= 16");
+    constexpr int kB = 16 * (B + 1) + 8;     // offset of column b's block
+    DFT<16, INV>::run(o);
+    if (h.t < 2 * B) {
+        const int col = h.t >= B, u = h.t - col * B;
+        float2* dst = h.hs + col * kB;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) dst[k2 * (B + 1) + u] = cmul(o[k2], tw_get(tw, 16 * B + k2 * B + u, INV));
+    }
+    __syncwarp(h.mask);
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        va[u] = h.hs[h.t * (B + 1) + u];
+        vb[u] = h.hs[kB + h.t * (B + 1) + u];
+    }
+    DFT<B, INV>::run(va);
+    DFT<B, INV>::run(vb);
     __syncwarp(h.mask);
 }
 
