@@ -52,6 +52,27 @@ __device__ __forceinline__ int band_row(int i, int y0, int m) {
     return r;
 }
 
+// ---- tensor memory as per-thread storage of the known field
+// The darkfield kernel issues no MMA; its 512 TMEM columns x 128 lanes (256 KB per
+// SM) hold each thread's share of the column-major known field p on the paired
+// column grids. Thread i of warp w owns lane 32 (w mod 4) + i, columns
+// 128 floor(w / 4) .. + 127: 16 complex values per column pair it transforms (at
+// most 4 pairs). A thread reads back only what it stored itself.
+constexpr int kTmemCols = 512;
+constexpr bool kTmemField = kDFThreads == 512;   // 16 warps: 4 per lane quarter, 128 columns each
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float2 (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+                 :: "r"(taddr), "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x), "f"(v[3].y), "f"(v[4].x), "f"(v[4].y), "f"(v[5].x), "f"(v[5].y), "f"(v[6].x), "f"(v[6].y), "f"(v[7].x), "f"(v[7].y), "f"(v[8].x), "f"(v[8].y), "f"(v[9].x), "f"(v[9].y), "f"(v[10].x), "f"(v[10].y), "f"(v[11].x), "f"(v[11].y), "f"(v[12].x), "f"(v[12].y), "f"(v[13].x), "f"(v[13].y), "f"(v[14].x), "f"(v[14].y), "f"(v[15].x), "f"(v[15].y) : "memory");
+}
+// load and wait in one statement, so no use of v can be scheduled before the wait
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float2 (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x), "=f"(v[2].y), "=f"(v[3].x), "=f"(v[3].y), "=f"(v[4].x), "=f"(v[4].y), "=f"(v[5].x), "=f"(v[5].y), "=f"(v[6].x), "=f"(v[6].y), "=f"(v[7].x), "=f"(v[7].y), "=f"(v[8].x), "=f"(v[8].y), "=f"(v[9].x), "=f"(v[9].y), "=f"(v[10].x), "=f"(v[10].y), "=f"(v[11].x), "=f"(v[11].y), "=f"(v[12].x), "=f"(v[12].y), "=f"(v[13].x), "=f"(v[13].y), "=f"(v[14].x), "=f"(v[14].y), "=f"(v[15].x), "=f"(v[15].y) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 struct HW {
     int t, hw;
     unsigned mask;
@@ -106,7 +127,7 @@ struct OutDot {         // w = C^H C d; returns Re <d, w>
 template <int B>
 struct MidStoreField {  // store p column-major (16 B per column)
     float2* PF;
-    static constexpr bool kReadsField = false;
+    static constexpr bool kReadsField = false, kTmem = false;
     __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&)[16]) const {
         float2* col = PF + (size_t)x * (16 * B);
 #pragma unroll
@@ -115,7 +136,7 @@ struct MidStoreField {  // store p column-major (16 B per column)
 };
 struct MidAbs2 {        // replace p by |p|^2
     float2* PF = nullptr;
-    static constexpr bool kReadsField = false;
+    static constexpr bool kReadsField = false, kTmem = false;
     __device__ void operator()(float2 (&o)[16], int, int, const float2 (&)[16]) const {
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) o[k1] = make_float2(cabs2(o[k1]), 0.f);
@@ -125,13 +146,32 @@ template <int B, bool CONJ>
 struct MidTimesField {  // o *= p / m^2 or conj(p) / m^2 (p loaded by the caller)
     const float2* PF;
     float scale;
-    static constexpr bool kReadsField = true;
+    static constexpr bool kReadsField = true, kTmem = false;
     __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&pf)[16]) const {
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) {
             const float2 p = pf[k1];
             o[k1] = cscale(CONJ ? cmulc(o[k1], p) : cmul(o[k1], p), scale);
         }
+    }
+};
+// The same two operations with p in the thread's TMEM columns (paired passes; the
+// whole warp calls them, r = the half-warp's column-pair round)
+struct MidStoreFieldT {
+    uint32_t taddr;
+    static constexpr bool kReadsField = false, kTmem = true;
+    __device__ void tm(float2 (&o)[16], int r) const { tmem_st16(taddr + 32 * r, o); }
+};
+template <bool CONJ>
+struct MidTimesFieldT {
+    uint32_t taddr;
+    float scale;
+    static constexpr bool kReadsField = false, kTmem = true;
+    __device__ void tm(float2 (&o)[16], int r) const {
+        float2 pf[16];
+        tmem_ld16(taddr + 32 * r, pf);
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) o[k1] = cscale(CONJ ? cmulc(o[k1], pf[k1]) : cmul(o[k1], pf[k1]), scale);
     }
 };
 
@@ -196,6 +236,7 @@ __device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float
 template <int B, class Mid>
 __device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
                                        float2* Go, int ldo, int yo0, int no, Mid mid) {
+    static_assert(!Mid::kTmem, "TMEM operations need the paired pass");
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
     for (int x = w.hw; x < ncols; x += kHW) {
@@ -237,7 +278,10 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
     const HalfWarp h = w.h();
     const int side = w.t >= B ? 1 : 0;           // lanes t < 2 B: column x + side, point u
     const int u = w.t - side * B;
-    for (int x = 2 * w.hw; x < ncols; x += 2 * kHW) {
+    // both half-warps of a warp take the same number of rounds (ncols / 2 = 8 B is even),
+    // so the warp is converged at the TMEM accesses
+    int r = 0;
+    for (int x = 2 * w.hw; x < ncols; x += 2 * kHW, ++r) {
         float2 va[B], vb[B], o[16], pf[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
@@ -251,12 +295,17 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
             }
         }
         fft_alpha2<B, true>(va, vb, o, h, tw);
-        if (Mid::kReadsField && w.t < 2 * B) {
-            const float2* col = mid.PF + (size_t)(x + side) * m;
+        if constexpr (Mid::kTmem) {
+            __syncwarp();
+            mid.tm(o, r);
+        } else {
+            if (Mid::kReadsField && w.t < 2 * B) {
+                const float2* col = mid.PF + (size_t)(x + side) * m;
 #pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) pf[k1] = col[u + B * k1];
+                for (int k1 = 0; k1 < 16; ++k1) pf[k1] = col[u + B * k1];
+            }
+            if (w.t < 2 * B) mid(o, x + side, u, pf);
         }
-        if (w.t < 2 * B) mid(o, x + side, u, pf);
         if (no > 0) {
             fft_beta2<B, false>(o, va, vb, h, tw);
 #pragma unroll
@@ -488,7 +537,22 @@ struct DFCtx {
     float2 *dv, *sv, *wv;
     double2* xv;
     double* red;
+    uint32_t tm;            // this thread's TMEM columns (lane and column fields)
 };
+
+// Whether a kernel with row grid 16 B has column grids that keep p in TMEM
+__host__ __device__ constexpr bool uses_tmem(int B) { return kTmemField && (B == 12 || B <= 8); }
+
+// Column pass that multiplies by p or conj(p): p from TMEM on paired grids, else
+// from the column-major copy in global scratch
+template <int BY, bool CONJ>
+__device__ __forceinline__ void cols_times(const DFCtx& c, const float2* tw, int m, const float2* Gi, int ldi, int yi0,
+                                           int ni, float2* Go, int ldo, int yo0, int no, float scale) {
+    if constexpr (2 * BY <= 16 && kTmemField)
+        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesFieldT<CONJ>{c.tm, scale});
+    else
+        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesField<BY, CONJ>{c.PF, scale});
+}
 
 __device__ __forceinline__ const float2* column_table(const DevPlan& P, int BY, int B) {
     return BY == B ? P.tw_r : BY == 6 ? P.tw_y6 : BY == 8 ? P.tw_y8 : P.tw_y9;
@@ -519,12 +583,17 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
                     ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
     __syncthreads();
     // p on the column grid (column-major in PF), then b -= P * P on Q (16 B grid), rows of b inverse along x
-    cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF});
+    if constexpr (2 * BY <= 16 && kTmemField) {
+        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreFieldT{c.tm});
+        tmem_wait_st();
+    } else {
+        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF});
+    }
     cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
     pass_rows_rhs<B>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
     const float scale = 1.f / ((float)m * (float)my);
     // s = d = C^H b
-    cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
+    cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, scale);
     const double g0 = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
     int par = 0;
     const double gamma0 = block_sum2(g0, c.red, par);
@@ -537,9 +606,9 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     for (; it < iters && !conv; ++it) {
         pass_rows_in<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{c.sv, c.dv, bf});
         __syncthreads();
-        cols<BY>(w, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ, MidTimesField<BY, true>{c.PF, scale});
+        cols_times<BY, true>(c, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ, scale);
         pass_rows_mask<B>(w, c.tw_m, c.GQ, nQ, qmask);
-        cols<BY>(w, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, MidTimesField<BY, false>{c.PF, scale});
+        cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, scale);
         const double dw = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
         const double delta = block_sum2(dw, c.red, par);
         if (!(delta > 0)) break;
@@ -600,7 +669,27 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
 
     make_step_twiddles(tw_m, P.tw_r, B);
     make_step_twiddles(tw_n, P.tw_n, BN);
+    // TMEM for the known field: all 512 columns. One block of this kernel fills an SM's
+    // register file (512 threads x 128 registers), so no other block of it holds TMEM
+    // on the SM and the allocation does not wait (were there one, it would wait only
+    // for that block's release at its end: blocks never wait on one another).
+    __shared__ uint32_t tmem_base;
+    const int warp = threadIdx.x >> 5;
+    if constexpr (uses_tmem(B)) {
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         :: "r"((uint32_t)__cvta_generic_to_shared(&tmem_base)), "r"(kTmemCols) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
     __syncthreads();
+    if constexpr (uses_tmem(B)) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        c.tm = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+    } else {
+        c.tm = 0;
+    }
 
     HW wn;                           // image (n-grid) setup passes
     c.w.hw = wn.hw = threadIdx.x >> 4;
@@ -645,6 +734,15 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             }
         }
         if (threadIdx.x == 0 && notconv && status) atomicOr(status + tile, APIC_TILE_NOTCONV);
+    }
+    if constexpr (uses_tmem(B)) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_base), "r"(kTmemCols)
+                         : "memory");
+        }
     }
 }
 
