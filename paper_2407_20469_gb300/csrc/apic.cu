@@ -285,12 +285,13 @@ apic_status upload(apic_plan* plan) {
         band_p = std::max(band_p, e.py1 - e.py0 + 1);
         band_q = std::max(band_q, e.qy1 - e.qy0 + 1);
         e.qmask_off = (int)qmask.size();
-        if (mr > 0) {   // Q membership per band row on the register grid
-            const int words = mr / 32;
-            qmask.resize(qmask.size() + (size_t)(e.qy1 - e.qy0 + 1) * words, 0u);
+        if (mr > 0) {   // Q membership per band row on the register grid, as 16-bit lane masks
+            const int Bm = mr / 16;      // x index xi = t + Bm k1 sits in lane t, bit k1
+            qmask.resize(qmask.size() + (size_t)(e.qy1 - e.qy0 + 1) * 8, 0u);
             for (size_t q = 0; q < Qs.x.size(); ++q) {
                 const int xi = ((Qs.x[q] % mr) + mr) % mr;
-                qmask[e.qmask_off + (size_t)(Qs.y[q] - e.qy0) * words + (xi >> 5)] |= 1u << (xi & 31);
+                const int t = xi % Bm, k1 = xi / Bm;
+                qmask[e.qmask_off + (size_t)(Qs.y[q] - e.qy0) * 8 + (t >> 1)] |= 1u << (16 * (t & 1) + k1);
             }
         }
         dfs.push_back(e);

@@ -63,7 +63,8 @@ struct DevPlan {
     const int* dP_x; const int* dP_y; const int* dP_pup; const int* dP_ap;
     const int* dQ_x; const int* dQ_y;
     const int* d_rowptr;
-    const unsigned* d_qmask;         // per used image: Q band rows x (mr / 32) words
+    const unsigned* d_qmask;         // per used image: Q band rows x 8 words of two 16-bit lane masks
+                                     // (lane t, bit k1: x index t + (mr / 16) k1 is in Q)
     // twiddles
     const float2* tw_n;              // n = h = w
     const float2* tw_m;

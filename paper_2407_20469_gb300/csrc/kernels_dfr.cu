@@ -7,9 +7,9 @@
 //   min ||C u - b|| by CG on the normal equations C^H C u = C^H b (CGNR): per
 //   iteration w = C^H mask_Q C d as five passes over the grid
 //     R1 rows of U: scatter d, inverse transform along x     -> GU
-//     C1 columns:   inverse along y, * conj(p) / m^2, forward along y -> GQ
+//     C1 columns:   inverse along y, * conj(p) / (m m_y), forward along y -> GQ
 //     R2 rows of Q: forward along x, keep Q, inverse along x (in place)
-//     C2 columns:   inverse along y, * p / m^2, forward along y        -> GU
+//     C2 columns:   inverse along y, * p / (m m_y), forward along y      -> GU
 //     R3 rows of U: forward along x, gather w on U, <d, w>
 //   then x += alpha d, s -= alpha w, and d = s + beta d (folded into the next
 //   R1). Transforms FP32; inner products, step lengths and the solution FP64.
@@ -125,13 +125,14 @@ struct OutDot {         // w = C^H C d; returns Re <d, w>
 
 // ---- per-column mid operations (lanes t < B; o[k1] is the value at y = t + B k1)
 template <int B>
-struct MidStoreField {  // store p column-major (16 B per column)
+struct MidStoreField {  // store p s (p scaled) column-major (16 B per column)
     float2* PF;
+    float scale;
     static constexpr bool kReadsField = false, kTmem = false;
     __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&)[16]) const {
         float2* col = PF + (size_t)x * (16 * B);
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) col[t + B * k1] = o[k1];
+        for (int k1 = 0; k1 < 16; ++k1) col[t + B * k1] = cscale(o[k1], scale);
     }
 };
 struct MidAbs2 {        // replace p by |p|^2
@@ -143,35 +144,35 @@ struct MidAbs2 {        // replace p by |p|^2
     }
 };
 template <int B, bool CONJ>
-struct MidTimesField {  // o *= p / m^2 or conj(p) / m^2 (p loaded by the caller)
+struct MidTimesField {  // o *= p s or conj(p s), p s = the stored, scaled field (loaded by the caller)
     const float2* PF;
-    float scale;
     static constexpr bool kReadsField = true, kTmem = false;
     __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&pf)[16]) const {
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) {
-            const float2 p = pf[k1];
-            o[k1] = cscale(CONJ ? cmulc(o[k1], p) : cmul(o[k1], p), scale);
-        }
+        for (int k1 = 0; k1 < 16; ++k1) o[k1] = CONJ ? cmulc(o[k1], pf[k1]) : cmul(o[k1], pf[k1]);
     }
 };
 // The same two operations with p in the thread's TMEM columns (paired passes; the
 // whole warp calls them, r = the half-warp's column-pair round)
 struct MidStoreFieldT {
     uint32_t taddr;
+    float scale;
     static constexpr bool kReadsField = false, kTmem = true;
-    __device__ void tm(float2 (&o)[16], int r) const { tmem_st16(taddr + 32 * r, o); }
+    __device__ void tm(float2 (&o)[16], int r) const {
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) o[k1] = cscale(o[k1], scale);
+        tmem_st16(taddr + 32 * r, o);
+    }
 };
 template <bool CONJ>
 struct MidTimesFieldT {
     uint32_t taddr;
-    float scale;
     static constexpr bool kReadsField = false, kTmem = true;
     __device__ void tm(float2 (&o)[16], int r) const {
         float2 pf[16];
         tmem_ld16(taddr + 32 * r, pf);
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) o[k1] = cscale(CONJ ? cmulc(o[k1], pf[k1]) : cmul(o[k1], pf[k1]), scale);
+        for (int k1 = 0; k1 < 16; ++k1) o[k1] = CONJ ? cmulc(o[k1], pf[k1]) : cmul(o[k1], pf[k1]);
     }
 };
 
@@ -339,17 +340,16 @@ __device__ __noinline__ void pass_rows_mask(HW w, const float2* tw, float2* G, i
     const HalfWarp h = w.h();
     for (int b = w.hw; b < nrows; b += kHW) {
         float2* row = G + (size_t)b * m;
-        const unsigned* mk = qmask + (size_t)b * (m / 32);
+        // lane t's Q membership of x = t + B k1 (bit k1)
+        const unsigned bits = qmask[(size_t)b * 8 + (w.t >> 1)] >> (16 * (w.t & 1));
         float2 v[B], o[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
         fft_alpha<B, false>(v, o, h, tw);
         if (w.t < B) {
 #pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) {
-                const int kx = w.t + B * k1;
-                if (!((mk[kx >> 5] >> (kx & 31)) & 1u)) o[k1] = make_float2(0.f, 0.f);
-            }
+            for (int k1 = 0; k1 < 16; ++k1)
+                if (!((bits >> k1) & 1u)) o[k1] = make_float2(0.f, 0.f);
         }
         fft_beta<B, true>(o, v, h, tw);
 #pragma unroll
@@ -543,15 +543,15 @@ struct DFCtx {
 // Whether a kernel with row grid 16 B has column grids that keep p in TMEM
 __host__ __device__ constexpr bool uses_tmem(int B) { return kTmemField && (B == 12 || B <= 8); }
 
-// Column pass that multiplies by p or conj(p): p from TMEM on paired grids, else
-// from the column-major copy in global scratch
+// Column pass that multiplies by the scaled field p s or its conjugate: from TMEM on
+// paired grids, else from the column-major copy in global scratch
 template <int BY, bool CONJ>
 __device__ __forceinline__ void cols_times(const DFCtx& c, const float2* tw, int m, const float2* Gi, int ldi, int yi0,
-                                           int ni, float2* Go, int ldo, int yo0, int no, float scale) {
+                                           int ni, float2* Go, int ldo, int yo0, int no) {
     if constexpr (2 * BY <= 16 && kTmemField)
-        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesFieldT<CONJ>{c.tm, scale});
+        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesFieldT<CONJ>{c.tm});
     else
-        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesField<BY, CONJ>{c.PF, scale});
+        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesField<BY, CONJ>{c.PF});
 }
 
 __device__ __forceinline__ const float2* column_table(const DevPlan& P, int BY, int B) {
@@ -582,18 +582,19 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     pass_rows_in<B>(w, c.tw_m, c.GQ, m, nP, prp, P.dP_x + p_off,
                     ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
     __syncthreads();
-    // p on the column grid (column-major in PF), then b -= P * P on Q (16 B grid), rows of b inverse along x
+    // p s on the column grid (s = 1 / (m my): the two unnormalised transforms around
+    // each product), then b -= P * P on Q (16 B grid), rows of b inverse along x
+    const float scale = 1.f / ((float)m * (float)my);
     if constexpr (2 * BY <= 16 && kTmemField) {
-        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreFieldT{c.tm});
+        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreFieldT{c.tm, scale});
         tmem_wait_st();
     } else {
-        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF});
+        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF, scale});
     }
     cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
     pass_rows_rhs<B>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
-    const float scale = 1.f / ((float)m * (float)my);
     // s = d = C^H b
-    cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, scale);
+    cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU);
     const double g0 = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
     int par = 0;
     const double gamma0 = block_sum2(g0, c.red, par);
@@ -606,9 +607,9 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     for (; it < iters && !conv; ++it) {
         pass_rows_in<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{c.sv, c.dv, bf});
         __syncthreads();
-        cols_times<BY, true>(c, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ, scale);
+        cols_times<BY, true>(c, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ);
         pass_rows_mask<B>(w, c.tw_m, c.GQ, nQ, qmask);
-        cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU, scale);
+        cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU);
         const double dw = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
         const double delta = block_sum2(dw, c.red, par);
         if (!(delta > 0)) break;
