@@ -271,7 +271,8 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const 
 
 // pass_cols for short columns (2 B <= 16): each half-warp transforms the column pair
 // x, x + 1 together (fft_alpha2 / fft_beta2), so every lane works in the DFT_16 step
-// and each pass makes half as many round trips per half-warp. ncols is even.
+// and each pass makes half as many round trips per half-warp. ncols is even; a grid
+// with an even row stride (16-byte aligned rows) moves each pair as one 16-byte access.
 template <int B, class Mid>
 __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
                                         float2* Go, int ldo, int yo0, int no, Mid mid) {
@@ -282,6 +283,7 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
     // both half-warps of a warp take the same number of rounds (ncols / 2 = 8 B is even),
     // so the warp is converged at the TMEM accesses
     int r = 0;
+    const bool vin = (ldi & 1) == 0, vout = (ldo & 1) == 0;
     for (int x = 2 * w.hw; x < ncols; x += 2 * kHW, ++r) {
         float2 va[B], vb[B], o[16], pf[16];
 #pragma unroll
@@ -289,8 +291,14 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
             const int bb = band_row(w.t + 16 * j, yi0, m);
             if (bb < ni) {
                 const float2* g = Gi + (size_t)bb * ldi + x;
-                va[j] = g[0];
-                vb[j] = g[1];
+                if (vin) {
+                    const float4 q = *reinterpret_cast<const float4*>(g);
+                    va[j] = make_float2(q.x, q.y);
+                    vb[j] = make_float2(q.z, q.w);
+                } else {
+                    va[j] = g[0];
+                    vb[j] = g[1];
+                }
             } else {
                 va[j] = vb[j] = make_float2(0.f, 0.f);
             }
@@ -314,8 +322,12 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
                 const int bb = band_row(w.t + 16 * k1, yo0, m);
                 if (bb < no) {
                     float2* g = Go + (size_t)bb * ldo + x;
-                    g[0] = va[k1];
-                    g[1] = vb[k1];
+                    if (vout) {
+                        *reinterpret_cast<float4*>(g) = make_float4(va[k1].x, va[k1].y, vb[k1].x, vb[k1].y);
+                    } else {
+                        g[0] = va[k1];
+                        g[1] = vb[k1];
+                    }
                 }
             }
         }
