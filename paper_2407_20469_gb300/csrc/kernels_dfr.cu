@@ -335,12 +335,79 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
     __syncthreads();
 }
 
-// column pass on a 16 B grid: paired columns where two fit a half-warp
+// pass_cols for columns too long to pair in the lanes (B > 8): each half-warp takes the
+// column pair x, x + 1 and transforms the two in turn, so that the pair still moves as
+// one 16-byte access per row on grids with an even row stride. ncols is even.
+template <int B, class Mid>
+__device__ __noinline__ void pass_cols_seq2(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0,
+                                            int ni, float2* Go, int ldo, int yo0, int no, Mid mid) {
+    static_assert(!Mid::kTmem, "TMEM operations need the paired pass");
+    constexpr int m = 16 * B;
+    const HalfWarp h = w.h();
+    const bool vin = (ldi & 1) == 0, vout = (ldo & 1) == 0;
+    for (int x = 2 * w.hw; x < ncols; x += 2 * kHW) {
+        float2 va[B], vb[B], o[16], pf[16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int bb = band_row(w.t + 16 * j, yi0, m);
+            if (bb < ni) {
+                const float2* g = Gi + (size_t)bb * ldi + x;
+                if (vin) {
+                    const float4 q = *reinterpret_cast<const float4*>(g);
+                    va[j] = make_float2(q.x, q.y);
+                    vb[j] = make_float2(q.z, q.w);
+                } else {
+                    va[j] = g[0];
+                    vb[j] = g[1];
+                }
+            } else {
+                va[j] = vb[j] = make_float2(0.f, 0.f);
+            }
+        }
+        fft_alpha<B, true>(va, o, h, tw);
+        if (Mid::kReadsField && w.t < B) {
+            const float2* col = mid.PF + (size_t)x * m;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) pf[k1] = col[w.t + B * k1];
+        }
+        if (w.t < B) mid(o, x, w.t, pf);
+        if (no > 0) fft_beta<B, false>(o, va, h, tw);
+        fft_alpha<B, true>(vb, o, h, tw);
+        if (Mid::kReadsField && w.t < B) {
+            const float2* col = mid.PF + (size_t)(x + 1) * m;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) pf[k1] = col[w.t + B * k1];
+        }
+        if (w.t < B) mid(o, x + 1, w.t, pf);
+        if (no > 0) {
+            fft_beta<B, false>(o, vb, h, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < B; ++k1) {
+                const int bb = band_row(w.t + 16 * k1, yo0, m);
+                if (bb < no) {
+                    float2* g = Go + (size_t)bb * ldo + x;
+                    if (vout) {
+                        *reinterpret_cast<float4*>(g) = make_float4(va[k1].x, va[k1].y, vb[k1].x, vb[k1].y);
+                    } else {
+                        g[0] = va[k1];
+                        g[1] = vb[k1];
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// column pass on a 16 B grid: paired columns where two fit a half-warp, column pairs
+// in turn up to B = 12, single columns beyond
 template <int B, class Mid>
 __device__ __forceinline__ void cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
                                      float2* Go, int ldo, int yo0, int no, Mid mid) {
     if constexpr (2 * B <= 16)
         pass_cols2<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
+    else if constexpr (B <= 12)
+        pass_cols_seq2<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
     else
         pass_cols<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
 }
