@@ -68,6 +68,25 @@ __device__ __forceinline__ double block_sum2(double v, double* red, int& parity)
     return total;
 }
 
+// block_sum2 of FP32 per-thread partials: FP32 within each warp, FP64 across the
+// warps (a handful of FP64 adds on warp 0 instead of five per lane of every warp).
+__device__ __forceinline__ double block_sum2f(float v, double* red, int& parity) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    double* r = red + parity * 32;
+    if (lane == 0) r[warp] = (double)v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < nw ? r[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) r[31] = t;
+    }
+    __syncthreads();
+    const double total = r[31];
+    parity ^= 1;
+    return total;
+}
+
 // Raises (never lowers) a kernel's dynamic shared-memory limit. The limit is
 // process-wide per function, so plans of different sizes that share a kernel
 // must not shrink it under one another.

@@ -12,9 +12,11 @@
 //     C2 columns:   inverse along y, * p / (m m_y), forward along y      -> GU
 //     R3 rows of U: forward along x, gather w on U, <d, w>
 //   then x += alpha d, s -= alpha w, and d = s + beta d (folded into the next
-//   R1). Transforms FP32; inner products, step lengths and the solution FP64.
+//   R1). Transforms, vectors and the partial sums of a thread and of a warp FP32;
+//   the sums across warps and the step lengths FP64 (the FP64 pipe is narrow, so it
+//   sees 16 values per reduction rather than every point).
 // GU / GQ are band-row grids (only rows holding U or Q points). GU and the CG
-// vectors (FP64 solution included) live in shared memory (GU with row stride
+// vectors (the solution included) live in shared memory (GU with row stride
 // m + 1, so the column passes are conflict free); GQ, the column-major known
 // field p and b on Q live in the block's global scratch (L2-resident). The setup transforms of each image
 // reuse the shared-memory space of GU. One block per tile (persistent); images
@@ -105,21 +107,21 @@ struct ValNextDir {     // d = s + beta d (stored back), scattered into the rows
 struct OutStart {       // s = d = C^H b, x = 0; returns |s|^2
     float2* sv;
     float2* dv;
-    double2* xv;
-    __device__ double operator()(int e, float2 v) const {
+    float2* xv;
+    __device__ float operator()(int e, float2 v) const {
         sv[e] = v;
         dv[e] = v;
-        xv[e] = make_double2(0.0, 0.0);
-        return (double)v.x * v.x + (double)v.y * v.y;
+        xv[e] = make_float2(0.f, 0.f);
+        return v.x * v.x + v.y * v.y;
     }
 };
 struct OutDot {         // w = C^H C d; returns Re <d, w>
     float2* wv;
     const float2* dv;
-    __device__ double operator()(int e, float2 v) const {
+    __device__ float operator()(int e, float2 v) const {
         wv[e] = v;
         const float2 d = dv[e];
-        return (double)d.x * v.x + (double)d.y * v.y;
+        return d.x * v.x + d.y * v.y;
     }
 };
 
@@ -205,11 +207,11 @@ __device__ __noinline__ void pass_rows_in(HW w, const float2* tw, float2* G, int
 
 // rows of a band of G: forward transform along x; returns sum of out(e, value) over this lane's points
 template <int B, class Out>
-__device__ __noinline__ double pass_rows_out(HW w, const float2* tw, const float2* G, int ld, int nrows,
+__device__ __noinline__ float pass_rows_out(HW w, const float2* tw, const float2* G, int ld, int nrows,
                                              const int* rp, const int* px, Out out) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
-    double acc = 0.0;
+    float acc = 0.f;
     for (int b = w.hw; b < nrows; b += kHW) {
         const float2* row = G + (size_t)b * ld;
         float2 v[B], o[16];
@@ -305,6 +307,7 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
         }
         fft_alpha2<B, true>(va, vb, o, h, tw);
         if constexpr (Mid::kTmem) {
+            static_assert(!Mid::kReadsField, "a TMEM operation loads its field itself");
             __syncwarp();
             mid.tm(o, r);
         } else {
@@ -555,7 +558,7 @@ __device__ __noinline__ void pass_rows_rhs(HW w, const float2* tw, float2* GQ, i
 //   [gu, c)        GU, band_u rows of m + 1 complex values
 //   [0, c)         during the setup transforms of an image: half-warp areas of
 //                  the n-grid passes, then the column stage (aliases the above)
-//   [x, c)         FP64 solution x
+//   [x, c)         solution x
 //   [c, total)     CG vectors d, s, w; step twiddles of m and n; reduction slots
 struct DFRSmem {
     size_t gu, stage, x, c, total;
@@ -584,7 +587,7 @@ __host__ __device__ inline DFRSmem dfr_smem_layout(int B, int BN, int band_u, in
     const size_t stage_f = (size_t)n * kStageLd * sizeof(float);
     const size_t stage_end = L.stage + align16(stage_c > stage_f ? stage_c : stage_f);
     L.x = gu_end > stage_end ? gu_end : stage_end;
-    L.c = L.x + align16((size_t)max_N * sizeof(double2));
+    L.c = L.x + align16((size_t)max_N * sizeof(float2));
     size_t t = L.c + (size_t)3 * max_N * sizeof(float2);                   // d, s, w
     t += (size_t)2 * (m + n) * sizeof(float2);                            // step twiddles
     t += (size_t)2 * m * sizeof(float2);                                  // column-grid step twiddles
@@ -614,7 +617,7 @@ struct DFCtx {
     float2* tw_y;           // step twiddles of the image's column grid (filled per image)
     float2 *GU, *GQ, *PF, *bq;
     float2 *dv, *sv, *wv;
-    double2* xv;
+    float2* xv;
     double* red;
     uint32_t tm;            // this thread's TMEM columns (lane and column fields)
 };
@@ -674,9 +677,9 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     pass_rows_rhs<B>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
     // s = d = C^H b
     cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU);
-    const double g0 = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
+    const float g0 = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
     int par = 0;
-    const double gamma0 = block_sum2(g0, c.red, par);
+    const double gamma0 = block_sum2f(g0, c.red, par);
     // CGNR
     double gamma = gamma0;
     bool conv = !(gamma0 > 1e-300);
@@ -689,23 +692,23 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
         cols_times<BY, true>(c, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ);
         pass_rows_mask<B>(w, c.tw_m, c.GQ, nQ, qmask);
         cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU);
-        const double dw = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
-        const double delta = block_sum2(dw, c.red, par);
+        const float dw = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
+        const double delta = block_sum2f(dw, c.red, par);
         if (!(delta > 0)) break;
         const double alpha = gamma / delta;
         const float af = (float)alpha;
-        double g2 = 0;
+        float g2 = 0.f;
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
             const float2 d = c.dv[e];
-            double2 x = c.xv[e];
-            x.x += alpha * d.x;
-            x.y += alpha * d.y;
+            float2 x = c.xv[e];
+            x.x += af * d.x;
+            x.y += af * d.y;
             c.xv[e] = x;
             const float2 sv = csub(c.sv[e], cscale(c.wv[e], af));
             c.sv[e] = sv;
-            g2 += (double)sv.x * sv.x + (double)sv.y * sv.y;
+            g2 += sv.x * sv.x + sv.y * sv.y;
         }
-        const double gnew = block_sum2(g2, c.red, par);
+        const double gnew = block_sum2f(g2, c.red, par);
         bf = (float)(gnew / gamma);
         gamma = gnew;
         conv = gnew <= stop;
@@ -716,8 +719,7 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     for (int e = threadIdx.x; e < N; e += blockDim.x) {
         float sn, cs;
         sincosf(ph[Upup[e]], &sn, &cs);
-        const double2 x = c.xv[e];
-        sp[Uap[e]] = cmul(make_float2((float)x.x, (float)x.y), make_float2(cs, -sn));
+        sp[Uap[e]] = cmul(c.xv[e], make_float2(cs, -sn));
     }
     __syncthreads();
     return conv ? it : -1 - it;
@@ -778,7 +780,7 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
     c.w.hs = reinterpret_cast<float2*>(sbase) + c.w.hw * HWM;
     wn.hs = reinterpret_cast<float2*>(sbase) + c.w.hw * HWN;
 
-    c.xv = reinterpret_cast<double2*>(sbase + SL.x);
+    c.xv = reinterpret_cast<float2*>(sbase + SL.x);
     char* base = scratch + (size_t)blockIdx.x * per_block;
     c.GQ = reinterpret_cast<float2*>(base);
     c.PF = c.GQ + (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m;   // column-major p, or F(I) rows
