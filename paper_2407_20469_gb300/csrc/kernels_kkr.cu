@@ -57,19 +57,21 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
     const long long hh = (long long)P.h * P.h, ww = (long long)P.w * P.w;
     const int nprob = n_tiles * P.n_bf;
 
+    int par = 0;
     for (int prob = blockIdx.x; prob < nprob; prob += gridDim.x) {
         const int tile = prob / P.n_bf, i = prob - tile * P.n_bf;
         if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
         const float* img = I + ((size_t)tile * P.n_img + i) * n * n;
         const int kix = P.led_x[i], kiy = P.led_y[i];
-        double s = 0;
+        // image sum for the log floor: FP32 within a thread (n^2 / 512 values) and a warp
+        float s = 0.f;
         const float4* img4 = reinterpret_cast<const float4*>(img);
         for (int q = threadIdx.x; q < n * n / 4; q += blockDim.x) {
             const float4 v = img4[q];
-            s += (double)v.x + v.y + v.z + v.w;
+            s += (v.x + v.y) + (v.z + v.w);
         }
-        s = block_sum(s, red);
-        const float eps = (float)(1e-6 * s / ((double)n * n));
+        const double stot = block_sum2f(s, red, par);
+        const float eps = (float)(1e-6 * stot / ((double)n * n));
 
         // P1: rows, log then forward along x
         for (int r = hw; r < n; r += kKKHW) {

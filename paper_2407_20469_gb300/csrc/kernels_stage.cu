@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles,
     const size_t npix = (size_t)P.h * P.w;
     const float* T = I + (size_t)tile * P.n_img * npix;
     double acc = 0;
-    int bad = 0;
+    int bad = 0, par = 0;
     auto invalid = [](float4 v) {
         return !(v.x >= 0.f && v.x < INFINITY) || !(v.y >= 0.f && v.y < INFINITY) ||
                !(v.z >= 0.f && v.z < INFINITY) || !(v.w >= 0.f && v.w < INFINITY);
@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles,
                 s += (v.x + v.y) + (v.z + v.w);
                 s2 += (v.x * v.x + v.y * v.y) + (v.z * v.z + v.w * v.w);
             }
-            const double st = block_sum((double)s, red);
-            const double st2 = block_sum((double)s2, red);
+            const double st = block_sum2((double)s, red, par);
+            const double st2 = block_sum2((double)s2, red, par);
             const double mean = st / npix;
             const double var = st2 / npix - mean * mean;
             acc += mean > 0 ? var / (mean * mean) : 0.0;
