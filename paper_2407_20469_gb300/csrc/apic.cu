@@ -227,22 +227,35 @@ apic_status upload(apic_plan* plan) {
         const Set Us = frame(d.U_x, d.U_y, &d.U_pup, &d.U_ap);
         const Set Ps = frame(d.P_x, d.P_y, &d.P_pup, &d.P_ap);
         const Set Qs = frame(d.Q_x, d.Q_y, nullptr, nullptr);
-        // Column grid of the register solve: the shortest supported length L on which
-        // both correlations of Eq. 13 are exact along y. C u (U with P, read on Q) has
-        // no alias when no q - p - k (q in U, p in P, k in Q) is a nonzero multiple of
-        // L, C^H r (Q with P, read on U) when no k + p - q is; every band must also fit.
-        e.by = mr / 16;
+        // Grid of the register solve: along each axis the correlations of Eq. 13 are
+        // exact on a circular grid of L points when C u (U with P, read on Q) has no
+        // q - p - k (q in U, p in P, k in Q) that is a nonzero multiple of L and C^H r
+        // (Q with P, read on U) no such k + p - q; every band must also fit. Of the
+        // supported (row, column) grids 16 bx x 16 by that are exact for the image, the
+        // one with the least estimated work per iteration (columns x relative cost of a
+        // column: paired 96 / 128 points, 144 and 192 points taken in turn) is used.
+        // P * P, whose lags reach further, stays on the mr x mr grid.
+        e.bx = e.by = mr / 16;
         if (mr == 192 && !Us.y.empty() && !Ps.y.empty() && !Qs.y.empty()) {
-            auto mm = [](const std::vector<int>& v) { return std::minmax_element(v.begin(), v.end()); };
-            const auto u = mm(Us.y), pp = mm(Ps.y), q = mm(Qs.y);
-            const int u0 = *u.first, u1 = *u.second, p0 = *pp.first, p1 = *pp.second, q0 = *q.first, q1 = *q.second;
-            const int need_c = std::max(std::abs(u0 - p1 - q1), std::abs(u1 - p0 - q0)) + 1;
-            const int need_ch = std::max(std::abs(q0 + p0 - u1), std::abs(q1 + p1 - u0)) + 1;
-            const int need = std::max({need_c, need_ch, u1 - u0 + 1, p1 - p0 + 1, q1 - q0 + 1});
-            for (int cand : {6, 8, 9, 12})
-                if (16 * cand >= need) {
-                    e.by = cand;
-                    break;
+            auto need = [](const std::vector<int>& U, const std::vector<int>& Pv, const std::vector<int>& Q) {
+                auto mm = [](const std::vector<int>& v) { return std::minmax_element(v.begin(), v.end()); };
+                const auto u = mm(U), pp = mm(Pv), q = mm(Q);
+                const int u0 = *u.first, u1 = *u.second, p0 = *pp.first, p1 = *pp.second, q0 = *q.first,
+                          q1 = *q.second;
+                const int need_c = std::max(std::abs(u0 - p1 - q1), std::abs(u1 - p0 - q0)) + 1;
+                const int need_ch = std::max(std::abs(q0 + p0 - u1), std::abs(q1 + p1 - u0)) + 1;
+                return std::max({need_c, need_ch, u1 - u0 + 1, p1 - p0 + 1, q1 - q0 + 1});
+            };
+            const int nx = need(Us.x, Ps.x, Qs.x), ny = need(Us.y, Ps.y, Qs.y);
+            struct Grid { int bx, by; double col_cost; };
+            static const Grid grids[] = {{12, 12, 2.0}, {12, 9, 1.68}, {12, 8, 1.13}, {12, 6, 1.0},
+                                         {10, 8, 1.13}, {10, 6, 1.0},  {9, 9, 1.68}};
+            double best = 1e300;
+            for (const Grid& g : grids)
+                if (16 * g.bx >= nx && 16 * g.by >= ny && 16 * g.bx * g.col_cost < best) {
+                    best = 16 * g.bx * g.col_cost;
+                    e.bx = g.bx;
+                    e.by = g.by;
                 }
         }
         e.u_off = (int)ux.size();
@@ -285,11 +298,11 @@ apic_status upload(apic_plan* plan) {
         band_p = std::max(band_p, e.py1 - e.py0 + 1);
         band_q = std::max(band_q, e.qy1 - e.qy0 + 1);
         e.qmask_off = (int)qmask.size();
-        if (mr > 0) {   // Q membership per band row on the register grid, as 16-bit lane masks
-            const int Bm = mr / 16;      // x index xi = t + Bm k1 sits in lane t, bit k1
+        if (mr > 0) {   // Q membership per band row on the image's row grid, as 16-bit lane masks
+            const int Bm = e.bx, mx = 16 * e.bx;   // x index xi = t + Bm k1 sits in lane t, bit k1
             qmask.resize(qmask.size() + (size_t)(e.qy1 - e.qy0 + 1) * 8, 0u);
             for (size_t q = 0; q < Qs.x.size(); ++q) {
-                const int xi = ((Qs.x[q] % mr) + mr) % mr;
+                const int xi = ((Qs.x[q] % mx) + mx) % mx;
                 const int t = xi % Bm, k1 = xi / Bm;
                 qmask[e.qmask_off + (size_t)(Qs.y[q] - e.qy0) * 8 + (t >> 1)] |= 1u << (16 * (t & 1) + k1);
             }
@@ -311,6 +324,7 @@ apic_status upload(apic_plan* plan) {
     const size_t o_twn = A.add(twiddles(H.h)), o_twm = A.add(twiddles(H.m)), o_twN = A.add(twiddles(H.H));
     const size_t o_twr = A.add(twiddles(std::max(mr, 16)));
     const size_t o_ty6 = A.add(twiddles(96)), o_ty8 = A.add(twiddles(128)), o_ty9 = A.add(twiddles(144));
+    const size_t o_ty10 = A.add(twiddles(160));
     const size_t o_qm = A.add(qmask);
 
     void* base = nullptr;
@@ -360,6 +374,7 @@ apic_status upload(apic_plan* plan) {
     D.tw_y6 = (const float2*)(b + o_ty6);
     D.tw_y8 = (const float2*)(b + o_ty8);
     D.tw_y9 = (const float2*)(b + o_ty9);
+    D.tw_y10 = (const float2*)(b + o_ty10);
     D.d_qmask = (const unsigned*)(b + o_qm);
     return APIC_OK;
 }

@@ -21,6 +21,7 @@ struct DevDF {
     int qmask_off;                   // offset of the Q-membership bit rows (register grid)
     int tr;                          // 1: solved transposed (point sets and image with x <-> y)
     int by;                          // column grid of the solve: 16 by points (register kernel)
+    int bx;                          // row grid of the solve: 16 bx points (register kernel)
 };
 
 struct DevPlan {
@@ -70,9 +71,10 @@ struct DevPlan {
     const float2* tw_m;
     const float2* tw_N;              // N = H = W
     const float2* tw_r;              // mr
-    const float2* tw_y6;             // 96, 128, 144: shorter column grids of the register darkfield
+    const float2* tw_y6;             // 96, 128, 144, 160: shorter grids of the register darkfield
     const float2* tw_y8;
     const float2* tw_y9;
+    const float2* tw_y10;
 };
 
 // Scratch sizes and grids decided at plan creation.

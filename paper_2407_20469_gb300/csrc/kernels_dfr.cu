@@ -115,6 +115,10 @@ struct OutStart {       // s = d = C^H b, x = 0; returns |s|^2
         return v.x * v.x + v.y * v.y;
     }
 };
+struct ValB {           // b on Q
+    const float2* bq;
+    __device__ float2 operator()(int e) const { return bq[e]; }
+};
 struct OutDot {         // w = C^H C d; returns Re <d, w>
     float2* wv;
     const float2* dv;
@@ -513,8 +517,9 @@ __device__ __noinline__ void pass_image_rows(HW w, const float2* tw, const float
 }
 
 // rows of Q holding the column-transformed |p|^2: forward along x, b = bq - (P*P)/m^2
-// on Q (kept in bq), then the rows of b inverse-transformed along x. Ends with __syncthreads.
-template <int B>
+// on Q (kept in bq), then (INV) the rows of b inverse-transformed along x. Ends with
+// __syncthreads.
+template <int B, bool INV>
 __device__ __noinline__ void pass_rows_rhs(HW w, const float2* tw, float2* GQ, int nQ, const int* qrp,
                                            const int* Qx, float2* bq) {
     constexpr int m = 16 * B;
@@ -534,6 +539,7 @@ __device__ __noinline__ void pass_rows_rhs(HW w, const float2* tw, float2* GQ, i
         for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16)
             bq[e] = csub(bq[e], cscale(w.hs[freq_index(Qx[e], m)], inv_m2));
         __syncwarp(w.mask);
+        if constexpr (!INV) continue;
 #pragma unroll
         for (int j = 0; j < B; ++j) w.hs[w.t + 16 * j] = make_float2(0.f, 0.f);
         __syncwarp(w.mask);
@@ -590,7 +596,7 @@ __host__ __device__ inline DFRSmem dfr_smem_layout(int B, int BN, int band_u, in
     L.c = L.x + align16((size_t)max_N * sizeof(float2));
     size_t t = L.c + (size_t)3 * max_N * sizeof(float2);                   // d, s, w
     t += (size_t)2 * (m + n) * sizeof(float2);                            // step twiddles
-    t += (size_t)2 * m * sizeof(float2);                                  // column-grid step twiddles
+    t += (size_t)4 * m * sizeof(float2);                                  // column- and row-grid step twiddles
     t = align16(t) + 64 * sizeof(double);                                 // reductions
     L.total = align16(t);
     return L;
@@ -615,6 +621,7 @@ struct DFCtx {
     HW w;
     const float2* tw_m;     // step twiddles of the rows (16 B points)
     float2* tw_y;           // step twiddles of the image's column grid (filled per image)
+    float2* tw_x;           // step twiddles of the image's row grid (filled per image)
     float2 *GU, *GQ, *PF, *bq;
     float2 *dv, *sv, *wv;
     float2* xv;
@@ -636,48 +643,65 @@ __device__ __forceinline__ void cols_times(const DFCtx& c, const float2* tw, int
         cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesField<BY, CONJ>{c.PF});
 }
 
-__device__ __forceinline__ const float2* column_table(const DevPlan& P, int BY, int B) {
-    return BY == B ? P.tw_r : BY == 6 ? P.tw_y6 : BY == 8 ? P.tw_y8 : P.tw_y9;
+// plain twiddle table of a 16 G-point grid of a solve on the 16 B-point register grid
+__device__ __forceinline__ const float2* grid_table(const DevPlan& P, int G, int B) {
+    return G == B ? P.tw_r : G == 6 ? P.tw_y6 : G == 8 ? P.tw_y8 : G == 9 ? P.tw_y9 : P.tw_y10;
 }
 
-// Solve of one darkfield image once b = F(I) on Q is in bq: rows on the 16 B
-// grid, columns on a 16 BY grid (BY <= B, chosen at plan time as the shortest on
+// Solve of one darkfield image once b = F(I) on Q is in bq, on a grid of 16 BX rows
+// points x 16 BY column points (chosen at plan time, <= 16 B each, as the cheapest on
 // which both correlations of Eq. 13 are free of aliasing). P * P, whose lags reach
-// further, is formed on the 16 B grid. Returns the CG iterations (negative: did
-// not converge).
-template <int B, int BY>
+// further, is formed on the 16 B x 16 B grid. Returns the CG iterations (negative:
+// did not converge).
+template <int B, int BX, int BY>
 __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const DevDF& D, float2* sp, const float* ph,
-                                     int iters, float tol) {
-    constexpr int m = 16 * B, my = 16 * BY, LDU = m + 1;
+                                        int iters, float tol) {
+    constexpr int m = 16 * B, mx = 16 * BX, my = 16 * BY, LDU = m + 1;
     const HW& w = c.w;
     const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
     const int uy0 = D.uy0, qy0 = D.qy0, py0 = D.py0;
     const int N = D.N, nU = D.uy1 - uy0 + 1, nQ = D.qy1 - qy0 + 1, nP = D.py1 - py0 + 1;
     const int *urp = P.d_rowptr + D.urp, *qrp = P.d_rowptr + D.qrp, *prp = P.d_rowptr + D.prp;
     const unsigned* qmask = P.d_qmask + D.qmask_off;
-    const float2* twc = c.tw_m;
+    const ValKnown pval{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off};
+    const float2* twy = c.tw_m;
     if (BY != B) {
-        make_step_twiddles(c.tw_y, column_table(P, BY, B), BY);
-        twc = c.tw_y;
+        make_step_twiddles(c.tw_y, grid_table(P, BY, B), BY);
+        twy = c.tw_y;
     }
-    // band rows of the known field P (Eq. 11) along x, staged in GQ
-    pass_rows_in<B>(w, c.tw_m, c.GQ, m, nP, prp, P.dP_x + p_off,
-                    ValKnown{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off});
+    const float2* twx = c.tw_m;
+    if (BX != B) {
+        make_step_twiddles(c.tw_x, grid_table(P, BX, B), BX);
+        twx = c.tw_x;
+        __syncthreads();
+    }
+    // band rows of the known field P (Eq. 11) along x on the row grid, staged in GQ
+    // (row stride mx), then p s on the column grid (s = 1 / (mx my): the two
+    // unnormalised transforms around each product)
+    pass_rows_in<BX>(w, twx, c.GQ, mx, nP, prp, P.dP_x + p_off, pval);
     __syncthreads();
-    // p s on the column grid (s = 1 / (m my): the two unnormalised transforms around
-    // each product), then b -= P * P on Q (16 B grid), rows of b inverse along x
-    const float scale = 1.f / ((float)m * (float)my);
+    const float scale = 1.f / ((float)mx * (float)my);
     if constexpr (2 * BY <= 16 && kTmemField) {
-        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreFieldT{c.tm, scale});
+        cols<BY>(w, twy, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, MidStoreFieldT{c.tm, scale});
         tmem_wait_st();
     } else {
-        cols<BY>(w, twc, m, c.GQ, m, py0, nP, c.GQ, m, 0, 0, MidStoreField<BY>{c.PF, scale});
+        cols<BY>(w, twy, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, MidStoreField<BY>{c.PF, scale});
     }
-    cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
-    pass_rows_rhs<B>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
+    // b -= P * P on Q (16 B grid), then the rows of b inverse along x on the row grid
+    if constexpr (BX == B) {
+        cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
+        pass_rows_rhs<B, true>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
+    } else {
+        pass_rows_in<B>(w, c.tw_m, c.GQ, m, nP, prp, P.dP_x + p_off, pval);
+        __syncthreads();
+        cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
+        pass_rows_rhs<B, false>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
+        pass_rows_in<BX>(w, twx, c.GQ, mx, nQ, qrp, P.dQ_x + q_off, ValB{c.bq});
+        __syncthreads();
+    }
     // s = d = C^H b
-    cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU);
-    const float g0 = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
+    cols_times<BY, false>(c, twy, mx, c.GQ, mx, qy0, nQ, c.GU, LDU, uy0, nU);
+    const float g0 = pass_rows_out<BX>(w, twx, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
     int par = 0;
     const double gamma0 = block_sum2f(g0, c.red, par);
     // CGNR
@@ -687,12 +711,12 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     int it = 0;
     float bf = 0.f;                  // first direction: d = s
     for (; it < iters && !conv; ++it) {
-        pass_rows_in<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{c.sv, c.dv, bf});
+        pass_rows_in<BX>(w, twx, c.GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{c.sv, c.dv, bf});
         __syncthreads();
-        cols_times<BY, true>(c, twc, m, c.GU, LDU, uy0, nU, c.GQ, m, qy0, nQ);
-        pass_rows_mask<B>(w, c.tw_m, c.GQ, nQ, qmask);
-        cols_times<BY, false>(c, twc, m, c.GQ, m, qy0, nQ, c.GU, LDU, uy0, nU);
-        const float dw = pass_rows_out<B>(w, c.tw_m, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
+        cols_times<BY, true>(c, twy, mx, c.GU, LDU, uy0, nU, c.GQ, mx, qy0, nQ);
+        pass_rows_mask<BX>(w, twx, c.GQ, nQ, qmask);
+        cols_times<BY, false>(c, twy, mx, c.GQ, mx, qy0, nQ, c.GU, LDU, uy0, nU);
+        const float dw = pass_rows_out<BX>(w, twx, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
         const double delta = block_sum2f(dw, c.red, par);
         if (!(delta > 0)) break;
         const double alpha = gamma / delta;
@@ -744,9 +768,10 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
     float2* tw_m = c.wv + P.max_N;
     float2* tw_n = tw_m + 2 * m;
     c.tw_y = tw_n + 2 * n;
+    c.tw_x = c.tw_y + 2 * m;
     c.red = reinterpret_cast<double*>(sbase + align16(SL.c + (size_t)3 * P.max_N * sizeof(float2) +
                                                       (size_t)2 * (m + n) * sizeof(float2) +
-                                                      (size_t)2 * m * sizeof(float2)));
+                                                      (size_t)4 * m * sizeof(float2)));
     c.tw_m = tw_m;
 
     make_step_twiddles(tw_m, P.tw_r, B);
@@ -799,15 +824,18 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
             pass_image_cols<BN>(wn, tw_n, stage, img, c.PF, D.qy0, nQ, D.tr != 0);
             pass_image_rows<BN>(wn, tw_n, c.PF, nQ, P.d_rowptr + D.qrp, P.dQ_x + D.q_off, c.bq);
             int r;
-            if constexpr (B == 12) {
-                switch (D.by) {
-                    case 6: r = df_solve<B, 6>(c, P, D, sp, ph, iters, tol); break;
-                    case 8: r = df_solve<B, 8>(c, P, D, sp, ph, iters, tol); break;
-                    case 9: r = df_solve<B, 9>(c, P, D, sp, ph, iters, tol); break;
-                    default: r = df_solve<B, B>(c, P, D, sp, ph, iters, tol); break;
+            if constexpr (B == 12) {     // the (row, column) grids the plan chooses from
+                switch (16 * D.bx + D.by) {
+                    case 16 * 12 + 6: r = df_solve<B, 12, 6>(c, P, D, sp, ph, iters, tol); break;
+                    case 16 * 12 + 8: r = df_solve<B, 12, 8>(c, P, D, sp, ph, iters, tol); break;
+                    case 16 * 12 + 9: r = df_solve<B, 12, 9>(c, P, D, sp, ph, iters, tol); break;
+                    case 16 * 10 + 6: r = df_solve<B, 10, 6>(c, P, D, sp, ph, iters, tol); break;
+                    case 16 * 10 + 8: r = df_solve<B, 10, 8>(c, P, D, sp, ph, iters, tol); break;
+                    case 16 * 9 + 9: r = df_solve<B, 9, 9>(c, P, D, sp, ph, iters, tol); break;
+                    default: r = df_solve<B, B, B>(c, P, D, sp, ph, iters, tol); break;
                 }
             } else {
-                r = df_solve<B, B>(c, P, D, sp, ph, iters, tol);
+                r = df_solve<B, B, B>(c, P, D, sp, ph, iters, tol);
             }
             if (r < 0) notconv = true;
             if (threadIdx.x == 0 && counters) {

@@ -155,6 +155,29 @@ struct DFT<3, INV> {
 };
 
 template <bool INV>
+struct DFT<5, INV> {
+    static __device__ __forceinline__ void run(float2 (&a)[5]) {
+        // with t1 = a1 + a4, t2 = a2 + a3, t3 = a1 - a4, t4 = a2 - a3 and W = exp(-2 pi i / 5):
+        // X1,4 = a0 + c1 t1 + c2 t2 -/+ i (s1 t3 + s2 t4), X2,3 = a0 + c2 t1 + c1 t2 -/+ i (s2 t3 - s1 t4)
+        // (forward; c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5); the inverse swaps the signs of i)
+        constexpr float c1 = cx::wre(1, 5), c2 = cx::wre(2, 5), s1 = -cx::wim(1, 5), s2 = -cx::wim(2, 5);
+        const float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]), t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+        const float2 m1 = make_float2(a[0].x + c1 * t1.x + c2 * t2.x, a[0].y + c1 * t1.y + c2 * t2.y);
+        const float2 m2 = make_float2(a[0].x + c2 * t1.x + c1 * t2.x, a[0].y + c2 * t1.y + c1 * t2.y);
+        const float2 n1 = make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+        const float2 n2 = make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+        // -i n = (n.y, -n.x)
+        const float2 r1 = INV ? make_float2(-n1.y, n1.x) : make_float2(n1.y, -n1.x);
+        const float2 r2 = INV ? make_float2(-n2.y, n2.x) : make_float2(n2.y, -n2.x);
+        a[0] = cadd(a[0], cadd(t1, t2));
+        a[1] = cadd(m1, r1);
+        a[4] = csub(m1, r1);
+        a[2] = cadd(m2, r2);
+        a[3] = csub(m2, r2);
+    }
+};
+
+template <bool INV>
 struct DFT<4, INV> {
     static __device__ __forceinline__ void run(float2 (&a)[4]) {
         const float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]), t2 = cadd(a[1], a[3]);
