@@ -102,6 +102,7 @@ struct apic_plan {
         cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
         cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
         cudaEvent_t in_tail = nullptr, early = nullptr;   // one-chunk order
+        cudaEvent_t part[4] = {};                          // one-chunk order: the full waves' inputs in parts
         float* d_in[2] = {};
         float* d_field[2] = {};
         float* d_zern[2] = {};
@@ -563,10 +564,17 @@ apic_status learned_buffers(apic_plan* p) {
 
 // Where the host pipeline joins the order of one chunk (reconstruct): wait_main
 // is waited on before the first stage of the full waves' tiles, early_done is
-// recorded once the fields of tiles [0, ma) and [m0, nt) are synthesized.
+// recorded once the fields of tiles [0, ma) and [m0, nt) are synthesized. With
+// parts > 0 (split order only) the full waves' tiles arrive in parts instead:
+// tiles [part_end[g - 1], part_end[g]) are ready at part_ready[g], and each part's
+// earlier stages start as soon as it is in.
 struct SplitHooks {
+    static constexpr int kMaxParts = 4;   // = the host pipeline's part events
     cudaEvent_t wait_main = nullptr;
     cudaEvent_t early_done = nullptr;
+    int parts = 0;
+    int part_end[kMaxParts] = {};
+    cudaEvent_t part_ready[kMaxParts] = {};
 };
 
 // Partial-wave geometry of a chunk of nt tiles: r trailing tiles (0: no split),
@@ -615,9 +623,9 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
         // for the partial wave (a = m0) and then for the full waves (a = 0), so a stage's
         // interval starts with the first call and ends with the call for a = 0
         bool pre_first = true;
-        auto pre_df = [&](int a, int k) -> apic_status {
+        auto pre_df = [&](int a, int k, bool final) -> apic_status {
             if (k == 0) return APIC_OK;
-            const bool mark0 = first && pre_first, mark1 = last && a == 0;
+            const bool mark0 = first && pre_first, mark1 = last && final;
             pre_first = false;
             float2* xd = plan->xdisc + (size_t)a * D.n_bf * D.npup;
             float* ph = plan->phi + (size_t)a * D.npup;
@@ -666,18 +674,28 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             APIC_TRY_LAUNCH(launch_background(D, r, It + (size_t)m0 * in_tile, plan->c2 + m0, stt + m0, thresh2, st,
                                               replace ? 1 : 0));
             if ((s = learned_part(m0, r)) != APIC_OK) return s;
-            if ((s = pre_df(m0, r)) != APIC_OK) return s;
+            if ((s = pre_df(m0, r, false)) != APIC_OK) return s;
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_fork, st));
             if (first) tm.mark(4, 0);
             APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
             APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)m0 * in_tile, plan->phi + (size_t)m0 * D.npup,
                                          plan->spec + (size_t)m0 * D.nap, stt + m0, true, plan->side, r));
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_tail, plan->side));
-            if (hk && hk->wait_main) APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
-            APIC_TRY_LAUNCH(launch_background(D, m0, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
-            if (last) tm.mark(0, 1);
-            if ((s = learned_part(0, m0)) != APIC_OK) return s;
-            if ((s = pre_df(0, m0)) != APIC_OK) return s;
+            const int parts = hk && hk->parts > 0 ? hk->parts : 1;
+            for (int g = 0, a = 0; g < parts; ++g) {
+                const int b = hk && hk->parts > 0 ? hk->part_end[g] : m0;
+                if (hk && hk->parts > 0) {
+                    APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->part_ready[g], 0));
+                } else if (hk && hk->wait_main) {
+                    APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
+                }
+                APIC_TRY_LAUNCH(launch_background(D, b - a, It + (size_t)a * in_tile, plan->c2 + a, stt + a, thresh2,
+                                                  st, replace ? 1 : 0));
+                if (last && g == parts - 1) tm.mark(0, 1);
+                if ((s = learned_part(a, b - a)) != APIC_OK) return s;
+                if ((s = pre_df(a, b - a, g == parts - 1)) != APIC_OK) return s;
+                a = b;
+            }
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
             APIC_TRY_LAUNCH(launch_df_on(plan, ma, It, plan->phi, plan->spec, stt, false, st, W - r));
             APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_pre, 0));
@@ -701,7 +719,7 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
             if (last) tm.mark(0, 1);
             if ((s = learned_part(0, nt)) != APIC_OK) return s;
-            if ((s = pre_df(0, nt)) != APIC_OK) return s;
+            if ((s = pre_df(0, nt, true)) != APIC_OK) return s;
             if (first) tm.mark(4, 0);
             APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
             if (last) tm.mark(4, 1);
@@ -832,6 +850,8 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         }
         if (io.in_tail) cudaEventDestroy(io.in_tail);
         if (io.early) cudaEventDestroy(io.early);
+        for (cudaEvent_t e : io.part)
+            if (e) cudaEventDestroy(e);
         if (io.s_in) cudaStreamDestroy(io.s_in);
         if (io.s_comp) cudaStreamDestroy(io.s_comp);
         if (io.s_out) cudaStreamDestroy(io.s_out);
@@ -1121,6 +1141,7 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
         APIC_TRY_CUDA(stream(io.s_out));
         APIC_TRY_CUDA(event(io.in_tail));
         APIC_TRY_CUDA(event(io.early));
+        for (auto& e : io.part) APIC_TRY_CUDA(event(e));
         for (int b = 0; b < 2; ++b) {
             APIC_TRY_CUDA(event(io.in_done[b]));
             APIC_TRY_CUDA(event(io.comp_done[b]));
@@ -1148,18 +1169,33 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
         float* dI = io.d_in[0];
         float* dF = io.d_field[0];
         const size_t fbytes = out_tile * sizeof(float2);
+        SplitHooks hk;
+        hk.early_done = io.early;
         if (r > 0) {
             APIC_TRY_CUDA(cudaMemcpyAsync(dI + (size_t)m0 * in_tile, h_I + (size_t)m0 * in_tile,
                                           (size_t)r * in_tile * sizeof(float), cudaMemcpyHostToDevice, io.s_in));
             APIC_TRY_CUDA(cudaEventRecord(io.in_tail, io.s_in));
+            // the full waves' tiles in parts of about one wave, so that each part's
+            // earlier stages overlap the copies of the next
+            static_assert(sizeof(io.part) / sizeof(io.part[0]) == SplitHooks::kMaxParts, "one event per part");
+            const int parts = std::min(SplitHooks::kMaxParts, std::max(1, (m0 + wave - 1) / wave));
+            for (int g = 0, a = 0; g < parts; ++g) {
+                const int b = (int)((long long)m0 * (g + 1) / parts);
+                APIC_TRY_CUDA(cudaMemcpyAsync(dI + (size_t)a * in_tile, h_I + (size_t)a * in_tile,
+                                              (size_t)(b - a) * in_tile * sizeof(float), cudaMemcpyHostToDevice,
+                                              io.s_in));
+                APIC_TRY_CUDA(cudaEventRecord(io.part[g], io.s_in));
+                hk.part_end[g] = b;
+                hk.part_ready[g] = io.part[g];
+                a = b;
+            }
+            hk.parts = parts;
+        } else {
+            APIC_TRY_CUDA(cudaMemcpyAsync(dI, h_I, (size_t)m0 * in_tile * sizeof(float), cudaMemcpyHostToDevice,
+                                          io.s_in));
         }
-        APIC_TRY_CUDA(cudaMemcpyAsync(dI, h_I, (size_t)m0 * in_tile * sizeof(float), cudaMemcpyHostToDevice,
-                                      io.s_in));
         APIC_TRY_CUDA(cudaEventRecord(io.in_done[0], io.s_in));
         APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_comp, r > 0 ? io.in_tail : io.in_done[0], 0));
-        SplitHooks hk;
-        hk.wait_main = r > 0 ? io.in_done[0] : nullptr;
-        hk.early_done = io.early;
         s = reconstruct(plan, nullptr, 0, n_tiles, dI, nullptr, dF, io.d_zern[0], nullptr, io.d_status[0], io.s_comp,
                         &hk);
         if (s != APIC_OK) return s;
