@@ -103,6 +103,7 @@ struct apic_plan {
         cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
         cudaEvent_t in_tail = nullptr, early = nullptr;   // one-chunk order
         cudaEvent_t part[4] = {};                          // one-chunk order: the full waves' inputs in parts
+        cudaEvent_t rdone[4] = {};                         // one-chunk order: fields of the first group's rounds
         float* d_in[2] = {};
         float* d_field[2] = {};
         float* d_zern[2] = {};
@@ -114,7 +115,7 @@ struct apic_plan {
     int grid_kkr = 0;
     // second stream for the last partial darkfield wave of a batch (see reconstruct)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr, ev_pre = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr, ev_pre = nullptr, ev_mbe = nullptr;
     float* feat = nullptr;                       // learned path: features, network coefficients
     float* c_net = nullptr;
     unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
@@ -468,6 +469,7 @@ apic_status alloc_workspace(apic_plan* p) {
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_tail, cudaEventDisableTiming));
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_pre, cudaEventDisableTiming));
+    APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_mbe, cudaEventDisableTiming));
     return APIC_OK;
 }
 
@@ -563,27 +565,33 @@ apic_status learned_buffers(apic_plan* p) {
 }
 
 // Where the host pipeline joins the order of one chunk (reconstruct): wait_main
-// is waited on before the first stage of the full waves' tiles, early_done is
-// recorded once the fields of tiles [0, ma) and [m0, nt) are synthesized. With
-// parts > 0 (split order only) the full waves' tiles arrive in parts instead:
-// tiles [part_end[g - 1], part_end[g]) are ready at part_ready[g], and each part's
-// earlier stages start as soon as it is in.
+// is waited on before the first stage of the full waves' tiles. Plain order:
+// early_done is recorded once all fields are synthesized. Split order:
+// field_ready[k] (when set) is recorded once the fields of MA's round k, tiles
+// [k wa, (k + 1) wa) with wa = W - r, are synthesized, together with those of T
+// = [m0, nt) after round 0 and of [ma, ml) after the last round; the fields
+// [ml, m0) are synthesized last. With parts > 0 (split order only) the full
+// waves' tiles arrive in parts: tiles [part_end[g - 1], part_end[g]) are ready
+// at part_ready[g], and each part's earlier stages start as soon as it is in.
 struct SplitHooks {
-    static constexpr int kMaxParts = 4;   // = the host pipeline's part events
+    static constexpr int kMaxParts = 4;   // = the host pipeline's part and round events
     cudaEvent_t wait_main = nullptr;
     cudaEvent_t early_done = nullptr;
     int parts = 0;
     int part_end[kMaxParts] = {};
     cudaEvent_t part_ready[kMaxParts] = {};
+    cudaEvent_t field_ready[kMaxParts] = {};
 };
 
 // Partial-wave geometry of a chunk of nt tiles: r trailing tiles (0: no split),
-// m0 = nt - r, and ma, the full waves' tiles that go to the W - r blocks.
-void split_geometry(const apic_plan* p, int nt, int& r, int& m0, int& ma) {
+// m0 = nt - r, ma, the full waves' tiles that go to the W - r blocks, and ml, the
+// first tile of the r blocks' last round (= ma when they take a single round).
+void split_geometry(const apic_plan* p, int nt, int& r, int& m0, int& ma, int& ml) {
     const int W = df_wave(p);
     r = (p->dev.n_used > 0 && nt > W) ? nt % W : 0;
     m0 = nt - r;
     ma = r > 0 ? (W - r) * (m0 / W) : m0;
+    ml = r > 0 && m0 - ma > r ? m0 - r : ma;
 }
 
 // Background, Kramers-Kronig, aberration (learned when `net`), stitching,
@@ -595,11 +603,12 @@ void split_geometry(const apic_plan* p, int nt, int& r, int& m0, int& ma) {
 // trailing tiles go first: their earlier stages run, their darkfield solves
 // start on a high-priority second stream (own scratch blocks), and meanwhile
 // the earlier stages of the other tiles run on the remaining SMs. Those tiles
-// then go to two launches sized so that each block takes the same number of
-// tiles: W - r blocks on the caller's stream (they start right away) and r
-// blocks on the second stream (they start where the partial wave ends); the
-// first group's synthesis runs while the second group finishes. Every tile
-// gets exactly the computation of the plain order.
+// then go to W - r blocks on the caller's stream (they start right away) and r
+// blocks on the second stream (they start where the partial wave ends), one
+// launch per round of one tile per block, so that each block takes the same
+// number of tiles; every round's fields but those of the second group's last
+// round are synthesized while later rounds run. Every tile gets exactly the
+// computation of the plain order.
 apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, const float* I, const float* uv,
                         float* field, float* zern, float* pupil, int32_t* status, cudaStream_t st,
                         const SplitHooks* hk = nullptr) {
@@ -617,8 +626,8 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
         const float* It = I + (size_t)t0 * in_tile;
         int32_t* stt = status ? status + t0 : plan->status;
         float* zt = zern + (size_t)t0 * APIC_N_ZERNIKE;
-        int r = 0, m0 = nt, ma = nt;     // partial-wave tiles, full-wave tiles, their first group
-        split_geometry(plan, nt, r, m0, ma);
+        int r = 0, m0 = nt, ma = nt, ml = nt;   // partial wave, full waves, their groups
+        split_geometry(plan, nt, r, m0, ma, ml);
         // earlier stages of tiles [a, a + k) of the chunk; in the split order this runs
         // for the partial wave (a = m0) and then for the full waves (a = 0), so a stage's
         // interval starts with the first call and ends with the call for a = 0
@@ -668,8 +677,10 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             // Tiles of the full waves split into MA = [0, ma) on W - r blocks and
             // MB = [ma, m0) on r blocks (k tiles per block each); T = [m0, nt) is the
             // partial wave. Caller's stream: T's earlier stages, then (fork) the full
-            // waves' background and earlier stages, MA's darkfield, synthesis of MA and
-            // T. Second stream: T's darkfield, then MB's darkfield and synthesis (join).
+            // waves' background and earlier stages, MA's darkfield rounds, each followed
+            // by its synthesis (T's after the first, ML = [ma, ml) after the last).
+            // Second stream: T's darkfield, then MB's darkfield rounds and the synthesis
+            // of its last round (join).
             if (first) tm.mark(0, 0);
             APIC_TRY_LAUNCH(launch_background(D, r, It + (size_t)m0 * in_tile, plan->c2 + m0, stt + m0, thresh2, st,
                                               replace ? 1 : 0));
@@ -697,19 +708,41 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                 a = b;
             }
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
-            APIC_TRY_LAUNCH(launch_df_on(plan, ma, It, plan->phi, plan->spec, stt, false, st, W - r));
             APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_pre, 0));
-            APIC_TRY_LAUNCH(launch_df_on(plan, m0 - ma, It + (size_t)ma * in_tile, plan->phi + (size_t)ma * D.npup,
-                                         plan->spec + (size_t)ma * D.nap, stt + ma, true, plan->side, r));
-            APIC_TRY_LAUNCH(launch_synthesize(D, L, m0 - ma, plan->spec + (size_t)ma * D.nap,
-                                              fld + (size_t)ma * out_tile, stt + ma, plan->side));
+            // MB one round (r tiles, one per block) per launch: the rounds before the
+            // last are synthesized on the caller's stream with MA, so that only the
+            // last round's fields remain once the second stream ends
+            for (int a = ma; a < m0; a += r) {
+                APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)a * in_tile, plan->phi + (size_t)a * D.npup,
+                                             plan->spec + (size_t)a * D.nap, stt + a, true, plan->side, r));
+                if (a + r == ml) APIC_TRY_CUDA(cudaEventRecord(plan->ev_mbe, plan->side));
+            }
+            APIC_TRY_LAUNCH(launch_synthesize(D, L, m0 - ml, plan->spec + (size_t)ml * D.nap,
+                                              fld + (size_t)ml * out_tile, stt + ml, plan->side));
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_join, plan->side));
-            APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_tail, 0));
-            if (first) tm.mark(5, 0);
-            APIC_TRY_LAUNCH(launch_synthesize(D, L, ma, plan->spec, fld, stt, st));
-            APIC_TRY_LAUNCH(launch_synthesize(D, L, r, plan->spec + (size_t)m0 * D.nap, fld + (size_t)m0 * out_tile,
-                                              stt + m0, st));
-            if (hk && hk->early_done) APIC_TRY_CUDA(cudaEventRecord(hk->early_done, st));
+            // MA one round (W - r tiles, one per block) per launch, each round's fields
+            // synthesized right after it (T's after the first round, [ma, ml) after the
+            // last), so that a host pipeline can copy them out while the rest runs
+            const int wa = W - r;
+            for (int a = 0, k = 0; a < ma; a += wa, ++k) {
+                APIC_TRY_LAUNCH(launch_df_on(plan, wa, It + (size_t)a * in_tile, plan->phi + (size_t)a * D.npup,
+                                             plan->spec + (size_t)a * D.nap, stt + a, false, st, wa));
+                if (first && k == 0) tm.mark(5, 0);
+                APIC_TRY_LAUNCH(launch_synthesize(D, L, wa, plan->spec + (size_t)a * D.nap, fld + (size_t)a * out_tile,
+                                                  stt + a, st));
+                if (k == 0) {
+                    APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_tail, 0));
+                    APIC_TRY_LAUNCH(launch_synthesize(D, L, r, plan->spec + (size_t)m0 * D.nap,
+                                                      fld + (size_t)m0 * out_tile, stt + m0, st));
+                }
+                if (a + wa == ma && ml > ma) {
+                    APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_mbe, 0));
+                    APIC_TRY_LAUNCH(launch_synthesize(D, L, ml - ma, plan->spec + (size_t)ma * D.nap,
+                                                      fld + (size_t)ma * out_tile, stt + ma, st));
+                }
+                if (hk && k < SplitHooks::kMaxParts && hk->field_ready[k])
+                    APIC_TRY_CUDA(cudaEventRecord(hk->field_ready[k], st));
+            }
             APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_join, 0));
             if (last) tm.mark(4, 1);
             if (last) tm.mark(5, 1);
@@ -842,6 +875,7 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         if (plan->ev_join) cudaEventDestroy(plan->ev_join);
         if (plan->ev_tail) cudaEventDestroy(plan->ev_tail);
         if (plan->ev_pre) cudaEventDestroy(plan->ev_pre);
+        if (plan->ev_mbe) cudaEventDestroy(plan->ev_mbe);
         auto& io = plan->io;
         for (int b = 0; b < 2; ++b) {
             if (io.in_done[b]) cudaEventDestroy(io.in_done[b]);
@@ -851,6 +885,8 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         if (io.in_tail) cudaEventDestroy(io.in_tail);
         if (io.early) cudaEventDestroy(io.early);
         for (cudaEvent_t e : io.part)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : io.rdone)
             if (e) cudaEventDestroy(e);
         if (io.s_in) cudaStreamDestroy(io.s_in);
         if (io.s_comp) cudaStreamDestroy(io.s_comp);
@@ -1142,6 +1178,7 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
         APIC_TRY_CUDA(event(io.in_tail));
         APIC_TRY_CUDA(event(io.early));
         for (auto& e : io.part) APIC_TRY_CUDA(event(e));
+        for (auto& e : io.rdone) APIC_TRY_CUDA(event(e));
         for (int b = 0; b < 2; ++b) {
             APIC_TRY_CUDA(event(io.in_done[b]));
             APIC_TRY_CUDA(event(io.comp_done[b]));
@@ -1161,11 +1198,11 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
     }
     if (n_tiles <= io.chunk) {
         // One chunk, copies woven into its order: the partial darkfield wave's
-        // inputs go first and its stages start while the other inputs copy; the
-        // fields of the tiles synthesized early copy out while the last darkfield
-        // group finishes.
-        int r = 0, m0 = n_tiles, ma = n_tiles;
-        split_geometry(plan, n_tiles, r, m0, ma);
+        // inputs go first and its stages start while the other inputs copy; each
+        // darkfield round's fields copy out as soon as they are synthesized, so that
+        // only the last round's remain once the computation ends.
+        int r = 0, m0 = n_tiles, ma = n_tiles, ml = n_tiles;
+        split_geometry(plan, n_tiles, r, m0, ma, ml);
         float* dI = io.d_in[0];
         float* dF = io.d_field[0];
         const size_t fbytes = out_tile * sizeof(float2);
@@ -1190,6 +1227,10 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
                 a = b;
             }
             hk.parts = parts;
+            for (int k = 0; k < m0 / wave; ++k) {
+                if (k >= SplitHooks::kMaxParts) return fail(APIC_EINTERNAL, "too many darkfield rounds in a chunk");
+                hk.field_ready[k] = io.rdone[k];
+            }
         } else {
             APIC_TRY_CUDA(cudaMemcpyAsync(dI, h_I, (size_t)m0 * in_tile * sizeof(float), cudaMemcpyHostToDevice,
                                           io.s_in));
@@ -1200,15 +1241,26 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
                         &hk);
         if (s != APIC_OK) return s;
         APIC_TRY_CUDA(cudaEventRecord(io.comp_done[0], io.s_comp));
-        APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.early, 0));
-        APIC_TRY_CUDA(cudaMemcpyAsync(h_field, dF, (size_t)ma * fbytes, cudaMemcpyDeviceToHost, io.s_out));
-        if (r > 0)
-            APIC_TRY_CUDA(cudaMemcpyAsync(h_field + (size_t)m0 * out_tile * 2, dF + (size_t)m0 * out_tile * 2,
-                                          (size_t)r * fbytes, cudaMemcpyDeviceToHost, io.s_out));
-        APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.comp_done[0], 0));
-        if (m0 > ma)
-            APIC_TRY_CUDA(cudaMemcpyAsync(h_field + (size_t)ma * out_tile * 2, dF + (size_t)ma * out_tile * 2,
-                                          (size_t)(m0 - ma) * fbytes, cudaMemcpyDeviceToHost, io.s_out));
+        auto fields_out = [&](int a, int k) -> cudaError_t {    // fields of tiles [a, a + k) to the host
+            if (k <= 0) return cudaSuccess;
+            return cudaMemcpyAsync(h_field + (size_t)a * out_tile * 2, dF + (size_t)a * out_tile * 2,
+                                   (size_t)k * fbytes, cudaMemcpyDeviceToHost, io.s_out);
+        };
+        if (r > 0) {
+            const int rounds = m0 / wave, wa = wave - r;
+            for (int k = 0; k < rounds; ++k) {
+                APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.rdone[k], 0));
+                APIC_TRY_CUDA(fields_out(k * wa, wa));
+                if (k == 0) APIC_TRY_CUDA(fields_out(m0, r));
+                if (k == rounds - 1) APIC_TRY_CUDA(fields_out(ma, ml - ma));
+            }
+            APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.comp_done[0], 0));
+            APIC_TRY_CUDA(fields_out(ml, m0 - ml));
+        } else {
+            APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.early, 0));
+            APIC_TRY_CUDA(fields_out(0, n_tiles));
+            APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.comp_done[0], 0));
+        }
         APIC_TRY_CUDA(cudaMemcpyAsync(h_zern, io.d_zern[0], (size_t)n_tiles * APIC_N_ZERNIKE * sizeof(float),
                                       cudaMemcpyDeviceToHost, io.s_out));
         if (h_status)
