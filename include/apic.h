@@ -158,6 +158,16 @@ apic_status apic_plan_df_set(const apic_plan* plan, int index, int which, int32_
                              int32_t* h_meta);
 
 /*
+ * Frame and transform grid of the darkfield solve of image `index` (processing
+ * order; an implementation choice that leaves Eq. 13 unchanged): h_grid[3]
+ * receives {1 if the image is solved with x and y swapped else 0, row grid
+ * points, column grid points of the register-FFT kernel in the solve frame,
+ * both exact for the correlations of that image (0 when the plan has no
+ * register grid)}; {0, 0, 0} for a skipped image. Accepts a host-only plan.
+ */
+apic_status apic_plan_df_grid(const apic_plan* plan, int index, int32_t* h_grid);
+
+/*
  * Whole per-tile reconstruction (Sec. 2.3, Fig. 2), for n_tiles tiles:
  *   d_intensity  [n_tiles][n_bf + n_df][h][w] float32 intensity stacks
  *   d_field      [n_tiles][u h][u w] complex64 out: high-resolution field

@@ -195,14 +195,9 @@ apic_status upload(apic_plan* plan) {
         e.N = (int)d.U_x.size();
         e.M = (int)d.Q_x.size();
         e.NP = (int)d.P_x.size();
-        // Solve frame: an image whose lag set is narrower along x than along y is
-        // solved transposed (x <-> y in every set and in the image), so the row
-        // bands the darkfield passes walk are the shorter ones. The problem is
-        // symmetric under the swap; points are re-sorted by their new rows.
-        auto extent = [](const std::vector<int>& v) {
-            return v.empty() ? 0 : *std::max_element(v.begin(), v.end()) - *std::min_element(v.begin(), v.end()) + 1;
-        };
-        const bool tr = extent(d.Q_x) < extent(d.Q_y);
+        // Solve frame and grid chosen with the host plan (x <-> y swapped in every
+        // set and in the image when d.solve_tr); points are re-sorted by their new rows.
+        const bool tr = d.solve_tr != 0;
         e.tr = tr ? 1 : 0;
         struct Set {
             std::vector<int> x, y, pup, ap;
@@ -229,37 +224,8 @@ apic_status upload(apic_plan* plan) {
         const Set Us = frame(d.U_x, d.U_y, &d.U_pup, &d.U_ap);
         const Set Ps = frame(d.P_x, d.P_y, &d.P_pup, &d.P_ap);
         const Set Qs = frame(d.Q_x, d.Q_y, nullptr, nullptr);
-        // Grid of the register solve: along each axis the correlations of Eq. 13 are
-        // exact on a circular grid of L points when C u (U with P, read on Q) has no
-        // q - p - k (q in U, p in P, k in Q) that is a nonzero multiple of L and C^H r
-        // (Q with P, read on U) no such k + p - q; every band must also fit. Of the
-        // supported (row, column) grids 16 bx x 16 by that are exact for the image, the
-        // one with the least estimated work per iteration (columns x relative cost of a
-        // column: paired 96 / 128 points, 144 and 192 points taken in turn) is used.
-        // P * P, whose lags reach further, stays on the mr x mr grid.
-        e.bx = e.by = mr / 16;
-        if (mr == 192 && !Us.y.empty() && !Ps.y.empty() && !Qs.y.empty()) {
-            auto need = [](const std::vector<int>& U, const std::vector<int>& Pv, const std::vector<int>& Q) {
-                auto mm = [](const std::vector<int>& v) { return std::minmax_element(v.begin(), v.end()); };
-                const auto u = mm(U), pp = mm(Pv), q = mm(Q);
-                const int u0 = *u.first, u1 = *u.second, p0 = *pp.first, p1 = *pp.second, q0 = *q.first,
-                          q1 = *q.second;
-                const int need_c = std::max(std::abs(u0 - p1 - q1), std::abs(u1 - p0 - q0)) + 1;
-                const int need_ch = std::max(std::abs(q0 + p0 - u1), std::abs(q1 + p1 - u0)) + 1;
-                return std::max({need_c, need_ch, u1 - u0 + 1, p1 - p0 + 1, q1 - q0 + 1});
-            };
-            const int nx = need(Us.x, Ps.x, Qs.x), ny = need(Us.y, Ps.y, Qs.y);
-            struct Grid { int bx, by; double col_cost; };
-            static const Grid grids[] = {{12, 12, 2.0}, {12, 9, 1.68}, {12, 8, 1.13}, {12, 6, 1.0},
-                                         {10, 8, 1.13}, {10, 6, 1.0},  {9, 9, 1.68}};
-            double best = 1e300;
-            for (const Grid& g : grids)
-                if (16 * g.bx >= nx && 16 * g.by >= ny && 16 * g.bx * g.col_cost < best) {
-                    best = 16 * g.bx * g.col_cost;
-                    e.bx = g.bx;
-                    e.by = g.by;
-                }
-        }
+        e.bx = d.solve_mx / 16;
+        e.by = d.solve_my / 16;
         e.u_off = (int)ux.size();
         e.p_off = (int)px.size();
         e.q_off = (int)qx.size();
@@ -1007,6 +973,17 @@ apic_status apic_plan_df_set(const apic_plan* plan, int index, int which, int32_
         dst[2 * i] = (*xs)[i];
         dst[2 * i + 1] = (*ys)[i];
     }
+    return APIC_OK;
+}
+
+apic_status apic_plan_df_grid(const apic_plan* plan, int index, int32_t* h_grid) {
+    if (!plan || !h_grid) return fail(APIC_EINVAL, "NULL plan or grid");
+    const HostPlan& H = plan->host;
+    if (index < 0 || index >= (int)H.df.size()) return fail(APIC_EINVAL, "darkfield index out of range");
+    const DarkfieldHost& d = H.df[index];
+    h_grid[0] = d.solve_tr;
+    h_grid[1] = d.solve_mx;
+    h_grid[2] = d.solve_my;
     return APIC_OK;
 }
 

@@ -26,6 +26,10 @@ struct DarkfieldHost {
     std::vector<int> U_x, U_y, U_pup, U_ap;   // unknown points, their pupil and aperture index
     std::vector<int> P_x, P_y, P_pup, P_ap;   // known points
     std::vector<int> Q_x, Q_y;                // equation lags (k of Eq. 13)
+    // frame and grid of the register-kernel solve (used images): solved transposed, row grid
+    // points, column grid points (mr x mr unless a shorter supported grid is exact; 0 without
+    // the register grid)
+    int solve_tr = 0, solve_mx = 0, solve_my = 0;
 };
 
 struct HostPlan {
