@@ -102,8 +102,9 @@ struct apic_plan {
         cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
         cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
         cudaEvent_t in_tail = nullptr, early = nullptr;   // one-chunk order
-        cudaEvent_t part[4] = {};                          // one-chunk order: the full waves' inputs in parts
+        cudaEvent_t part[8] = {};                          // one-chunk order: the full waves' inputs in parts
         cudaEvent_t rdone[4] = {};                         // one-chunk order: fields of the first group's rounds
+        cudaEvent_t ml_done = nullptr;                     // one-chunk order: fields of the second group's early rounds
         float* d_in[2] = {};
         float* d_field[2] = {};
         float* d_zern[2] = {};
@@ -535,18 +536,22 @@ apic_status learned_buffers(apic_plan* p) {
 // early_done is recorded once all fields are synthesized. Split order:
 // field_ready[k] (when set) is recorded once the fields of MA's round k, tiles
 // [k wa, (k + 1) wa) with wa = W - r, are synthesized, together with those of T
-// = [m0, nt) after round 0 and of [ma, ml) after the last round; the fields
-// [ml, m0) are synthesized last. With parts > 0 (split order only) the full
-// waves' tiles arrive in parts: tiles [part_end[g - 1], part_end[g]) are ready
-// at part_ready[g], and each part's earlier stages start as soon as it is in.
+// = [m0, nt) after round 0; ml_ready (when set; then on the second stream) once
+// those of ML = [ma, ml) are; the fields [ml, m0) are synthesized last. Without
+// ml_ready ML is synthesized after MA's last round. With parts > 0 (split order
+// only) the full waves' tiles arrive in parts: tiles [part_end[g - 1],
+// part_end[g]) are ready at part_ready[g], and each part's earlier stages start
+// as soon as it is in.
 struct SplitHooks {
-    static constexpr int kMaxParts = 4;   // = the host pipeline's part and round events
+    static constexpr int kMaxParts = 8;    // = the host pipeline's part events
+    static constexpr int kMaxRounds = 4;   // = the host pipeline's round events
     cudaEvent_t wait_main = nullptr;
     cudaEvent_t early_done = nullptr;
     int parts = 0;
     int part_end[kMaxParts] = {};
     cudaEvent_t part_ready[kMaxParts] = {};
-    cudaEvent_t field_ready[kMaxParts] = {};
+    cudaEvent_t field_ready[kMaxRounds] = {};
+    cudaEvent_t ml_ready = nullptr;
 };
 
 // Partial-wave geometry of a chunk of nt tiles: r trailing tiles (0: no split),
@@ -681,7 +686,14 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             for (int a = ma; a < m0; a += r) {
                 APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)a * in_tile, plan->phi + (size_t)a * D.npup,
                                              plan->spec + (size_t)a * D.nap, stt + a, true, plan->side, r));
-                if (a + r == ml) APIC_TRY_CUDA(cudaEventRecord(plan->ev_mbe, plan->side));
+                if (a + r == ml) {
+                    APIC_TRY_CUDA(cudaEventRecord(plan->ev_mbe, plan->side));
+                    if (hk && hk->ml_ready) {     // ML's fields right away, for the host pipeline
+                        APIC_TRY_LAUNCH(launch_synthesize(D, L, ml - ma, plan->spec + (size_t)ma * D.nap,
+                                                          fld + (size_t)ma * out_tile, stt + ma, plan->side));
+                        APIC_TRY_CUDA(cudaEventRecord(hk->ml_ready, plan->side));
+                    }
+                }
             }
             APIC_TRY_LAUNCH(launch_synthesize(D, L, m0 - ml, plan->spec + (size_t)ml * D.nap,
                                               fld + (size_t)ml * out_tile, stt + ml, plan->side));
@@ -701,12 +713,12 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                     APIC_TRY_LAUNCH(launch_synthesize(D, L, r, plan->spec + (size_t)m0 * D.nap,
                                                       fld + (size_t)m0 * out_tile, stt + m0, st));
                 }
-                if (a + wa == ma && ml > ma) {
+                if (a + wa == ma && ml > ma && !(hk && hk->ml_ready)) {
                     APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_mbe, 0));
                     APIC_TRY_LAUNCH(launch_synthesize(D, L, ml - ma, plan->spec + (size_t)ma * D.nap,
                                                       fld + (size_t)ma * out_tile, stt + ma, st));
                 }
-                if (hk && k < SplitHooks::kMaxParts && hk->field_ready[k])
+                if (hk && k < SplitHooks::kMaxRounds && hk->field_ready[k])
                     APIC_TRY_CUDA(cudaEventRecord(hk->field_ready[k], st));
             }
             APIC_TRY_CUDA(cudaStreamWaitEvent(st, plan->ev_join, 0));
@@ -854,6 +866,7 @@ apic_status apic_plan_destroy(apic_plan* plan) {
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : io.rdone)
             if (e) cudaEventDestroy(e);
+        if (io.ml_done) cudaEventDestroy(io.ml_done);
         if (io.s_in) cudaStreamDestroy(io.s_in);
         if (io.s_comp) cudaStreamDestroy(io.s_comp);
         if (io.s_out) cudaStreamDestroy(io.s_out);
@@ -1156,6 +1169,7 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
         APIC_TRY_CUDA(event(io.early));
         for (auto& e : io.part) APIC_TRY_CUDA(event(e));
         for (auto& e : io.rdone) APIC_TRY_CUDA(event(e));
+        APIC_TRY_CUDA(event(io.ml_done));
         for (int b = 0; b < 2; ++b) {
             APIC_TRY_CUDA(event(io.in_done[b]));
             APIC_TRY_CUDA(event(io.comp_done[b]));
@@ -1189,10 +1203,12 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
             APIC_TRY_CUDA(cudaMemcpyAsync(dI + (size_t)m0 * in_tile, h_I + (size_t)m0 * in_tile,
                                           (size_t)r * in_tile * sizeof(float), cudaMemcpyHostToDevice, io.s_in));
             APIC_TRY_CUDA(cudaEventRecord(io.in_tail, io.s_in));
-            // the full waves' tiles in parts of about one wave, so that each part's
-            // earlier stages overlap the copies of the next
+            // the full waves' tiles in parts of about a third of a wave, so that each
+            // part's earlier stages overlap the copies of the next and little is left
+            // to prepare once the last part is in
             static_assert(sizeof(io.part) / sizeof(io.part[0]) == SplitHooks::kMaxParts, "one event per part");
-            const int parts = std::min(SplitHooks::kMaxParts, std::max(1, (m0 + wave - 1) / wave));
+            static_assert(sizeof(io.rdone) / sizeof(io.rdone[0]) == SplitHooks::kMaxRounds, "one event per round");
+            const int parts = std::min(SplitHooks::kMaxParts, std::max(1, (3 * m0 + wave - 1) / wave));
             for (int g = 0, a = 0; g < parts; ++g) {
                 const int b = (int)((long long)m0 * (g + 1) / parts);
                 APIC_TRY_CUDA(cudaMemcpyAsync(dI + (size_t)a * in_tile, h_I + (size_t)a * in_tile,
@@ -1205,9 +1221,10 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
             }
             hk.parts = parts;
             for (int k = 0; k < m0 / wave; ++k) {
-                if (k >= SplitHooks::kMaxParts) return fail(APIC_EINTERNAL, "too many darkfield rounds in a chunk");
+                if (k >= SplitHooks::kMaxRounds) return fail(APIC_EINTERNAL, "too many darkfield rounds in a chunk");
                 hk.field_ready[k] = io.rdone[k];
             }
+            hk.ml_ready = io.ml_done;
         } else {
             APIC_TRY_CUDA(cudaMemcpyAsync(dI, h_I, (size_t)m0 * in_tile * sizeof(float), cudaMemcpyHostToDevice,
                                           io.s_in));
@@ -1224,12 +1241,17 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
                                    (size_t)k * fbytes, cudaMemcpyDeviceToHost, io.s_out);
         };
         if (r > 0) {
+            // in the order the fields become ready: MA's rounds, ML (second stream) before
+            // MA's last round, then the second group's last round
             const int rounds = m0 / wave, wa = wave - r;
             for (int k = 0; k < rounds; ++k) {
+                if (k == rounds - 1 && ml > ma) {
+                    APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.ml_done, 0));
+                    APIC_TRY_CUDA(fields_out(ma, ml - ma));
+                }
                 APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.rdone[k], 0));
                 APIC_TRY_CUDA(fields_out(k * wa, wa));
                 if (k == 0) APIC_TRY_CUDA(fields_out(m0, r));
-                if (k == rounds - 1) APIC_TRY_CUDA(fields_out(ma, ml - ma));
             }
             APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.comp_done[0], 0));
             APIC_TRY_CUDA(fields_out(ml, m0 - ml));

@@ -444,7 +444,8 @@ __device__ __noinline__ void pass_rows_mask(HW w, const float2* tw, float2* G, i
     __syncthreads();
 }
 
-// columns of the real image (n = 16 BN; with tr the transposed image): forward along
+// columns of the real image (n = 16 BN; with tr the transposed image; read once, with
+// evict-first loads that leave the L2-resident band grids in place): forward along
 // y, rows qy0.. (nQ) stored to GX (row length n). Chunks of 32 columns staged through
 // shared memory for coalesced image reads; half-warps 0..31 transform them. Ends with
 // __syncthreads.
@@ -458,12 +459,12 @@ __device__ __noinline__ void pass_image_cols(HW w, const float2* tw, float2* sta
         if (tr) {   // image read transposed: column c of the solve frame is image row c
             for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
                 const int c = idx / n, y = idx - c * n;
-                stage_f[y * kStageLd + c] = img[(size_t)(c0 + c) * n + y];
+                stage_f[y * kStageLd + c] = __ldcs(img + (size_t)(c0 + c) * n + y);
             }
         } else {
             for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
                 const int y = idx >> 5, c = idx & 31;
-                stage_f[y * kStageLd + c] = img[(size_t)y * n + c0 + c];
+                stage_f[y * kStageLd + c] = __ldcs(img + (size_t)y * n + c0 + c);
             }
         }
         __syncthreads();

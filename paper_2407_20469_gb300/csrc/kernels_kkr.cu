@@ -78,7 +78,8 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
             const float* row = img + (size_t)r * n;
             float2 v[BN], o[16];
 #pragma unroll
-            for (int j = 0; j < BN; ++j) v[j] = make_float2(__logf(fmaxf(row[t + 16 * j], eps)), 0.f);
+            for (int j = 0; j < BN; ++j)      // last read of the image: evict first from L2
+                v[j] = make_float2(__logf(fmaxf(__ldcs(row + t + 16 * j), eps)), 0.f);
             fft_alpha<BN, false>(v, o, h, tw);
             if (t < BN) {
                 float2* gr = G + (size_t)r * n;

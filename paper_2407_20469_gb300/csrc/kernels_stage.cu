@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles,
             float s = 0.f, s2 = 0.f;
 #pragma unroll 4
             for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-                const float4 v = T4[k];
+                const float4 v = __ldcs(T4 + k);        // streamed: evict first from L2
                 bad |= invalid(v);
                 s += (v.x + v.y) + (v.z + v.w);
                 s2 += (v.x * v.x + v.y * v.y) + (v.z * v.z + v.w * v.w);
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_background(DevPlan P, int n_tiles,
             acc += mean > 0 ? var / (mean * mean) : 0.0;
         } else {
 #pragma unroll 4
-            for (int k = threadIdx.x; k < nq; k += blockDim.x) bad |= invalid(T4[k]);
+            for (int k = threadIdx.x; k < nq; k += blockDim.x) bad |= invalid(__ldcs(T4 + k));
         }
     }
     const int anybad = __syncthreads_or(bad);

@@ -40,9 +40,9 @@ __global__ void __launch_bounds__(kThreads) k_synthesize(DevPlan P, int n_tiles,
                 c.a[q * ld + y] = F[(size_t)y * N + c0 + q];
             }
             const float2* R = fft_chunk<true>(c);
-            for (int t = threadIdx.x; t < S * N; t += blockDim.x) {
+            for (int t = threadIdx.x; t < S * N; t += blockDim.x) {   // final values: evict first from L2
                 const int y = t / S, q = t - y * S;
-                F[(size_t)y * N + c0 + q] = R[q * ld + y];
+                __stcs(F + (size_t)y * N + c0 + q, R[q * ld + y]);
             }
             __syncthreads();
         }
