@@ -168,6 +168,17 @@ apic_status apic_plan_df_set(const apic_plan* plan, int index, int which, int32_
 apic_status apic_plan_df_grid(const apic_plan* plan, int index, int32_t* h_grid);
 
 /*
+ * Sets the register-kernel grid of darkfield image `index` to mx row points x
+ * my column points, one of the supported pairs 192 x {96, 128, 144, 192},
+ * 160 x {96, 128} and 144 x 144 (plans whose register grid is 192 points), and
+ * rebuilds the plan's device tables (synchronises the device). APIC_EINVAL if
+ * the image is skipped, the pair is unsupported or it would alias the image's
+ * correlations. The plan's own choice is the cheapest exact pair; this lets a
+ * caller (or a test) run any other.
+ */
+apic_status apic_plan_set_df_grid(apic_plan* plan, int index, int mx, int my);
+
+/*
  * Whole per-tile reconstruction (Sec. 2.3, Fig. 2), for n_tiles tiles:
  *   d_intensity  [n_tiles][n_bf + n_df][h][w] float32 intensity stacks
  *   d_field      [n_tiles][u h][u w] complex64 out: high-resolution field

@@ -28,7 +28,7 @@ APIC_TABLE_LEDS, APIC_TABLE_PUPIL, APIC_TABLE_APERTURE = 0, 1, 2
 # Every symbol include/apic.h declares (checked by the CPU test suite).
 EXPORTS = [
     "apic_status_string", "apic_last_error", "apic_plan_create", "apic_plan_destroy",
-    "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_df_grid", "apic_plan_counters", "apic_plan_timing",
+    "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_df_grid", "apic_plan_set_df_grid", "apic_plan_counters", "apic_plan_timing",
     "apic_plan_stage_ms", "apic_reconstruct_batch", "apic_reconstruct_host", "apic_background",
     "apic_kk_spectra", "apic_kk_spectra_noalloc", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
     "apic_pupil", "apic_simulate", "apic_net_param_count", "apic_net_feature_count", "apic_net_create",
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_plan_table": (i32, [vp, i32, C.POINTER(C.c_int32), sz]),
         "apic_plan_df_set": (i32, [vp, i32, i32, C.POINTER(C.c_int32), sz, C.POINTER(C.c_int32)]),
         "apic_plan_df_grid": (i32, [vp, i32, C.POINTER(C.c_int32)]),
+        "apic_plan_set_df_grid": (i32, [vp, i32, i32, i32]),
         "apic_plan_counters": (i32, [vp, C.POINTER(C.c_int64), i32, i32]),
         "apic_plan_timing": (i32, [vp, i32]),
         "apic_plan_stage_ms": (i32, [vp, C.POINTER(C.c_double), i32, C.POINTER(C.c_int32), i32]),
@@ -225,6 +226,10 @@ class Plan:
         _check(load().apic_plan_df_grid(self.handle, index, g.ctypes.data_as(C.POINTER(C.c_int32))),
                "apic_plan_df_grid")
         return int(g[0]), int(g[1]), int(g[2])
+
+    def set_df_grid(self, index: int, mx: int, my: int):
+        """Use the mx x my register grid for darkfield image `index` (a supported, exact pair)."""
+        _check(load().apic_plan_set_df_grid(self.handle, index, mx, my), "apic_plan_set_df_grid")
 
     def counters(self, reset: bool = False) -> dict:
         """Work counters: kernel launches, CGLS iterations, darkfield solves (synchronises)."""

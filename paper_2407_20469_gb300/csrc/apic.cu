@@ -1000,6 +1000,33 @@ apic_status apic_plan_df_grid(const apic_plan* plan, int index, int32_t* h_grid)
     return APIC_OK;
 }
 
+apic_status apic_plan_set_df_grid(apic_plan* plan, int index, int mx, int my) {
+    if (!plan) return fail(APIC_EINVAL, "NULL plan");
+    HostPlan& H = plan->host;
+    if (index < 0 || index >= (int)H.df.size()) return fail(APIC_EINVAL, "darkfield index out of range");
+    DarkfieldHost& d = H.df[index];
+    if (!d.used) return fail(APIC_EINVAL, "darkfield image " + std::to_string(index) + " is skipped");
+    if (H.mr != 192) return fail(APIC_EINVAL, "the plan's register grid is not 192 points");
+    if (!df_grid_supported(mx, my)) return fail(APIC_EINVAL, "unsupported darkfield grid");
+    int nx = 0, ny = 0;
+    df_grid_needs(d, nx, ny);
+    if (mx < nx || my < ny)
+        return fail(APIC_EINVAL, "grid " + std::to_string(mx) + " x " + std::to_string(my) + " aliases (needs " +
+                                     std::to_string(nx) + " x " + std::to_string(ny) + ")");
+    if (d.solve_mx == mx && d.solve_my == my) return APIC_OK;
+    d.solve_mx = mx;
+    d.solve_my = my;
+    if (plan->host_only) return APIC_OK;
+    // new device tables (the grid enters the per-image records and the Q lane masks)
+    APIC_TRY_CUDA(cudaDeviceSynchronize());
+    if (plan->d_tables) {
+        cudaFree(plan->d_tables);
+        plan->allocs.erase(std::find(plan->allocs.begin(), plan->allocs.end(), plan->d_tables));
+        plan->d_tables = nullptr;
+    }
+    return upload(plan);
+}
+
 apic_status apic_background(apic_plan* plan, int n_tiles, const float* I, float* c2, int32_t* status,
                             void* stream) {
     apic_status s = check_stage(plan, n_tiles);

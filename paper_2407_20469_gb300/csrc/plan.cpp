@@ -25,27 +25,27 @@
 
 namespace apic {
 
-// Frame and grid of the register-kernel solve of one darkfield image (an
-// implementation choice; the problem of Eq. 13 is unchanged):
-// - an image whose lag set Q is narrower along x than along y is solved
-//   transposed (x <-> y in every set and in the image), so the row bands the
-//   darkfield passes walk are the shorter ones;
-// - along each axis the correlations are exact on a circular grid of L points
-//   when C u (U with P, read on Q) has no q - p - k (q in U, p in P, k in Q)
-//   that is a nonzero multiple of L and C^H r (Q with P, read on U) no such
-//   k + p - q, and every band fits; of the supported (row, column) grids on the
-//   192-point register grid, the exact one with the least estimated work per
-//   iteration (columns x relative cost of a column: 96 / 128-point columns go
-//   two per half-warp, 144 / 192-point ones one at a time) is used. Other
-//   register grids use mr x mr.
-static void solve_grid(DarkfieldHost& d, int mr) {
-    auto extent = [](const std::vector<int>& v) {
-        return v.empty() ? 0 : *std::max_element(v.begin(), v.end()) - *std::min_element(v.begin(), v.end()) + 1;
-    };
-    const bool tr = extent(d.Q_x) < extent(d.Q_y);
-    d.solve_tr = tr ? 1 : 0;
-    d.solve_mx = d.solve_my = mr;
-    if (mr != 192 || d.U_x.empty() || d.P_x.empty() || d.Q_x.empty()) return;
+namespace {
+struct DFGrid {
+    int mx, my;
+    double col_cost;   // relative cost of one column of my points (paired when my <= 128)
+};
+const DFGrid kDFGrids[] = {{192, 192, 2.0}, {192, 144, 1.68}, {192, 128, 1.13}, {192, 96, 1.0},
+                           {160, 128, 1.13}, {160, 96, 1.0},  {144, 144, 1.68}};
+}  // namespace
+
+bool df_grid_supported(int mx, int my) {
+    for (const DFGrid& g : kDFGrids)
+        if (g.mx == mx && g.my == my) return true;
+    return false;
+}
+
+// Along each axis the correlations of Eq. 13 are exact on a circular grid of L
+// points when C u (U with P, read on Q) has no q - p - k (q in U, p in P, k in Q)
+// that is a nonzero multiple of L and C^H r (Q with P, read on U) no such
+// k + p - q, and every band fits: the least such L along the solve frame's rows
+// (nx) and columns (ny).
+void df_grid_needs(const DarkfieldHost& d, int& nx, int& ny) {
     auto need = [](const std::vector<int>& U, const std::vector<int>& Pv, const std::vector<int>& Q) {
         auto mm = [](const std::vector<int>& v) { return std::minmax_element(v.begin(), v.end()); };
         const auto u = mm(U), pp = mm(Pv), q = mm(Q);
@@ -54,17 +54,33 @@ static void solve_grid(DarkfieldHost& d, int mr) {
         const int need_ch = std::max(std::abs(q0 + p0 - u1), std::abs(q1 + p1 - u0)) + 1;
         return std::max({need_c, need_ch, u1 - u0 + 1, p1 - p0 + 1, q1 - q0 + 1});
     };
-    // solve-frame axes: rows run along x' = (tr ? y : x)
-    const int nx = tr ? need(d.U_y, d.P_y, d.Q_y) : need(d.U_x, d.P_x, d.Q_x);
-    const int ny = tr ? need(d.U_x, d.P_x, d.Q_x) : need(d.U_y, d.P_y, d.Q_y);
-    struct Grid {
-        int mx, my;
-        double col_cost;
+    nx = ny = 0;
+    if (d.U_x.empty() || d.P_x.empty() || d.Q_x.empty()) return;
+    const bool tr = d.solve_tr != 0;         // solve frame: rows run along x' = (tr ? y : x)
+    nx = tr ? need(d.U_y, d.P_y, d.Q_y) : need(d.U_x, d.P_x, d.Q_x);
+    ny = tr ? need(d.U_x, d.P_x, d.Q_x) : need(d.U_y, d.P_y, d.Q_y);
+}
+
+// Frame and grid of the register-kernel solve of one darkfield image (an
+// implementation choice; the problem of Eq. 13 is unchanged):
+// - an image whose lag set Q is narrower along x than along y is solved
+//   transposed (x <-> y in every set and in the image), so the row bands the
+//   darkfield passes walk are the shorter ones;
+// - of the supported (row, column) grids on the 192-point register grid, the
+//   exact one (df_grid_needs) with the least estimated work per iteration
+//   (columns x relative cost of a column) is used. Other register grids use
+//   mr x mr.
+static void solve_grid(DarkfieldHost& d, int mr) {
+    auto extent = [](const std::vector<int>& v) {
+        return v.empty() ? 0 : *std::max_element(v.begin(), v.end()) - *std::min_element(v.begin(), v.end()) + 1;
     };
-    static const Grid grids[] = {{192, 192, 2.0}, {192, 144, 1.68}, {192, 128, 1.13}, {192, 96, 1.0},
-                                 {160, 128, 1.13}, {160, 96, 1.0},  {144, 144, 1.68}};
+    d.solve_tr = extent(d.Q_x) < extent(d.Q_y) ? 1 : 0;
+    d.solve_mx = d.solve_my = mr;
+    if (mr != 192 || d.U_x.empty() || d.P_x.empty() || d.Q_x.empty()) return;
+    int nx = 0, ny = 0;
+    df_grid_needs(d, nx, ny);
     double best = 1e300;
-    for (const Grid& g : grids)
+    for (const DFGrid& g : kDFGrids)
         if (g.mx >= nx && g.my >= ny && g.mx * g.col_cost < best) {
             best = g.mx * g.col_cost;
             d.solve_mx = g.mx;

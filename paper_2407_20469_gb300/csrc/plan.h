@@ -60,5 +60,9 @@ struct HostPlan {
 
 // Builds the plan; returns an empty string on success, else the reason.
 std::string build_host_plan(const GeomParams& p, HostPlan& out);
+// Supported (row, column) grids of the register darkfield solve on the 192-point grid.
+bool df_grid_supported(int mx, int my);
+// Least alias-free grid lengths of a used darkfield image along its solve frame's rows and columns.
+void df_grid_needs(const DarkfieldHost& d, int& nx, int& ny);
 
 }  // namespace apic

@@ -501,3 +501,41 @@ def test_reconstruct_host_one_chunk_split_matches_device_path():
         plan.reconstruct_host(T, Ih, f_h, z_h, s_h)
         torch.cuda.synchronize()
         assert torch.equal(s_h, s_d.cpu()) and torch.equal(z_h, z_d.cpu()) and torch.equal(f_h, f_d.cpu())
+
+
+DF_GRIDS = [(192, 192), (192, 144), (192, 128), (192, 96), (160, 128), (160, 96), (144, 144)]
+
+
+def test_every_supported_darkfield_grid_matches_oracle():
+    """Each (row, column) grid of the register darkfield solve, forced on every image
+    for which it is exact, reproduces the checker's field: the plan itself picks only
+    160 x 96, 160 x 128 and 144 x 144 for these 256-pixel tiles, so the other solve
+    instantiations run here. A pair that would alias an image is refused."""
+    n = 256
+    I, _, _ = make_tiles(n, 1, seed=77)
+    res = oracle_tile(I[0], n)
+    Id = dev(I)
+    for mx, my in DF_GRIDS:
+        plan = new_plan(n, max_tiles=1)
+        used = [i for i in range(plan.info.n_df) if plan.df_set(i, 0)[1][1]]
+        forced = 0
+        for i in used:
+            try:
+                plan.set_df_grid(i, mx, my)
+                forced += 1
+            except apic.ApicError as e:
+                assert "aliases" in str(e)
+                assert plan.df_grid(i)[1:] != (mx, my)
+        assert forced > 0
+        assert sum(plan.df_grid(i)[1:] == (mx, my) for i in used) == forced
+        H = plan.info.out_h
+        field = torch.zeros((1, H, 2 * H), dtype=torch.float32, device="cuda")
+        z = torch.zeros((1, 15), dtype=torch.float32, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        plan.reconstruct_batch(1, Id, field, z, None, st)
+        torch.cuda.synchronize()
+        assert st.cpu().numpy()[0] == 0, (mx, my)
+        assert rel_l2(as_complex(field)[0], res.field) < FIELD_TOL, (mx, my)
+        plan.close()
+    with pytest.raises(apic.ApicError):
+        new_plan(n, max_tiles=1).set_df_grid(0, 176, 96)     # not a supported pair
