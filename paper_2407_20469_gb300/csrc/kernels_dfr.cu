@@ -1,27 +1,36 @@
 // kernels_dfr.cu - darkfield spectrum extension (WSI-APIC Eq. 11-13) with
-// register-resident half-warp FFTs on an m x m correlation grid, m = 16 B.
+// register-resident half-warp FFTs.
 //
 // Per darkfield image j (pupil frame c = K + k_j; U unknown, P known, Q lags):
 //   b(k) = F(I_j)(k) - (P*P)(k) on Q                              (Eq. 13 left)
 //   C u  = series coefficients on Q of u(x) conj p(x)              (Eq. 13 right)
 //   min ||C u - b|| by CG on the normal equations C^H C u = C^H b (CGNR): per
-//   iteration w = C^H mask_Q C d as five passes over the grid
+//   iteration w = C^H mask_Q C d as five passes over an mx x my grid
 //     R1 rows of U: scatter d, inverse transform along x     -> GU
-//     C1 columns:   inverse along y, * conj(p) / (m m_y), forward along y -> GQ
+//     C1 columns:   inverse along y, * conj(p) / (mx my), forward along y -> GQ
 //     R2 rows of Q: forward along x, keep Q, inverse along x (in place)
-//     C2 columns:   inverse along y, * p / (m m_y), forward along y      -> GU
+//     C2 columns:   inverse along y, * p / (mx my), forward along y       -> GU
 //     R3 rows of U: forward along x, gather w on U, <d, w>
 //   then x += alpha d, s -= alpha w, and d = s + beta d (folded into the next
 //   R1). Transforms, vectors and the partial sums of a thread and of a warp FP32;
 //   the sums across warps and the step lengths FP64 (the FP64 pipe is narrow, so it
 //   sees 16 values per reduction rather than every point).
+// Each image is solved in its own frame (x and y swapped when that makes the row
+// bands shorter) on its own grid: mx = 16 BX row points and my = 16 BY column
+// points, the cheapest supported pair on which both correlations are exact
+// (chosen with the plan); P * P, whose lags reach further, uses the m x m grid
+// (m = 16 B). Columns of <= 128 points go two per half-warp (all 16 lanes in the
+// DFT_16 step), longer ones two per half-warp in turn; column pairs of grids with
+// an even row stride move as one 16-byte access per row. The known field p of the
+// paired grids lives in tensor memory (each thread's own lane and columns).
 // GU / GQ are band-row grids (only rows holding U or Q points). GU and the CG
 // vectors (the solution included) live in shared memory (GU with row stride
 // m + 1, so the column passes are conflict free); GQ, the column-major known
-// field p and b on Q live in the block's global scratch (L2-resident). The setup transforms of each image
-// reuse the shared-memory space of GU. One block per tile (persistent); images
-// of a tile are sequential. Each pass is a separate (non-inlined) function so
-// registers are allocated per pass.
+// field p of the longer grids and b on Q live in the block's global scratch
+// (L2-resident; data read once - the images - is loaded evict-first). The setup
+// transforms of each image reuse the shared-memory space of GU. One block per tile
+// (persistent); images of a tile are sequential. Each pass is a separate
+// (non-inlined) function so registers are allocated per pass.
 #include <math.h>
 
 #include <algorithm>
