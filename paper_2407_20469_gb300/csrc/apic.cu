@@ -601,19 +601,24 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
         split_geometry(plan, nt, r, m0, ma, ml);
         // earlier stages of tiles [a, a + k) of the chunk; in the split order this runs
         // for the partial wave (a = m0) and then for the full waves (a = 0), so a stage's
-        // interval starts with the first call and ends with the call for a = 0
+        // interval starts with the first call and ends with the call for a = 0. cap > 0
+        // limits the persistent kernels (KK, aberration) to cap SMs' worth of blocks: the
+        // full waves' earlier stages then never hold an SM the partial wave's darkfield
+        // blocks are about to take (a persistent block keeps its SM for milliseconds)
         bool pre_first = true;
-        auto pre_df = [&](int a, int k, bool final) -> apic_status {
+        auto pre_df = [&](int a, int k, bool final, int cap) -> apic_status {
             if (k == 0) return APIC_OK;
             const bool mark0 = first && pre_first, mark1 = last && final;
             pre_first = false;
             float2* xd = plan->xdisc + (size_t)a * D.n_bf * D.npup;
             float* ph = plan->phi + (size_t)a * D.npup;
+            Launch La = L;
+            if (cap > 0) La.grid_ab = std::min(L.grid_ab, 2 * cap);
             if (mark0) tm.mark(1, 0);
-            APIC_TRY_LAUNCH(launch_kk_any(plan, 0, k, It + (size_t)a * in_tile, xd, plan->kk_scratch, stt + a, st));
+            APIC_TRY_LAUNCH(launch_kk_any(plan, cap, k, It + (size_t)a * in_tile, xd, plan->kk_scratch, stt + a, st));
             if (mark1) tm.mark(1, 1);
             if (mark0) tm.mark(2, 0);
-            APIC_TRY_LAUNCH(launch_aberration(D, L, k, xd, zt + (size_t)a * APIC_N_ZERNIKE, plan->beta_scratch,
+            APIC_TRY_LAUNCH(launch_aberration(D, La, k, xd, zt + (size_t)a * APIC_N_ZERNIKE, plan->beta_scratch,
                                               plan->ab_passes, stt + a, st,
                                               net ? plan->c_net + (size_t)a * APIC_N_ZERNIKE : nullptr, warm ? 1 : 0));
             if (mark1) tm.mark(2, 1);
@@ -624,11 +629,11 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             return APIC_OK;
         };
         // network coefficients of tiles [a, a + k) of the chunk (learned path)
-        auto learned_part = [&](int a, int k) -> apic_status {
+        auto learned_part = [&](int a, int k, int cap) -> apic_status {
             if (!net || k == 0) return APIC_OK;
             float* feat = plan->feat + (size_t)a * feature_floats();
-            APIC_TRY_LAUNCH(launch_features(D, plan->grid_kkr, k, It + (size_t)a * in_tile, feat, plan->kk_scratch,
-                                            st));
+            const int fgrid = cap > 0 ? std::min(cap, plan->grid_kkr) : plan->grid_kkr;
+            APIC_TRY_LAUNCH(launch_features(D, fgrid, k, It + (size_t)a * in_tile, feat, plan->kk_scratch, st));
             const int nb = net_max_batch(net);
             for (int b0 = 0; b0 < k; b0 += nb) {
                 const int bn = std::min(nb, k - b0);
@@ -655,8 +660,8 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             if (first) tm.mark(0, 0);
             APIC_TRY_LAUNCH(launch_background(D, r, It + (size_t)m0 * in_tile, plan->c2 + m0, stt + m0, thresh2, st,
                                               replace ? 1 : 0));
-            if ((s = learned_part(m0, r)) != APIC_OK) return s;
-            if ((s = pre_df(m0, r, false)) != APIC_OK) return s;
+            if ((s = learned_part(m0, r, 0)) != APIC_OK) return s;
+            if ((s = pre_df(m0, r, false, 0)) != APIC_OK) return s;
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_fork, st));
             if (first) tm.mark(4, 0);
             APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
@@ -674,8 +679,8 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                 APIC_TRY_LAUNCH(launch_background(D, b - a, It + (size_t)a * in_tile, plan->c2 + a, stt + a, thresh2,
                                                   st, replace ? 1 : 0));
                 if (last && g == parts - 1) tm.mark(0, 1);
-                if ((s = learned_part(a, b - a)) != APIC_OK) return s;
-                if ((s = pre_df(a, b - a, g == parts - 1)) != APIC_OK) return s;
+                if ((s = learned_part(a, b - a, W - r)) != APIC_OK) return s;
+                if ((s = pre_df(a, b - a, g == parts - 1, W - r)) != APIC_OK) return s;
                 a = b;
             }
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
@@ -729,8 +734,8 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             if (first) tm.mark(0, 0);
             APIC_TRY_LAUNCH(launch_background(D, nt, It, plan->c2, stt, thresh2, st, replace ? 1 : 0));
             if (last) tm.mark(0, 1);
-            if ((s = learned_part(0, nt)) != APIC_OK) return s;
-            if ((s = pre_df(0, nt, true)) != APIC_OK) return s;
+            if ((s = learned_part(0, nt, 0)) != APIC_OK) return s;
+            if ((s = pre_df(0, nt, true, 0)) != APIC_OK) return s;
             if (first) tm.mark(4, 0);
             APIC_TRY_LAUNCH(launch_df(plan, nt, It, plan->spec, stt, st));
             if (last) tm.mark(4, 1);
