@@ -66,11 +66,14 @@ __device__ __forceinline__ int band_row(int i, int y0, int m) {
 // ---- tensor memory as per-thread storage of the known field
 // The darkfield kernel issues no MMA; its 512 TMEM columns x 128 lanes (256 KB per
 // SM) hold each thread's share of the column-major known field p on the paired
-// column grids. Thread i of warp w owns lane 32 (w mod 4) + i, columns
-// 128 floor(w / 4) .. + 127: 16 complex values per column pair it transforms (at
-// most 4 pairs). A thread reads back only what it stored itself.
+// column grids. Thread i of warp w owns lane 32 (w mod 4) + i and the
+// kTmemSlotCols columns of slot floor(w / 4): 16 complex values (32 columns) per
+// column pair it transforms. A thread reads back only what it stored itself.
 constexpr int kTmemCols = 512;
-constexpr bool kTmemField = kDFThreads == 512;   // 16 warps: 4 per lane quarter, 128 columns each
+constexpr int kTmemSlots = kDFThreads / 128;                  // warps per lane quarter
+constexpr int kTmemSlotCols = kTmemSlots > 0 ? (kTmemCols / kTmemSlots) & ~31 : 0;
+// every pass has at most 3 pair rounds (<= 96 pairs of columns over >= 32 half-warps)
+constexpr bool kTmemField = kDFThreads % 128 == 0 && kTmemSlotCols >= 96;
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float2 (&v)[16]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
@@ -803,7 +806,7 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
     __syncthreads();
     if constexpr (uses_tmem(B)) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        c.tm = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+        c.tm = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kTmemSlotCols * (warp >> 2));
     } else {
         c.tm = 0;
     }
