@@ -82,3 +82,45 @@ def test_solve_grid_keeps_the_correlations_exact(n, ill):
     assert checked == plan.info.n_df_used > 0
     if mr == 192:              # the 256-pixel tiles use grids shorter than 192 on both axes
         assert any(g[0] < mr for g in grids) and any(g[1] < mr for g in grids)
+
+
+DF_GRIDS = [(192, 192), (192, 144), (192, 128), (192, 96), (160, 128), (160, 96), (144, 144)]
+
+
+def test_every_accepted_grid_override_is_exact():
+    """apic_plan_set_df_grid accepts a supported grid for an image only if it keeps
+    the image's correlations exact (same FFT-vs-wrap-free check as above), refuses
+    unsupported pairs, and refuses at least one supported pair on these images."""
+    n = 256
+    plan = apic.Plan.from_illumination(n, synth.illumination(), flags=apic.APIC_HOST_ONLY)
+    rng = np.random.default_rng(5)
+    accepted = refused = 0
+    for idx in range(plan.info.n_df):
+        U, meta = plan.df_set(idx, 0)
+        if not meta[1]:
+            with pytest.raises(apic.ApicError):
+                plan.set_df_grid(idx, 192, 192)
+            continue
+        P, _ = plan.df_set(idx, 1)
+        Q, _ = plan.df_set(idx, 2)
+        tr = plan.df_grid(idx)[0]
+        if tr:
+            U, P, Q = U[:, ::-1], P[:, ::-1], Q[:, ::-1]
+        u = rng.standard_normal(len(U)) + 1j * rng.standard_normal(len(U))
+        pv = rng.standard_normal(len(P)) + 1j * rng.standard_normal(len(P))
+        r = rng.standard_normal(len(Q)) + 1j * rng.standard_normal(len(Q))
+        cu_ref, chr_ref = _correlations(U, P, Q, u, pv, r, BIG, BIG)
+        for mx, my in DF_GRIDS:
+            try:
+                plan.set_df_grid(idx, mx, my)
+            except apic.ApicError as e:
+                assert "aliases" in str(e)
+                refused += 1
+                continue
+            assert plan.df_grid(idx) == (tr, mx, my)
+            cu, chr_ = _correlations(U, P, Q, u, pv, r, mx, my)
+            assert _rel(cu, cu_ref) < 1e-10 and _rel(chr_, chr_ref) < 1e-10, (idx, mx, my)
+            accepted += 1
+        with pytest.raises(apic.ApicError):
+            plan.set_df_grid(idx, 176, 128)
+    assert accepted > 0 and refused > 0
