@@ -25,7 +25,8 @@
 // paired grids lives in tensor memory (each thread's own lane and columns).
 // GU / GQ are band-row grids (only rows holding U or Q points). GU and the CG
 // vectors (the solution included) live in shared memory (GU with row stride
-// m + 1, so the column passes are conflict free); GQ, the column-major known
+// gu_ld(B): column passes are conflict free per warp - m + 2 where they move column
+// pairs as 16-byte accesses, m + 1 where single columns); GQ, the column-major known
 // field p of the longer grids and b on Q live in the block's global scratch
 // (L2-resident; data read once - the images - is loaded evict-first). The setup
 // transforms of each image reuse the shared-memory space of GU. One block per tile
@@ -574,7 +575,7 @@ __device__ __noinline__ void pass_rows_rhs(HW w, const float2* tw, float2* GQ, i
 
 // Shared memory of one block (bytes, 16-aligned offsets):
 //   [0, gu)        half-warp areas of the m-grid passes
-//   [gu, c)        GU, band_u rows of m + 1 complex values
+//   [gu, c)        GU, band_u rows of gu_ld(B) complex values
 //   [0, c)         during the setup transforms of an image: half-warp areas of
 //                  the n-grid passes, then the column stage (aliases the above)
 //   [x, c)         solution x
@@ -594,13 +595,17 @@ __host__ __device__ constexpr int hw_area_m(int B) {
     return hw_single_size(B) > p ? hw_single_size(B) : p;
 }
 
+// Row stride of GU (complex values): even (16-byte aligned rows) where the column
+// passes move column pairs, odd where they move single columns (B = 16)
+__host__ __device__ constexpr int gu_ld(int B) { return B <= 12 ? 16 * B + 2 : 16 * B + 1; }
+
 __host__ __device__ inline DFRSmem dfr_smem_layout(int B, int BN, int band_u, int band_q, int max_N) {
     const int m = 16 * B, n = 16 * BN;
     const int hws_m = hw_area_m(B);
     const int hws_n = hw_single_size(BN);
     DFRSmem L;
     L.gu = align16((size_t)kHW * hws_m * sizeof(float2));
-    const size_t gu_end = L.gu + align16((size_t)band_u * (m + 1) * sizeof(float2));
+    const size_t gu_end = L.gu + align16((size_t)band_u * gu_ld(B) * sizeof(float2));
     L.stage = align16((size_t)kHW * hws_n * sizeof(float2));
     const size_t stage_c = (size_t)band_q * kStageLd * sizeof(float2);
     const size_t stage_f = (size_t)n * kStageLd * sizeof(float);
@@ -669,7 +674,7 @@ __device__ __forceinline__ const float2* grid_table(const DevPlan& P, int G, int
 template <int B, int BX, int BY>
 __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const DevDF& D, float2* sp, const float* ph,
                                         int iters, float tol) {
-    constexpr int m = 16 * B, mx = 16 * BX, my = 16 * BY, LDU = m + 1;
+    constexpr int m = 16 * B, mx = 16 * BX, my = 16 * BY, LDU = gu_ld(B);
     const HW& w = c.w;
     const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
     const int uy0 = D.uy0, qy0 = D.qy0, py0 = D.py0;
