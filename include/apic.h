@@ -223,14 +223,18 @@ apic_status apic_plan_timing(apic_plan* plan, int enable);
 apic_status apic_plan_stage_ms(apic_plan* plan, double* h_ms, int n, int32_t* h_calls, int reset);
 
 /*
- * apic_reconstruct_batch from and to HOST memory, pipelined: the tiles are
- * processed in chunks (the first one GPU-wide wave of the darkfield kernel,
- * the rest up to four waves or max_tiles); while one chunk is reconstructed, the next chunk's
- * intensities are copied in and the previous chunk's results copied out
- * (three internal streams, two sets of device staging buffers that the plan
- * allocates on first use and keeps). For the copies to overlap the host
- * buffers must be pinned (cudaHostAlloc / cudaHostRegister); pageable buffers
- * work but serialise. Returns when all results are in host memory.
+ * apic_reconstruct_batch from and to HOST memory, pipelined. A batch that fits
+ * one chunk (up to four GPU-wide darkfield waves and max_tiles) has its copies
+ * woven into the reconstruction's own order: the partial wave's intensities
+ * first, the others in parts whose earlier stages start as each part lands,
+ * and every darkfield round's fields copied out as soon as they are
+ * synthesized. Larger batches go in chunks (the first one wave, the rest up to
+ * four waves or max_tiles): while one chunk is reconstructed the next chunk's
+ * intensities are copied in and the previous chunk's results copied out.
+ * Three internal streams and two sets of device staging buffers, allocated on
+ * first use and kept. For the copies to overlap the host buffers must be
+ * pinned (cudaHostAlloc / cudaHostRegister); pageable buffers work but
+ * serialise. Returns when all results are in host memory.
  *   h_intensity [n_tiles][n_bf + n_df][h][w] f32, h_field [n_tiles][u h][u w]
  *   complex64, h_zernike [n_tiles][15] f32, h_tile_status [n_tiles] or NULL.
  */

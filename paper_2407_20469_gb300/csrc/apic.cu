@@ -651,7 +651,7 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
         float2* fld = (float2*)field + (size_t)t0 * out_tile;
         if (r > 0) {
             // Tiles of the full waves split into MA = [0, ma) on W - r blocks and
-            // MB = [ma, m0) on r blocks (k tiles per block each); T = [m0, nt) is the
+            // MB = [ma, m0) on r blocks (one tile per block per round, m0 / W rounds each); T = [m0, nt) is the
             // partial wave. Caller's stream: T's earlier stages, then (fork) the full
             // waves' background and earlier stages, MA's darkfield rounds, each followed
             // by its synthesis (T's after the first, ML = [ma, ml) after the last).
