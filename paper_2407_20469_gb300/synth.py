@@ -70,6 +70,13 @@ def illumination_8_24() -> Illumination:
     return illumination(8, ((0.29, 8, 0.0), (0.34, 8, 22.5), (0.40, 8, 11.25)))
 
 
+def illumination_12_22() -> Illumination:
+    """The paper's set-up size (Sec. 3): 12 NA-matching LEDs and 22 darkfield LEDs up
+    to illumination NA 0.44, here on rings at NA 0.31 (6), 0.375 (8) and 0.44 (8);
+    the exact positions are not printed, so the rings are this recipe's choice."""
+    return illumination(12, ((0.31, 6, 0.0), (0.375, 8, 22.5), (0.44, 8, 0.0)))
+
+
 def _smooth_noise(rng: np.random.Generator, H: int, W: int, sigma_px: float) -> np.ndarray:
     z = rng.standard_normal((H, W))
     fy = np.fft.fftfreq(H)[:, None]

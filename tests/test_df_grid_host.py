@@ -49,7 +49,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("n,ill", [(256, synth.illumination()), (128, synth.illumination()),
-                                   (128, synth.illumination_8_24())])
+                                   (128, synth.illumination_8_24()), (256, synth.illumination_12_22())])
 def test_solve_grid_keeps_the_correlations_exact(n, ill):
     plan = apic.Plan.from_illumination(n, ill, flags=apic.APIC_HOST_ONLY)
     rng = np.random.default_rng(11)

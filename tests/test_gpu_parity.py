@@ -158,6 +158,8 @@ def test_stitch_darkfield_synthesize_from_oracle_inputs():
     (128, 3, 2, synth.illumination(), None),          # ragged tail across two chunks
     (128, 2, 2, synth.illumination(), 1e4),           # Poisson noise at 10^4 photons / px
     (128, 1, 1, synth.illumination_8_24(), None),     # 8 + 24 illumination
+    (128, 2, 2, synth.illumination_12_22(), None),    # 12 + 22 up to NA 0.44 (the paper's set-up size)
+    (256, 1, 1, synth.illumination_12_22(), None),    # the same on 256-pixel tiles (per-image grids)
     (64, 5, 8, synth.illumination(), None),           # small tiles
 ])
 def test_end_to_end_matches_oracle(n, count, max_tiles, ill, photons):

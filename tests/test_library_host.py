@@ -37,7 +37,8 @@ def _geom(n):
 
 
 @pytest.mark.parametrize("n,ill", [(64, synth.illumination()), (128, synth.illumination()),
-                                   (128, synth.illumination_8_24()), (256, synth.illumination())])
+                                   (128, synth.illumination_8_24()), (256, synth.illumination()),
+                                   (128, synth.illumination_12_22())])
 def test_host_geometry_matches_oracle(n, ill):
     plan = apic.Plan.from_illumination(n, ill, flags=apic.APIC_HOST_ONLY)
     g = _geom(n)
