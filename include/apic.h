@@ -379,6 +379,23 @@ apic_status apic_paste_fields(apic_plan* plan, int n_tiles, const float* d_field
                               const int32_t* d_windows, int slide_h, int slide_w,
                               float* d_slide_field, void* stream);
 
+/* Blend the fields of a slide's whole window grid where windows overlap (the
+ * paper reconstructs overlapping patches, Sec. 2.3, 3.2; registration, Sec.
+ * 2.5, stays out): n_tiles = n_rows x n_cols windows in apic_slide_windows'
+ * row-major order, d_field [n_tiles][u h][u w] complex64, d_windows [n_tiles][6].
+ *   d_corr  [n_tiles][2] complex64 out: sum over the overlap with the left /
+ *           upper neighbour of f_t conj(f_neighbour) (0 without one);
+ *   d_phase [n_tiles] complex64 out: exp(-i phi_t), the tiles' global phases
+ *           chained along the grid from these correlations (phi = 0 for the
+ *           first window; first row from left neighbours, the rest from upper);
+ *   d_slide_field [u slide_h][u slide_w] complex64 out: the sum over covering
+ *           windows of w_t exp(-i phi_t) f_t divided by the sum of w_t, with
+ *           w_t a product of linear ramps across each overlap (1 elsewhere).
+ * Caller-owned device buffers; asynchronous on `stream`. */
+apic_status apic_blend_fields(apic_plan* plan, int n_tiles, const float* d_field, const int32_t* d_windows,
+                              int n_rows, int n_cols, int slide_h, int slide_w, float* d_corr, float* d_phase,
+                              float* d_slide_field, void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned aberration network. The paper has no counterpart: its aberration
  * estimate is the closed-form solve of Eq. 10 alone. This small CNN predicts

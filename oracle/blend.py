@@ -3,9 +3,10 @@
 TEST INFRASTRUCTURE ONLY: imported by tests/ (and nothing on the product path).
 
 The paper reconstructs a slide patch by patch from overlapping patches
-(Sec. 2.3, 3.2) and leaves the joining of patches to a registration step that
-is out of scope here (Sec. 2.5). Where neighbouring windows overlap, this
-checker states the blending the library performs, in output (upsampled)
+(Sec. 2.3, 3.2) and blends the overlaps of registered fields of view without
+giving a rule (Sec. 2.5; the SIFT registration itself is out of scope). Where
+neighbouring windows overlap, this checker states the blending the library
+performs, in output (upsampled)
 pixels; window t (row-major on a rows x cols grid, as apic_slide_windows lists
 them) covers [u y0_t, u y0_t + L) x [u x0_t, u x0_t + L), L = u tile:
   1. relative global phase of window t and its left / upper neighbour s:

@@ -28,13 +28,14 @@ APIC_TABLE_LEDS, APIC_TABLE_PUPIL, APIC_TABLE_APERTURE = 0, 1, 2
 # Every symbol include/apic.h declares (checked by the CPU test suite).
 EXPORTS = [
     "apic_status_string", "apic_last_error", "apic_plan_create", "apic_plan_destroy",
-    "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_df_grid", "apic_plan_set_df_grid", "apic_plan_counters", "apic_plan_timing",
+    "apic_plan_query", "apic_plan_table", "apic_plan_df_set", "apic_plan_df_grid", "apic_plan_set_df_grid",
+    "apic_plan_counters", "apic_plan_timing",
     "apic_plan_stage_ms", "apic_reconstruct_batch", "apic_reconstruct_host", "apic_background",
     "apic_kk_spectra", "apic_kk_spectra_noalloc", "apic_aberration", "apic_stitch", "apic_darkfield", "apic_synthesize",
     "apic_pupil", "apic_simulate", "apic_net_param_count", "apic_net_feature_count", "apic_net_create",
     "apic_net_destroy", "apic_net_set_params", "apic_net_get_params", "apic_net_get_grads", "apic_net_forward",
     "apic_net_backward", "apic_net_adamw", "apic_net_activation", "apic_features", "apic_reconstruct_learned",
-    "apic_slide_windows", "apic_cut_tiles", "apic_paste_fields", "apic_plan_autotune",
+    "apic_slide_windows", "apic_cut_tiles", "apic_paste_fields", "apic_blend_fields", "apic_plan_autotune",
 ]
 
 
@@ -110,6 +111,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_slide_windows": (i32, [i32, i32, i32, i32, C.POINTER(C.c_int32), i32, C.POINTER(C.c_int)]),
         "apic_cut_tiles": (i32, [vp, i32, vp, i32, i32, vp, vp, vp]),
         "apic_paste_fields": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
+        "apic_blend_fields": (i32, [vp, i32, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -313,6 +315,12 @@ class Plan:
     def paste_fields(self, n_tiles, field, windows, slide_h, slide_w, slide_field, stream=None):
         _check(load().apic_paste_fields(self.handle, n_tiles, _ptr(field), _ptr(windows), slide_h, slide_w,
                                         _ptr(slide_field), _stream(stream)), "apic_paste_fields")
+
+    def blend_fields(self, n_tiles, field, windows, n_rows, n_cols, slide_h, slide_w, corr, phase, slide_field,
+                     stream=None):
+        _check(load().apic_blend_fields(self.handle, n_tiles, _ptr(field), _ptr(windows), n_rows, n_cols, slide_h,
+                                        slide_w, _ptr(corr), _ptr(phase), _ptr(slide_field), _stream(stream)),
+               "apic_blend_fields")
 
     def features(self, n_tiles, intensity, feat, stream=None):
         """Network input features [n_tiles][64][64][8] of the first 8 images of each stack."""

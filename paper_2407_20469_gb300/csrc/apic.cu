@@ -1441,6 +1441,21 @@ apic_status apic_paste_fields(apic_plan* plan, int n_tiles, const float* field, 
     return APIC_OK;
 }
 
+apic_status apic_blend_fields(apic_plan* plan, int n_tiles, const float* field, const int32_t* windows, int n_rows,
+                              int n_cols, int slide_h, int slide_w, float* corr, float* phase, float* slide_field,
+                              void* stream) {
+    apic_status s = check_plan(plan, n_tiles);
+    if (s != APIC_OK) return s;
+    if (!field || !windows || !corr || !phase || !slide_field)
+        return fail(APIC_EINVAL, "NULL field, windows, correlation, phase or output");
+    if (n_rows < 1 || n_cols < 1 || (long long)n_rows * n_cols != n_tiles)
+        return fail(APIC_EINVAL, "n_tiles must be n_rows x n_cols (the slide's whole window grid)");
+    if (slide_h < plan->dev.h || slide_w < plan->dev.w) return fail(APIC_EINVAL, "slide smaller than a tile");
+    APIC_TRY_LAUNCH(launch_blend(plan->dev, n_tiles, n_rows, n_cols, (const float2*)field, windows, slide_h, slide_w,
+                                 (float2*)corr, (float2*)phase, (float2*)slide_field, (cudaStream_t)stream));
+    return APIC_OK;
+}
+
 apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* obj, const float* zern, float photons,
                           uint64_t seed, float* I, void* stream) {
     apic_status s = check_plan(plan, n_tiles);

@@ -142,6 +142,8 @@ cudaError_t launch_cut_tiles(const DevPlan& P, int n_tiles, const float* slide, 
                              float* out, cudaStream_t st);
 cudaError_t launch_paste_fields(const DevPlan& P, int n_tiles, const float2* field, const int32_t* win, int Hs,
                                 int Ws, float2* slide, cudaStream_t st);
+cudaError_t launch_blend(const DevPlan& P, int n_tiles, int rows, int cols, const float2* field, const int32_t* win,
+                         int Hs, int Ws, float2* corr, float2* z, float2* out, cudaStream_t st);
 // Records the message returned by apic_last_error (apic.cu).
 int record_error(int status, const char* msg);
 

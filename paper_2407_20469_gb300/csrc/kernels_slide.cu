@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/apic.h"
+#include "common.cuh"
 #include "internal.cuh"
 
 namespace apic {
@@ -79,6 +80,144 @@ __global__ void k_paste_fields(int n_tiles, int h, int w, int u, const float2* _
 }
 
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
+
+// ---- overlap blending of the windows' fields
+// Windows are row-major on an n_rows x n_cols grid (apic_slide_windows); window k
+// covers [u y0, u y0 + L) x [u x0, u x0 + L) of the output, L = u tile.
+
+// start (low-resolution pixels) of window row i / column j
+__device__ __forceinline__ int win_y(const int32_t* win, int cols, int i) { return win[6 * (i * cols)]; }
+__device__ __forceinline__ int win_x(const int32_t* win, int j) { return win[6 * j + 1]; }
+
+// sum over the overlap of window k with its left (d = 0) / upper (d = 1) neighbour
+// s of f_k conj(f_s): FP32 per thread, FP64 across the block; 0 without neighbour
+__global__ void k_blend_corr(int n_tiles, int cols, int u, int L, const float2* __restrict__ field,
+                             const int32_t* __restrict__ win, float2* __restrict__ corr) {
+    __shared__ double red[64];
+    const int k = blockIdx.x >> 1, d = blockIdx.x & 1;
+    if (k >= n_tiles) return;
+    const int nb = d == 0 ? (k % cols ? k - 1 : -1) : (k >= cols ? k - cols : -1);
+    float sr = 0.f, si = 0.f;
+    if (nb >= 0) {
+        const int ty = u * win[6 * k], tx = u * win[6 * k + 1], sy = u * win[6 * nb], sx = u * win[6 * nb + 1];
+        const int ya = max(ty, sy), yb = min(ty + L, sy + L), xa = max(tx, sx), xb = min(tx + L, sx + L);
+        const int w = xb - xa;
+        const float2* ft = field + (size_t)k * L * L;
+        const float2* fs = field + (size_t)nb * L * L;
+        if (ya < yb && w > 0)
+            for (int idx = threadIdx.x; idx < (yb - ya) * w; idx += blockDim.x) {
+                const int Y = ya + idx / w, X = xa + idx % w;
+                const float2 a = ft[(size_t)(Y - ty) * L + (X - tx)], b = fs[(size_t)(Y - sy) * L + (X - sx)];
+                sr += a.x * b.x + a.y * b.y;                   // a conj(b)
+                si += a.y * b.x - a.x * b.y;
+            }
+    }
+    const double tr = block_sum((double)sr, red), ti = block_sum((double)si, red);
+    if (threadIdx.x == 0) corr[2 * k + d] = make_float2((float)tr, (float)ti);
+}
+
+// exp(-i phi_k): the first row chained left to right, then every column downward
+__global__ void k_blend_phases(int rows, int cols, const float2* __restrict__ corr, float2* __restrict__ z) {
+    auto step = [](double2 prev, float2 c) {            // prev * conj(c) / |c| (prev when c = 0)
+        const double m = sqrt((double)c.x * c.x + (double)c.y * c.y);
+        if (!(m > 0.0)) return prev;
+        const double cr = c.x / m, ci = -c.y / m;
+        return make_double2(prev.x * cr - prev.y * ci, prev.x * ci + prev.y * cr);
+    };
+    __shared__ double2 top[1024];
+    for (int j = threadIdx.x; j < cols && j < 1024; j += blockDim.x) top[j] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        double2 v = make_double2(1.0, 0.0);
+        for (int j = 0; j < cols; ++j) {
+            if (j > 0) v = step(v, corr[2 * j]);
+            z[j] = make_float2((float)v.x, (float)v.y);
+            if (j < 1024) top[j] = v;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+        double2 v = j < 1024 ? top[j] : make_double2(z[j].x, z[j].y);
+        for (int i = 1; i < rows; ++i) {
+            const int k = i * cols + j;
+            v = step(v, corr[2 * k + 1]);
+            z[k] = make_float2((float)v.x, (float)v.y);
+        }
+    }
+}
+
+// weight of window j (starts s[], n of them, length L) at output position p along one axis
+__device__ __forceinline__ float blend_ramp(int sj, int sprev, int snext, bool has_prev, bool has_next, int p, int L) {
+    float w = 1.f;
+    if (has_prev) {
+        const int ov = sprev + L - sj;
+        if (ov > 0 && p < sj + ov) w *= ((float)(p - sj) + 0.5f) / (float)ov;
+    }
+    if (has_next) {
+        const int ov = sj + L - snext;
+        if (ov > 0 && p >= snext) w *= ((float)(sj + L - p) - 0.5f) / (float)ov;
+    }
+    return w;
+}
+
+// output pixel (Y, X): weighted, phase-aligned sum of the windows covering it
+__global__ void k_blend(int rows, int cols, int u, int L, const float2* __restrict__ field,
+                        const int32_t* __restrict__ win, const float2* __restrict__ z, int Ho, int Wo,
+                        float2* __restrict__ out) {
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < (size_t)Ho * Wo;
+         i0 += (size_t)gridDim.x * blockDim.x) {
+        const int Y = (int)(i0 / Wo), X = (int)(i0 - (size_t)Y * Wo);
+        // last window row / column starting at or before the pixel (binary search)
+        int lo = 0, hi = rows - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (u * win_y(win, cols, mid) <= Y) lo = mid; else hi = mid - 1;
+        }
+        const int iy = lo;
+        lo = 0;
+        hi = cols - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (u * win_x(win, mid) <= X) lo = mid; else hi = mid - 1;
+        }
+        const int jx = lo;
+        float ar = 0.f, ai = 0.f, ws = 0.f;
+        for (int i = iy; i >= 0; --i) {
+            const int sy = u * win_y(win, cols, i);
+            if (sy + L <= Y) break;
+            if (sy > Y) continue;                           // only when the first row starts below Y
+            const float wy = blend_ramp(sy, i > 0 ? u * win_y(win, cols, i - 1) : 0,
+                                        i + 1 < rows ? u * win_y(win, cols, i + 1) : 0, i > 0, i + 1 < rows, Y, L);
+            for (int j = jx; j >= 0; --j) {
+                const int sx = u * win_x(win, j);
+                if (sx + L <= X) break;
+                if (sx > X) continue;
+                const float wx = blend_ramp(sx, j > 0 ? u * win_x(win, j - 1) : 0,
+                                            j + 1 < cols ? u * win_x(win, j + 1) : 0, j > 0, j + 1 < cols, X, L);
+                const int k = i * cols + j;
+                const float2 f = field[(size_t)k * L * L + (size_t)(Y - sy) * L + (X - sx)];
+                const float2 zk = z[k];
+                const float w = wy * wx;
+                ar += w * (f.x * zk.x - f.y * zk.y);
+                ai += w * (f.x * zk.y + f.y * zk.x);
+                ws += w;
+            }
+        }
+        out[i0] = ws > 0.f ? make_float2(ar / ws, ai / ws) : make_float2(0.f, 0.f);
+    }
+}
+
+cudaError_t launch_blend(const DevPlan& P, int n_tiles, int rows, int cols, const float2* field, const int32_t* win,
+                         int Hs, int Ws, float2* corr, float2* z, float2* out, cudaStream_t st) {
+    const int u = P.H / P.h, L = P.H;
+    k_blend_corr<<<2 * n_tiles, 256, 0, st>>>(n_tiles, cols, u, L, field, win, corr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_blend_phases<<<1, 256, 0, st>>>(rows, cols, corr, z);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t total = (size_t)u * Hs * u * Ws;
+    k_blend<<<grid_for(total), 256, 0, st>>>(rows, cols, u, L, field, win, z, u * Hs, u * Ws, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cut_tiles(const DevPlan& P, int n_tiles, const float* slide, int Hs, int Ws, const int32_t* win,
                              float* out, cudaStream_t st) {

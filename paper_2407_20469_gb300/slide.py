@@ -23,9 +23,34 @@ def window_positions(windows: np.ndarray, slide_h: int, slide_w: int, tile: int)
     return np.stack([u, v], axis=1).astype(np.float32)
 
 
+def grid_shape(windows: np.ndarray):
+    """(rows, cols) of a row-major window list from apic_slide_windows."""
+    cols = int(np.sum(windows[:, 0] == windows[0, 0]))
+    return len(windows) // cols, cols
+
+
+def blend_slide(plan: apic.Plan, fields, windows: np.ndarray, slide_h: int, slide_w: int, stream=None):
+    """Blend the fields [n][u h][2 u w] of a slide's whole window grid where windows overlap
+    (apic_blend_fields): (slide field [u slide_h][2 u slide_w], correlations [n][4], phases [n][2])."""
+    import torch
+    rows, cols = grid_shape(windows)
+    n = len(windows)
+    dev = fields.device
+    u = plan.info.out_h // plan.info.tile_h
+    corr = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    phase = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    out = torch.empty((u * slide_h, 2 * u * slide_w), dtype=torch.float32, device=dev)
+    plan.blend_fields(n, fields, torch.as_tensor(windows, device=dev), rows, cols, slide_h, slide_w, corr, phase, out,
+                      stream)
+    return out, corr, phase
+
+
 def reconstruct_slide(plan: apic.Plan, slide, slide_h: int, slide_w: int, stride: int, batch: int | None = None,
-                      net: apic.Net | None = None, mode: int = 0, stream=None):
-    """(field [u slide_h][2 u slide_w] float32 interleaved complex, zernike [n][15], status [n], windows [n][6])."""
+                      net: apic.Net | None = None, mode: int = 0, stream=None, blend: bool = False):
+    """(field [u slide_h][2 u slide_w] float32 interleaved complex, zernike [n][15], status [n], windows [n][6]).
+
+    blend=False pastes each window's owned part (each tile keeps its own global phase);
+    blend=True keeps every window's field and blends the overlaps (blend_slide)."""
     import torch
     tile = plan.info.tile_h
     windows = apic.slide_windows(slide_h, slide_w, tile, stride)
@@ -42,13 +67,18 @@ def reconstruct_slide(plan: apic.Plan, slide, slide_h: int, slide_w: int, stride
     status = torch.empty(n, dtype=torch.int32, device=dev)
     out = torch.zeros((plan.info.out_h // tile * slide_h, 2 * (plan.info.out_w // tile) * slide_w),
                       dtype=torch.float32, device=dev)
+    kept = torch.empty((n, H, 2 * H), dtype=torch.float32, device=dev) if blend else None
     for t0 in range(0, n, batch):
         c = min(batch, n - t0)
+        fc = kept[t0:t0 + c] if blend else field
         plan.cut_tiles(c, slide, slide_h, slide_w, win_d[t0:t0 + c], I, stream)
         if net is None:
-            plan.reconstruct_batch(c, I, field, zern[t0:t0 + c], None, status[t0:t0 + c], stream)
+            plan.reconstruct_batch(c, I, fc, zern[t0:t0 + c], None, status[t0:t0 + c], stream)
         else:
-            plan.reconstruct_learned(net, mode, c, I, uv_d[t0:t0 + c], field, zern[t0:t0 + c], None,
+            plan.reconstruct_learned(net, mode, c, I, uv_d[t0:t0 + c], fc, zern[t0:t0 + c], None,
                                      status[t0:t0 + c], stream)
-        plan.paste_fields(c, field, win_d[t0:t0 + c], slide_h, slide_w, out, stream)
+        if not blend:
+            plan.paste_fields(c, field, win_d[t0:t0 + c], slide_h, slide_w, out, stream)
+    if blend:
+        out = blend_slide(plan, kept, windows, slide_h, slide_w, stream)[0]
     return out, zern, status, windows

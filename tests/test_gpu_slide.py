@@ -80,3 +80,69 @@ def test_ragged_slide_through_the_learned_path(plan):
     assert len(win) == 6                                   # 2 x 3 windows, the last of each axis moved inward
     assert torch.isfinite(out).all() and torch.isfinite(z).all()
     assert not np.any(st.cpu().numpy() & apic.APIC_TILE_BADINPUT)
+
+
+def _blend_case(plan, Hs, Ws, stride, fields_np):
+    win = apic.slide_windows(Hs, Ws, 64, stride)
+    f = torch.as_tensor(np.ascontiguousarray(np.stack([fields_np.real, fields_np.imag], -1).astype(np.float32))
+                        .reshape(len(win), 128, 256), device="cuda")
+    out, corr, phase = slide.blend_slide(plan, f, win, Hs, Ws)
+    torch.cuda.synchronize()
+    c = corr.cpu().numpy().astype(np.float64)
+    z = phase.cpu().numpy().astype(np.float64)
+    o = out.cpu().numpy().astype(np.float64).reshape(2 * Hs, 2 * Ws, 2)
+    return win, c[:, 0::2] + 1j * c[:, 1::2], z[:, 0] + 1j * z[:, 1], o[..., 0] + 1j * o[..., 1]
+
+
+def test_blend_matches_the_oracle_on_unrelated_fields(plan):
+    from oracle import blend
+    rng = np.random.default_rng(6)
+    Hs, Ws, stride = 150, 211, 48                          # ragged: the last window of each axis moved inward
+    n = len(apic.slide_windows(Hs, Ws, 64, stride))
+    fields = (rng.standard_normal((n, 128, 128)) + 1j * rng.standard_normal((n, 128, 128))).astype(np.complex64)
+    win, c, z, o = _blend_case(plan, Hs, Ws, stride, fields)
+    f64 = fields.astype(np.complex128)
+    rows, cols = blend.grid_shape(win)
+    c_ref = blend.correlations(f64, win, 2)
+    scale = blend.correlations(np.abs(f64), win, 2).real   # sum over each overlap of |f_t| |f_s|
+    assert np.all(np.abs(c - c_ref) <= 1e-6 * scale)       # FP32 products and partial sums
+    assert np.all(c[0] == 0) and np.all(c[cols:, 1] != 0) and np.all(c[:cols, 1] == 0)
+    z_own = blend.phases(c, rows, cols)                    # the chain of the kernel's own correlations
+    assert np.max(np.abs(z - z_own)) < 1e-5
+    o_ref = blend.blend(f64, win, z, Hs, Ws, 2)
+    assert np.linalg.norm(o - o_ref) / np.linalg.norm(o_ref) < 2e-6
+
+
+def test_phase_shifted_crops_reassemble_on_the_gpu(plan):
+    rng = np.random.default_rng(7)
+    Hs, Ws, stride = 150, 211, 40
+    win = apic.slide_windows(Hs, Ws, 64, stride)
+    G = rng.standard_normal((2 * Hs, 2 * Ws)) + 1j * rng.standard_normal((2 * Hs, 2 * Ws))
+    theta = rng.uniform(-np.pi, np.pi, len(win))
+    fields = np.stack([np.exp(1j * theta[k]) * G[2 * y:2 * y + 128, 2 * x:2 * x + 128]
+                       for k, (y, x) in enumerate(win[:, :2])])
+    _, _, z, o = _blend_case(plan, Hs, Ws, stride, fields)
+    assert np.max(np.abs(z * np.exp(1j * theta) - np.exp(1j * theta[0]))) < 1e-5
+    assert np.max(np.abs(o - np.exp(1j * theta[0]) * G)) < 1e-4
+
+
+def test_blend_without_overlap_equals_paste(plan):
+    rows, cols, n = 2, 3, 64
+    uv, zern, blank = learn.draw_tiles(rows * cols, 8, learn.field_table())
+    I = learn.simulate(plan, zern, blank, 8)
+    s = I.reshape(rows, cols, 24, n, n).permute(2, 0, 3, 1, 4).reshape(24, rows * n, cols * n).contiguous()
+    a, za, _, _ = slide.reconstruct_slide(plan, s, rows * n, cols * n, stride=n, batch=4)
+    b, zb, _, _ = slide.reconstruct_slide(plan, s, rows * n, cols * n, stride=n, batch=4, blend=True)
+    torch.cuda.synchronize()
+    assert torch.equal(za, zb)
+    assert torch.equal(a, b)                               # no overlap: zero correlations, unit phases and weights
+
+
+def test_blended_reconstruction_of_an_overlapping_slide(plan):
+    rng = np.random.default_rng(8)
+    Hs, Ws = 100, 150
+    s = torch.as_tensor(rng.random((24, Hs, Ws), dtype=np.float32) + 0.5, device="cuda")
+    out, z, st, win = slide.reconstruct_slide(plan, s, Hs, Ws, stride=40, batch=3, blend=True)
+    torch.cuda.synchronize()
+    assert out.shape == (2 * Hs, 4 * Ws)
+    assert torch.isfinite(out).all()
