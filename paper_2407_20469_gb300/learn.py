@@ -21,12 +21,13 @@ BLANK_AMP, BLANK_PHASE = 0.01, 0.02        # near-blank objects: 1 % amplitude, 
 DEFOCUS_JITTER = 0.2                      # per-tile offset of Noll 4 (rad), uniform +-
 
 
-def device_objects(T: int, H: int, seed: int, device, blank=None, sigma: float = 4.0):
+def device_objects(T: int, H: int, seed: int, device, blank=None, sigma: float = 4.0, scale=None):
     """Smooth random transmissions, interleaved complex64 [T, H, 2H].
 
     Amplitude 0.8 + 0.2 s0 and phase pi s1 from min-max normalised smoothed
     noise s0, s1; tiles with blank[t] get amplitude 0.99 + 0.01 s0 and phase
-    0.02 s1 instead.
+    0.02 s1 instead. scale[t] (faint tissue) multiplies a sample tile's
+    amplitude range 0.2 and phase range pi.
     """
     import torch
     g = torch.Generator(device=device).manual_seed(int(seed))
@@ -35,6 +36,10 @@ def device_objects(T: int, H: int, seed: int, device, blank=None, sigma: float =
     out = torch.empty((T, H, 2 * H), dtype=torch.float32, device=device)
     a = torch.full((T,), 0.2, device=device)
     p = torch.full((T,), math.pi, device=device)
+    if scale is not None:
+        f = torch.as_tensor(np.asarray(scale, dtype=np.float32), device=device)
+        a *= f
+        p *= f
     if blank is not None:
         b = torch.as_tensor(np.asarray(blank, dtype=bool), device=device)
         a[b] = BLANK_AMP
@@ -83,13 +88,15 @@ def draw_tiles(n: int, seed: int, table: np.ndarray, blank_frac: float = 0.0, uv
     return uv.astype(np.float32), coefficients(table, uv, defocus), blank
 
 
-def simulate(plan: apic.Plan, zern, blank, seed: int, photons: float = 1e4, start: int = 0, count: int | None = None):
-    """Intensity stacks [count, n_img, h, w] (device) of tiles start..start+count."""
+def simulate(plan: apic.Plan, zern, blank, seed: int, photons: float = 1e4, start: int = 0, count: int | None = None,
+             scale=None):
+    """Intensity stacks [count, n_img, h, w] (device) of tiles start..start+count (scale: see device_objects)."""
     import torch
     n = plan.info.tile_h
     H = plan.info.out_h
     count = len(zern) - start if count is None else count
-    obj = device_objects(count, H, seed * 7919 + start, "cuda", blank[start:start + count])
+    obj = device_objects(count, H, seed * 7919 + start, "cuda", blank[start:start + count],
+                         scale=None if scale is None else scale[start:start + count])
     z = torch.as_tensor(np.ascontiguousarray(zern[start:start + count]), device="cuda")
     I = torch.empty((count, plan.info.n_bf + plan.info.n_df, n, n), dtype=torch.float32, device="cuda")
     plan.simulate(count, obj, z, photons, seed * 104729 + start, I)
@@ -110,8 +117,9 @@ def dataset(plan: apic.Plan, n: int, seed: int, table: np.ndarray, blank_frac: f
     return feat, torch.as_tensor(uv, device="cuda"), torch.as_tensor(zern, device="cuda"), blank
 
 
-def init_params(seed: int) -> np.ndarray:
-    """He-normal weights (fan-in scaled), zero biases, in the library's flat layout."""
+def init_params(seed: int, out_gain: float = 1.0) -> np.ndarray:
+    """He-normal weights (fan-in scaled), zero biases, in the library's flat layout; out_gain scales
+    the output layer's weights (small: the first outputs stay near zero)."""
     rng = np.random.default_rng(seed)
     p = {}
     for name, shape in apic.param_shapes():
@@ -120,7 +128,7 @@ def init_params(seed: int) -> np.ndarray:
         else:
             fan_in = int(np.prod(shape[1:]))
             gain = 1.0 if name == "w5" else 2.0
-            p[name] = rng.standard_normal(shape) * math.sqrt(gain / fan_in)
+            p[name] = rng.standard_normal(shape) * math.sqrt(gain / fan_in) * (out_gain if name == "w5" else 1.0)
     return apic.pack_params(p)
 
 
