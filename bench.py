@@ -64,8 +64,12 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-assisted timing")
     ap.add_argument("--per-tile", type=int, default=32,
                     help="tiles timed one call at a time for the unbatched comparison (0: skip)")
-    ap.add_argument("--images", choices=["8+16", "8+24"], default="8+16",
-                    help="illumination set (8+24: rings at NA 0.29 / 0.34 / 0.40)")
+    ap.add_argument("--images", choices=["8+16", "8+24", "12+22"], default="8+16",
+                    help="illumination set (8+24: rings at NA 0.29 / 0.34 / 0.40; 12+22: the paper's set-up size, "
+                         "darkfield rings at NA 0.31 / 0.375 / 0.44)")
+    ap.add_argument("--workload", choices=["tiles", "rgb", "blend"], default="tiles",
+                    help="tiles: the batch reconstruction (default line); rgb: the same batch at three wavelengths, "
+                         "one plan each; blend: overlap blending of a 16 x 32 window grid with 6 %% overlap")
     ap.add_argument("--seed", type=int, default=2407)
     ap.add_argument("--df-tol", type=float, default=0.0, help="CGLS tolerance (0: library default)")
     ap.add_argument("--df-iters", type=int, default=0, help="CGLS iteration cap (0: library default)")
@@ -298,7 +302,7 @@ def gpu_arm(args):
     device = torch.device("cuda", torch.cuda.current_device())
 
     n, T = args.tile, args.tiles
-    ill = synth.illumination_8_24() if args.images == "8+24" else synth.illumination()
+    ill = illumination_for(args.images)
     plan = apic.Plan.from_illumination(n, ill, max_tiles=T, df_tol=args.df_tol, df_iters=args.df_iters)
     info = plan.info
     H = info.out_h
@@ -437,6 +441,7 @@ def gpu_arm(args):
             tr = json.load(fh)
         tol = args.df_tol if args.df_tol > 0 else DEFAULT_DF_TOL
         if (tr.get("source_sha") == source_sha() and tr.get("tile") == n and tr.get("tiles") == T
+                and tr.get("images", "8+16") == args.images
                 and abs(tr.get("df_tol", 0) - tol) < 1e-12 and not args.df_iters):
             traffic = tr.get("dram_bytes_per_launch")
     roofline = {"bound": "alu", "kernel": "k_darkfield_reg", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
@@ -463,7 +468,7 @@ def gpu_arm(args):
     if per_tile is not None:
         per_tile["batched_over_per_tile"] = value / per_tile["value"]
         line["per_tile_calls"] = per_tile
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.images == "8+16":
         I1, g1, k1, ill1 = oracle_tile_sample(n, args.seed)
         res, secs = run_oracle(I1, g1, k1, ill1.n_bf)
         line["cpu_baseline"] = {"value": (2 * n) ** 2 / secs / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(),
@@ -490,10 +495,182 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def illumination_for(images):
+    from paper_2407_20469_gb300 import synth
+    return {"8+16": synth.illumination, "8+24": synth.illumination_8_24,
+            "12+22": synth.illumination_12_22}[images]()
+
+
+def clock_id(device):
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    uuid = str(getattr(props, "uuid", ""))
+    return ("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(device.index))
+
+
+def timed(fn, steps, device):
+    """(ms over `steps` calls of fn on the current stream, clock record), after a synchronize."""
+    import torch
+    clocks = ClockSampler(clock_id(device))
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.5)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), clocks.stop()
+
+
+RGB_UM = (0.47, 0.52, 0.63)
+
+
+def rgb_arm(args):
+    """The batch workload at three wavelengths (one plan per colour, kept): one step reconstructs
+    every tile in every channel. Darkfield roofline summed over the channels' launches."""
+    import torch
+    from paper_2407_20469_gb300 import apic, build, channels, synth
+    build.build()
+    device = torch.device("cuda", torch.cuda.current_device())
+    n, T = args.tile, args.tiles
+    cp = channels.ChannelPlans(n, RGB_UM, max_tiles=T)
+    C = len(RGB_UM)
+    info = cp.plan(RGB_UM[0]).info
+    H = info.out_h
+    zern_true = torch.from_numpy(np.resize(field_zernike(), (T, 15))).to(device)
+    I, F, Z, S = [], [], [], []
+    for c, w in enumerate(RGB_UM):
+        p = cp.plan(w)
+        obj = device_objects(T, H, args.seed + 7919 * c, device)
+        x = torch.empty((T, p.info.n_bf + p.info.n_df, n, n), dtype=torch.float32, device=device)
+        p.simulate(T, obj, zern_true, synth.PHOTONS, args.seed + c, x)
+        del obj
+        I.append(x)
+        F.append(torch.empty((T, H, 2 * H), dtype=torch.float32, device=device))
+        Z.append(torch.empty((T, 15), dtype=torch.float32, device=device))
+        S.append(torch.empty((T,), dtype=torch.int32, device=device))
+    step = lambda: cp.reconstruct(T, I, F, Z, S)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for w in RGB_UM:
+        cp.plan(w).timing(True)
+        cp.plan(w).stage_ms(reset=True)
+        cp.plan(w).counters(reset=True)
+    ms, clk = timed(step, args.steps, device)
+    df_ms = flops = launches = 0.0
+    per_channel = {}
+    for w in RGB_UM:
+        p = cp.plan(w)
+        stage, calls = p.stage_ms(reset=True)
+        cnt = p.counters(reset=True)
+        p.timing(False)
+        setup, per_it = df_flops_per_solve(n, p.info.fft_m, 1)
+        f = (cnt["df_solves"] * setup + cnt["cg_iterations"] * per_it) / max(calls, 1)
+        d = stage["darkfield"] / max(calls, 1)
+        df_ms += d
+        flops += f
+        launches += cnt["launches"]
+        per_channel[str(w)] = {"darkfield_ms_per_step": d, "cg_iterations_per_step": cnt["cg_iterations"] / max(calls, 1),
+                               "fft_m": p.info.fft_m, "n_df_used": p.info.n_df_used}
+    achieved = flops / (df_ms / 1e3) / 1e12
+    st = np.concatenate([s.cpu().numpy() for s in S])
+    value = C * T * H * H * args.steps / (ms / 1e3) / 1e6
+    line = {
+        "metric": "APIC output Mpx/s over all colour channels", "value": value, "unit": "Mpx/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{T} tiles x {n}x{n} low-res ({H}x{H} output) at {C} wavelengths "
+                               f"{list(RGB_UM)} um, 8+16 images each, one plan per wavelength",
+                   "channels": C, "tiles_per_channel": T, "l2": "inputs_larger_than_l2",
+                   "tiles_status_nonzero": int(np.count_nonzero(st)), "per_channel": per_channel},
+        "roofline": {"bound": "alu", "kernel": "k_darkfield_reg", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "launch_ms": df_ms},
+        "e2e": None, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    cp.close()
+
+
+def blend_bytes(windows, u, L, out_px):
+    """Algorithmic bytes of one apic_blend_fields call: every window's field read once, the slide
+    field (out_px pixels) written once, and the overlap strips with the left / upper neighbour read
+    (both sides) by the correlation pass, complex64."""
+    rows = int(np.sum(windows[:, 1] == windows[0, 1]))
+    cols = len(windows) // rows
+    ov = 0
+    for k in range(len(windows)):
+        for nb in ((k - 1) if k % cols else -1, (k - cols) if k >= cols else -1):
+            if nb < 0:
+                continue
+            dy = L - abs(u * int(windows[k, 0]) - u * int(windows[nb, 0]))
+            dx = L - abs(u * int(windows[k, 1]) - u * int(windows[nb, 1]))
+            if dy > 0 and dx > 0:
+                ov += 2 * dy * dx
+    return 8 * (len(windows) * L * L + out_px + ov)
+
+
+def blend_arm(args):
+    """Overlap blending of a 16 x 32 grid of windows with 6 % overlap (the paper's scan overlap):
+    correlations, phase chain and the weighted sum, one apic_blend_fields call per step."""
+    import torch
+    from paper_2407_20469_gb300 import apic, build, slide, synth
+    build.build()
+    device = torch.device("cuda", torch.cuda.current_device())
+    n = args.tile
+    rows, cols = 16, 32
+    stride = n - int(round(0.06 * n))
+    Hs, Ws = (rows - 1) * stride + n, (cols - 1) * stride + n
+    plan = apic.Plan.from_illumination(n, synth.illumination(), max_tiles=1)
+    u = plan.info.out_h // n
+    L = u * n
+    win = apic.slide_windows(Hs, Ws, n, stride)
+    assert len(win) == rows * cols
+    g = torch.Generator(device=device).manual_seed(args.seed)
+    fields = torch.randn((len(win), L, 2 * L), device=device, generator=g)
+    out, corr, phase = slide.blend_slide(plan, fields, win, Hs, Ws)      # buffers, and the first call
+    win_d = torch.as_tensor(win, device=device)
+    step = lambda: plan.blend_fields(len(win), fields, win_d, rows, cols, Hs, Ws, corr, phase, out)
+    for _ in range(args.warmup):
+        step()
+    ms, clk = timed(step, args.steps, device)
+    nbytes = blend_bytes(win, u, L, u * u * Hs * Ws)
+    achieved = nbytes / (ms / args.steps / 1e3) / 1e9
+    peak, kind = 6800.0, "fallback"
+    if os.path.exists(PEAKS):
+        with open(PEAKS) as fh:
+            peak, kind = float(json.load(fh)["hbm_gbs"]), "measured"
+    value = u * u * Hs * Ws * args.steps / (ms / 1e3) / 1e6
+    line = {
+        "metric": "blended slide output Mpx/s", "value": value, "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{rows}x{cols} windows of {n}x{n} ({L}x{L} output fields), stride {stride} "
+                               f"(6 % overlap), slide {Hs}x{Ws} low-res",
+                   "l2": f"inputs_larger_than_l2 ({len(win) * L * L * 8 / 1e9:.2f} GB of fields)",
+                   "finite": bool(torch.isfinite(out).all().item())},
+        "roofline": {"bound": "hbm", "kernel": "apic_blend_fields (k_blend_corr + k_blend_phases + k_blend)",
+                     "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes_per_call": nbytes},
+        "e2e": None, "gpu_launches": 3 * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "rgb":
+        rgb_arm(args)
+    elif args.workload == "blend":
+        blend_arm(args)
     else:
         gpu_arm(args)
 

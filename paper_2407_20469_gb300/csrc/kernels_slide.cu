@@ -159,50 +159,171 @@ __device__ __forceinline__ float blend_ramp(int sj, int sprev, int snext, bool h
     return w;
 }
 
-// output pixel (Y, X): weighted, phase-aligned sum of the windows covering it
+// weighted, phase-aligned sum of the windows covering output pixel (Y, X)
+__device__ __forceinline__ float2 blend_one(int rows, int cols, int u, int L, const float2* __restrict__ field,
+                                            const int32_t* __restrict__ win, const float2* __restrict__ z, int Y,
+                                            int X) {
+    int lo = 0, hi = rows - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (u * win_y(win, cols, mid) <= Y) lo = mid; else hi = mid - 1;
+    }
+    const int iy = lo;
+    lo = 0;
+    hi = cols - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (u * win_x(win, mid) <= X) lo = mid; else hi = mid - 1;
+    }
+    const int jx = lo;
+    float ar = 0.f, ai = 0.f, ws = 0.f;
+    for (int i = iy; i >= 0; --i) {
+        const int sy = u * win_y(win, cols, i);
+        if (sy + L <= Y) break;
+        if (sy > Y) continue;
+        const float wy = blend_ramp(sy, i > 0 ? u * win_y(win, cols, i - 1) : 0,
+                                    i + 1 < rows ? u * win_y(win, cols, i + 1) : 0, i > 0, i + 1 < rows, Y, L);
+        for (int j = jx; j >= 0; --j) {
+            const int sx = u * win_x(win, j);
+            if (sx + L <= X) break;
+            if (sx > X) continue;
+            const float wx = blend_ramp(sx, j > 0 ? u * win_x(win, j - 1) : 0,
+                                        j + 1 < cols ? u * win_x(win, j + 1) : 0, j > 0, j + 1 < cols, X, L);
+            const int k = i * cols + j;
+            const float2 f = field[(size_t)k * L * L + (size_t)(Y - sy) * L + (X - sx)];
+            const float2 zk = z[k];
+            const float w = wy * wx;
+            ar += w * (f.x * zk.x - f.y * zk.y);
+            ai += w * (f.x * zk.y + f.y * zk.x);
+            ws += w;
+        }
+    }
+    return ws > 0.f ? make_float2(ar / ws, ai / ws) : make_float2(0.f, 0.f);
+}
+
+// output pixel (Y, X) one at a time (odd upsampling or buffers not 16-byte aligned)
 __global__ void k_blend(int rows, int cols, int u, int L, const float2* __restrict__ field,
                         const int32_t* __restrict__ win, const float2* __restrict__ z, int Ho, int Wo,
                         float2* __restrict__ out) {
     for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < (size_t)Ho * Wo;
          i0 += (size_t)gridDim.x * blockDim.x) {
         const int Y = (int)(i0 / Wo), X = (int)(i0 - (size_t)Y * Wo);
-        // last window row / column starting at or before the pixel (binary search)
-        int lo = 0, hi = rows - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (u * win_y(win, cols, mid) <= Y) lo = mid; else hi = mid - 1;
-        }
-        const int iy = lo;
-        lo = 0;
-        hi = cols - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (u * win_x(win, mid) <= X) lo = mid; else hi = mid - 1;
-        }
-        const int jx = lo;
-        float ar = 0.f, ai = 0.f, ws = 0.f;
-        for (int i = iy; i >= 0; --i) {
-            const int sy = u * win_y(win, cols, i);
-            if (sy + L <= Y) break;
-            if (sy > Y) continue;                           // only when the first row starts below Y
-            const float wy = blend_ramp(sy, i > 0 ? u * win_y(win, cols, i - 1) : 0,
-                                        i + 1 < rows ? u * win_y(win, cols, i + 1) : 0, i > 0, i + 1 < rows, Y, L);
-            for (int j = jx; j >= 0; --j) {
-                const int sx = u * win_x(win, j);
-                if (sx + L <= X) break;
-                if (sx > X) continue;
-                const float wx = blend_ramp(sx, j > 0 ? u * win_x(win, j - 1) : 0,
-                                            j + 1 < cols ? u * win_x(win, j + 1) : 0, j > 0, j + 1 < cols, X, L);
-                const int k = i * cols + j;
-                const float2 f = field[(size_t)k * L * L + (size_t)(Y - sy) * L + (X - sx)];
-                const float2 zk = z[k];
-                const float w = wy * wx;
-                ar += w * (f.x * zk.x - f.y * zk.y);
-                ai += w * (f.x * zk.y + f.y * zk.x);
-                ws += w;
+        out[i0] = blend_one(rows, cols, u, L, field, win, z, Y, X);
+    }
+}
+
+// Output pixel pairs (X, X + 1), X even, over a stripe of kBlendRows rows. With u even,
+// window edges in output pixels are even, so both pixels of a pair lie in the same windows
+// and their field values are one 16-byte load. The windows covering a pixel along one axis
+// are a contiguous run ending at the last one that starts at or before it; each thread
+// finds its column run and ramps once, and the block's first kBlendRows threads find the
+// row runs and ramps of the stripe into shared memory. A run longer than kMaxCover falls
+// back to the per-pixel rule.
+constexpr int kMaxCover = 4, kBlendThreads = 128, kBlendRows = 32;
+
+// run of windows (starts u * start(0..count-1), increasing) covering p: last index and length
+// (length kMaxCover + 1 when longer than kMaxCover)
+template <class Start>
+__device__ __forceinline__ int2 cover_run(Start start, int count, int u, int L, int p) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (u * start(mid) <= p) lo = mid; else hi = mid - 1;
+    }
+    int n = 0;
+    while (lo - n >= 0 && n <= kMaxCover) {
+        const int s = u * start(lo - n);
+        if (s > p || s + L <= p) break;
+        ++n;
+    }
+    return make_int2(lo, n);
+}
+
+__global__ void __launch_bounds__(kBlendThreads) k_blend_pairs(int rows, int cols, int u, int L,
+                                                                const float2* __restrict__ field,
+                                                                const int32_t* __restrict__ win,
+                                                                const float2* __restrict__ z, int Ho, int Wo,
+                                                                float2* __restrict__ out) {
+    __shared__ int s_last[kBlendRows], s_n[kBlendRows], s_sy[kBlendRows][kMaxCover];
+    __shared__ float s_wy[kBlendRows][kMaxCover];
+    const int Y0 = blockIdx.y * kBlendRows, Y1 = min(Ho, Y0 + kBlendRows);
+    auto ystart = [&](int i) { return win_y(win, cols, i); };
+    auto xstart = [&](int j) { return win_x(win, j); };
+    if (threadIdx.x < kBlendRows && Y0 + (int)threadIdx.x < Y1) {
+        const int r = threadIdx.x, Y = Y0 + r;
+        const int2 run = cover_run(ystart, rows, u, L, Y);
+        s_last[r] = run.x;
+        s_n[r] = run.y > kMaxCover ? -1 : run.y;
+#pragma unroll
+        for (int c = 0; c < kMaxCover; ++c) {
+            s_sy[r][c] = 0;
+            s_wy[r][c] = 0.f;
+            if (c < run.y && run.y <= kMaxCover) {
+                const int i = run.x - c, sy = u * ystart(i);
+                s_sy[r][c] = sy;
+                s_wy[r][c] = blend_ramp(sy, i > 0 ? u * ystart(i - 1) : 0, i + 1 < rows ? u * ystart(i + 1) : 0,
+                                        i > 0, i + 1 < rows, Y, L);
             }
         }
-        out[i0] = ws > 0.f ? make_float2(ar / ws, ai / ws) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int X = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (X >= Wo) return;                                   // no synchronisation below
+    const int2 cx = cover_run(xstart, cols, u, L, X);
+    const int jhi = cx.x, nj = cx.y;
+    const bool generic_x = nj > kMaxCover;
+    int sxs[kMaxCover];
+    float wxa[kMaxCover], wxb[kMaxCover];
+#pragma unroll
+    for (int c = 0; c < kMaxCover; ++c) {
+        sxs[c] = 0;
+        wxa[c] = wxb[c] = 0.f;
+        if (!generic_x && c < nj) {
+            const int j = jhi - c;
+            const int sx = u * xstart(j);
+            const int sp = j > 0 ? u * xstart(j - 1) : 0, sn = j + 1 < cols ? u * xstart(j + 1) : 0;
+            sxs[c] = sx;
+            wxa[c] = blend_ramp(sx, sp, sn, j > 0, j + 1 < cols, X, L);
+            wxb[c] = blend_ramp(sx, sp, sn, j > 0, j + 1 < cols, X + 1, L);
+        }
+    }
+#pragma unroll 2
+    for (int Y = Y0; Y < Y1; ++Y) {
+        const int r = Y - Y0, ni = s_n[r];
+        float4 o;
+        if (generic_x || ni < 0) {
+            const float2 a = blend_one(rows, cols, u, L, field, win, z, Y, X);
+            const float2 b = blend_one(rows, cols, u, L, field, win, z, Y, X + 1);
+            o = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            float ar0 = 0.f, ai0 = 0.f, ws0 = 0.f, ar1 = 0.f, ai1 = 0.f, ws1 = 0.f;
+#pragma unroll
+            for (int ci = 0; ci < kMaxCover; ++ci) {
+                if (ci < ni) {
+                    const int i = s_last[r] - ci, sy = s_sy[r][ci];
+                    const float wy = s_wy[r][ci];
+#pragma unroll
+                    for (int c = 0; c < kMaxCover; ++c) {
+                        if (c < nj) {
+                            const int k = i * cols + jhi - c;
+                            const float4 f = __ldcs(reinterpret_cast<const float4*>(
+                                field + (size_t)k * L * L + (size_t)(Y - sy) * L + (X - sxs[c])));
+                            const float2 zk = z[k];
+                            const float w0 = wy * wxa[c], w1 = wy * wxb[c];
+                            ar0 += w0 * (f.x * zk.x - f.y * zk.y);
+                            ai0 += w0 * (f.x * zk.y + f.y * zk.x);
+                            ws0 += w0;
+                            ar1 += w1 * (f.z * zk.x - f.w * zk.y);
+                            ai1 += w1 * (f.z * zk.y + f.w * zk.x);
+                            ws1 += w1;
+                        }
+                    }
+                }
+            }
+            o = make_float4(ws0 > 0.f ? ar0 / ws0 : 0.f, ws0 > 0.f ? ai0 / ws0 : 0.f,
+                            ws1 > 0.f ? ar1 / ws1 : 0.f, ws1 > 0.f ? ai1 / ws1 : 0.f);
+        }
+        __stcs(reinterpret_cast<float4*>(out + (size_t)Y * Wo + X), o);
     }
 }
 
@@ -214,8 +335,15 @@ cudaError_t launch_blend(const DevPlan& P, int n_tiles, int rows, int cols, cons
     if (e != cudaSuccess) return e;
     k_blend_phases<<<1, 256, 0, st>>>(rows, cols, corr, z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t total = (size_t)u * Hs * u * Ws;
-    k_blend<<<grid_for(total), 256, 0, st>>>(rows, cols, u, L, field, win, z, u * Hs, u * Ws, out);
+    const int Ho = u * Hs, Wo = u * Ws;
+    const bool pairs = u % 2 == 0 && (((uintptr_t)field | (uintptr_t)out) & 15) == 0;
+    if (pairs) {
+        const dim3 grid((unsigned)((Wo / 2 + kBlendThreads - 1) / kBlendThreads),
+                        (unsigned)((Ho + kBlendRows - 1) / kBlendRows));
+        k_blend_pairs<<<grid, kBlendThreads, 0, st>>>(rows, cols, u, L, field, win, z, Ho, Wo, out);
+    } else {
+        k_blend<<<grid_for((size_t)Ho * Wo), 256, 0, st>>>(rows, cols, u, L, field, win, z, Ho, Wo, out);
+    }
     return cudaGetLastError();
 }
 
