@@ -654,7 +654,7 @@ def blend_arm(args):
                                f"(6 % overlap), slide {Hs}x{Ws} low-res",
                    "l2": f"inputs_larger_than_l2 ({len(win) * L * L * 8 / 1e9:.2f} GB of fields)",
                    "finite": bool(torch.isfinite(out).all().item())},
-        "roofline": {"bound": "hbm", "kernel": "apic_blend_fields (k_blend_corr + k_blend_phases + k_blend)",
+        "roofline": {"bound": "hbm", "kernel": "apic_blend_fields (k_blend_corr + k_blend_phases + k_blend_pairs)",
                      "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "algorithmic_bytes_per_call": nbytes},
         "e2e": None, "gpu_launches": 3 * args.steps, "clocks": clk,

@@ -116,30 +116,59 @@ __global__ void k_blend_corr(int n_tiles, int cols, int u, int L, const float2* 
     if (threadIdx.x == 0) corr[2 * k + d] = make_float2((float)tr, (float)ti);
 }
 
-// exp(-i phi_k): the first row chained left to right, then every column downward
-__global__ void k_blend_phases(int rows, int cols, const float2* __restrict__ corr, float2* __restrict__ z) {
-    auto step = [](double2 prev, float2 c) {            // prev * conj(c) / |c| (prev when c = 0)
-        const double m = sqrt((double)c.x * c.x + (double)c.y * c.y);
-        if (!(m > 0.0)) return prev;
-        const double cr = c.x / m, ci = -c.y / m;
-        return make_double2(prev.x * cr - prev.y * ci, prev.x * ci + prev.y * cr);
-    };
-    __shared__ double2 top[1024];
-    for (int j = threadIdx.x; j < cols && j < 1024; j += blockDim.x) top[j] = make_double2(0.0, 0.0);
-    if (threadIdx.x == 0) {
+// exp(-i phi_k): the first row chained left to right, then every column downward.
+// 1. every window's step toward its parent, conj(c) / |c| ((1, 0) for c = 0; the left
+//    neighbour's correlation in the first row, the upper one's elsewhere), all in parallel
+//    (scaled by max(|re|, |im|) first so that tiny correlations do not underflow);
+// 2. the first row's prefix product, log-depth in shared memory (FP64) when the row fits
+//    the block, else chained by one thread; 3. each column chained downward by its own thread.
+__device__ __forceinline__ float2 unit_conj(float2 c) {
+    const float m = fmaxf(fabsf(c.x), fabsf(c.y));
+    if (!(m > 0.f)) return make_float2(1.f, 0.f);
+    const float x = c.x / m, y = c.y / m;
+    const float r = 1.f / sqrtf(x * x + y * y);
+    return make_float2(x * r, -y * r);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+constexpr int kPhaseThreads = 1024;
+
+__global__ void __launch_bounds__(kPhaseThreads) k_blend_phases(int rows, int cols, const float2* __restrict__ corr,
+                                                                 float2* __restrict__ z) {
+    __shared__ double2 top[kPhaseThreads];
+    const int n = rows * cols, t = threadIdx.x;
+    for (int k = t; k < n; k += blockDim.x)
+        z[k] = k == 0 ? make_float2(1.f, 0.f) : unit_conj(k < cols ? corr[2 * k] : corr[2 * k + 1]);
+    __syncthreads();                                       // z is read across threads below
+    const bool scan = cols <= (int)blockDim.x;
+    if (scan) {
+        if (t < cols) top[t] = make_double2(z[t].x, z[t].y);
+        __syncthreads();
+        for (int d = 1; d < cols; d <<= 1) {               // inclusive prefix product
+            const bool act = t < cols && t >= d;
+            double2 v = make_double2(0.0, 0.0);
+            if (act) v = cmul(top[t - d], top[t]);
+            __syncthreads();
+            if (act) top[t] = v;
+            __syncthreads();
+        }
+    } else if (t == 0) {
         double2 v = make_double2(1.0, 0.0);
-        for (int j = 0; j < cols; ++j) {
-            if (j > 0) v = step(v, corr[2 * j]);
+        for (int j = 1; j < cols; ++j) {
+            v = cmul(v, make_double2(z[j].x, z[j].y));
             z[j] = make_float2((float)v.x, (float)v.y);
-            if (j < 1024) top[j] = v;
         }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < cols; j += blockDim.x) {
-        double2 v = j < 1024 ? top[j] : make_double2(z[j].x, z[j].y);
+    for (int j = t; j < cols; j += blockDim.x) {
+        double2 v = scan ? top[j] : make_double2(z[j].x, z[j].y);
+        z[j] = make_float2((float)v.x, (float)v.y);
         for (int i = 1; i < rows; ++i) {
             const int k = i * cols + j;
-            v = step(v, corr[2 * k + 1]);
+            v = cmul(v, make_double2(z[k].x, z[k].y));
             z[k] = make_float2((float)v.x, (float)v.y);
         }
     }
@@ -333,7 +362,7 @@ cudaError_t launch_blend(const DevPlan& P, int n_tiles, int rows, int cols, cons
     k_blend_corr<<<2 * n_tiles, 256, 0, st>>>(n_tiles, cols, u, L, field, win, corr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_blend_phases<<<1, 256, 0, st>>>(rows, cols, corr, z);
+    k_blend_phases<<<1, kPhaseThreads, 0, st>>>(rows, cols, corr, z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int Ho = u * Hs, Wo = u * Ws;
     const bool pairs = u % 2 == 0 && (((uintptr_t)field | (uintptr_t)out) & 15) == 0;
