@@ -390,8 +390,16 @@ apic_status apic_paste_fields(apic_plan* plan, int n_tiles, const float* d_field
  *           first window; first row from left neighbours, the rest from upper);
  *   d_slide_field [u slide_h][u slide_w] complex64 out: the sum over covering
  *           windows of w_t exp(-i phi_t) f_t divided by the sum of w_t, with
- *           w_t a product of linear ramps across each overlap (1 elsewhere).
- * Caller-owned device buffers; asynchronous on `stream`. */
+ *           w_t a product of linear ramps across each overlap (1 elsewhere;
+ *           0 where no window covers a pixel).
+ * The grid must be a product grid with increasing starts: every window of a
+ * row has its row's y0, every window of a column its column's x0 (as
+ * apic_slide_windows makes them); other layouts give undefined weights but
+ * no access outside the buffers. With u even and d_field, d_slide_field
+ * 16-byte aligned the blend moves pixel pairs as 16-byte accesses; otherwise
+ * it takes one pixel at a time (same result up to rounding order). Errors:
+ * APIC_EINVAL for NULL pointers, n_tiles != n_rows x n_cols, or a slide
+ * smaller than a tile. Caller-owned device buffers; asynchronous on `stream`. */
 apic_status apic_blend_fields(apic_plan* plan, int n_tiles, const float* d_field, const int32_t* d_windows,
                               int n_rows, int n_cols, int slide_h, int slide_w, float* d_corr, float* d_phase,
                               float* d_slide_field, void* stream);
