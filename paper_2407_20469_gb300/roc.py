@@ -138,9 +138,10 @@ def train_classifier(plan: apic.Plan, n: int, seed: int, epochs: int = 6, faint_
     return net, hist
 
 
-def evaluate(plan: apic.Plan, net: apic.Net, n: int, seed: int, faint_frac: float, max_false_skip: float,
-             bg_contrast: float):
-    """ROC summary of the variance statistic and the classifier on n fresh tiles."""
+def evaluate(plan: apic.Plan, net: apic.Net, n: int, seed: int, faint_frac: float, max_false_skip: float):
+    """ROC summary of the variance statistic and the classifier on n fresh tiles; the library's own
+    flags are those of the plan's bg_contrast."""
+    bg_contrast = float(plan.params.bg_contrast)
     tiles = draw(n, seed, faint_frac=faint_frac)
     blank = tiles[2]
     c2, flag, score, _, _ = measure(plan, tiles, seed, net)
@@ -182,7 +183,7 @@ def main(argv=None):
     res = {"tile": a.tile, "train_tiles": a.train, "epochs": a.epochs, "train_loss": [round(h, 6) for h in hist],
            "train_seconds": round(t1 - t0, 1), "max_false_skip": a.max_false_skip}
     for name, ff, s in (("standard", 0.0, a.seed + 1), ("faint", 1.0, a.seed + 2)):
-        res[name] = evaluate(plan, net, a.eval, s, ff, a.max_false_skip, a.bg_contrast)
+        res[name] = evaluate(plan, net, a.eval, s, ff, a.max_false_skip)
     print(json.dumps(res))
     net.close()
     plan.close()

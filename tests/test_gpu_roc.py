@@ -34,7 +34,7 @@ def test_flags_are_the_statistic_below_the_threshold(setup):
 def test_standard_tiles_separate(setup):
     plan, net, hist = setup
     assert hist[-1] < hist[0]
-    r = roc.evaluate(plan, net, 1024, 33, 0.0, 1e-3, 0.02)
+    r = roc.evaluate(plan, net, 1024, 33, 0.0, 1e-3)
     v = r["variance"]
     assert v["auc"] > 0.999
     assert v["at_bg_contrast"]["skipped_sample"] == 0.0
@@ -45,7 +45,7 @@ def test_standard_tiles_separate(setup):
 
 def test_faint_tissue_roc_is_valid(setup):
     plan, net, _ = setup
-    r = roc.evaluate(plan, net, 1024, 34, 1.0, 1e-2, 0.02)
+    r = roc.evaluate(plan, net, 1024, 34, 1.0, 1e-2)
     for k in ("variance", "cnn"):
         assert 0.5 < r[k]["auc"] <= 1.0
         assert r[k]["calibrated"]["skipped_sample"] <= 1e-2
