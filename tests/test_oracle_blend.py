@@ -19,7 +19,9 @@ def windows_for(h, w, tile, stride):
     return np.array([[y, x, 0, 0, 0, 0] for y in ys for x in xs], dtype=np.int64)
 
 
-@pytest.mark.parametrize("h,w,tile,stride,u", [(64, 96, 32, 24, 2), (40, 40, 16, 12, 1), (50, 70, 32, 20, 2)])
+# stride < tile / 2: three or more windows cover a pixel and the weights no longer sum to one
+@pytest.mark.parametrize("h,w,tile,stride,u", [(64, 96, 32, 24, 2), (40, 40, 16, 12, 1), (50, 70, 32, 20, 2),
+                                               (40, 40, 16, 6, 1), (64, 96, 32, 10, 2)])
 def test_crops_with_random_phases_blend_back_to_the_field(h, w, tile, stride, u):
     rng = np.random.default_rng(h + w)
     win = windows_for(h, w, tile, stride)
