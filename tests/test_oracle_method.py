@@ -265,6 +265,9 @@ def test_end_to_end_recovers_field_and_pupil(phase_hi, scale, tol):
     # pupil phase RMS over the disc (orthonormal basis: RMS = |dc| for j >= 4)
     assert np.sqrt(np.sum((res.c15 - c) ** 2)) < 0.05
     assert np.all(res.c15[:3] == 0)
+    # the pupil out is the forward model's transfer function of Eq. 1 (a flat object
+    # spectrum seen under normal incidence: Circ exp(+j phi) on the camera grid)
+    assert rel_l2(res.pupil, forward.camera_spectrum(np.ones((g.H, g.W)), g, (0, 0), c)) < 1e-2
 
 
 def test_synthetic_aperture_resolution_matches_paper_formula():
