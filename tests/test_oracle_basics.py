@@ -171,6 +171,55 @@ def test_darkfield_sets_partition_and_exclusions():
         assert Q == up - pu - uu
 
 
+def _corr_brute(pts, vals):
+    """(s * s)(k) = sum_q s(q) conj(s(q - k)), pair by pair: the image spectrum of Eq. 12."""
+    out = {}
+    for q, a in zip(pts, vals):
+        for q2, b in zip(pts, vals):
+            k = (q[0] - q2[0], q[1] - q2[1])
+            out[k] = out.get(k, 0) + a * np.conj(b)
+    return out
+
+
+def test_eq13_holds_exactly_on_q_and_nowhere_else_in_u_minus_p():
+    # sets where the mirrored cross term reaches lags of U - P that U * U does not
+    U = [(0, 1), (-1, -2), (0, 3), (-1, 0), (1, 1), (-1, 2), (3, -1), (2, -1)]
+    P = [(1, 0), (-1, 3)]
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal(len(U)) + 1j * rng.standard_normal(len(U))
+    p = rng.standard_normal(len(P)) + 1j * rng.standard_normal(len(P))
+    full = _corr_brute(U + P, np.concatenate([u, p]))
+    PP = _corr_brute(P, p)
+    s = grid.darkfield_sets(np.array(U + P), set(P), 0, (0, 0))
+    assert set(map(tuple, s.U.tolist())) == set(U)
+    Q = set(map(tuple, s.Q.tolist()))
+    up = {(a[0] - b[0], a[1] - b[1]) for a in U for b in P}
+    assert Q <= up and len(up - Q) >= 3
+    for k in up:
+        cross = sum(u[i] * np.conj(p[m]) for i, a in enumerate(U) for m, b in enumerate(P)
+                    if (a[0] - b[0], a[1] - b[1]) == k)
+        exact = abs(full[k] - PP.get(k, 0) - cross) < 1e-12
+        assert exact == (k in Q)          # F(I) - P*P = C U holds on Q, and only there
+
+
+def test_darkfield_solvability_rules():
+    # one unknown point between two known ones: U - P is symmetric, the mirrored term
+    # covers all of it, no equation is left
+    D = np.array([[0, 0], [1, 0], [-1, 0]])
+    s = grid.darkfield_sets(D, {(1, 0), (-1, 0)}, 0, (0, 0))
+    assert len(s.U) == 1 and len(s.Q) == 0 and not s.used
+    # Sec. 4 bounds the unknown share of a darkfield disc by 42 %
+    g = geom(64)
+    k = (30, 0)
+    D = grid.disc_points(g, k)
+    order = np.argsort(D[:, 0], kind="stable")             # unknown = the cap of largest Kx
+    for frac, ok in ((0.41, True), (0.43, False)):
+        nu = int(round(frac * len(D)))
+        s = grid.darkfield_sets(D, set(map(tuple, D[order[:len(D) - nu]].tolist())), 0, k)
+        assert len(s.U) == nu and len(s.Q) >= nu
+        assert s.used == ok
+
+
 def test_darkfield_order_inside_out():
     k = np.array([[5, 0], [0, 3], [3, 0], [-3, 0], [0, -3]])
     order = grid.darkfield_order(k)
