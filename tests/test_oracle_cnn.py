@@ -56,3 +56,32 @@ def test_features_are_log_normalised_spectrum_magnitudes():
     ref = math.log(abs(F) / I[1].sum() + cnn.FEATURE_FLOOR)
     assert abs(f[1, -2 + 32, 3 + 32] - ref) < 1e-12
     assert abs(f[0, 32, 32] - math.log(1 + cnn.FEATURE_FLOOR)) < 1e-12
+
+
+def test_position_input_reaches_the_dense_layer():
+    """Closed form: with every convolution zeroed the pooled features are 0, so a dense
+    layer reading only (u, v) gives out = (relu(u), relu(v), 0, ...)."""
+    p, x, _, _ = small_case(2, B=4)
+    for k in p:
+        p[k] = np.zeros_like(p[k])
+    p["w4"][0, cnn.CHANNELS[4]] = 1.0
+    p["w4"][1, cnn.CHANNELS[4] + 1] = 1.0
+    p["w5"][0, 0] = 1.0
+    p["w5"][1, 1] = 1.0
+    uv = np.array([[0.5, -0.25], [-0.75, 0.125], [0.0, 1.0], [0.3, 0.2]])
+    out, _ = cnn.forward(p, x, uv)
+    assert np.array_equal(out[:, :2], np.maximum(uv, 0.0))
+    assert np.all(out[:, 2:] == 0)
+
+
+def test_max_pool_ties_go_to_the_first_position():
+    """Ties of the 2 x 2 max-pool take the first maximum in (dy, dx) order, and the
+    backward pass routes the gradient there alone."""
+    x = np.zeros((1, 1, 2, 4))
+    x[0, 0] = [[1.0, 3.0, 2.0, 2.0],
+               [3.0, 0.5, 2.0, 2.0]]
+    y, arg = cnn._pool(x)
+    assert y.tolist() == [[[[3.0, 2.0]]]]
+    assert arg.tolist() == [[[[1, 0]]]]                     # (0, 1) in the first block, (0, 0) in the second
+    g = cnn._pool_backward(np.ones((1, 1, 1, 2)), arg, x.shape)
+    assert g[0, 0].tolist() == [[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 0.0, 0.0]]

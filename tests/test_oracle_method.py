@@ -62,6 +62,16 @@ def test_forward_eq3_recentring_and_parseval():
     assert abs(I.mean() - np.sum(np.abs(S) ** 2)) < 1e-12
 
 
+def test_forward_shot_noise_statistics():
+    """Poisson(photons I) / photons: mean I and variance I / photons (uniform I = 1 under a plane wave)."""
+    g = geom(64)
+    k, _ = leds(g)
+    obj = np.ones((g.H, g.W), dtype=np.complex128)
+    I = forward.intensity_stack(obj, g, k[:8], np.zeros(15), photons=1e4, rng=np.random.default_rng(5))
+    assert abs(I.mean() - 1.0) < 2e-4
+    assert abs(I.var() / 1e-4 - 1.0) < 0.05
+
+
 def test_forward_plane_wave_object():
     g = geom(32)
     y, x = np.mgrid[0:g.H, 0:g.W]
