@@ -134,11 +134,21 @@ def _check(code: int, where: str):
         raise ApicError(code, where)
 
 
-def _ptr(x) -> int | None:
+def _ptr(x, host: bool = False) -> int | None:
+    """Address of a buffer for the C ABI: None, a raw address, or a contiguous tensor that the
+    callee can reach - device memory or pinned host memory for device arguments, CPU memory for
+    host arguments (host=True). Anything else raises ValueError here instead of reaching a kernel."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
+    if not x.is_contiguous():
+        raise ValueError("buffers passed to the library must be contiguous")
+    if host:
+        if x.device.type != "cpu":
+            raise ValueError(f"expected a host (CPU) buffer, got one on {x.device}")
+    elif x.device.type != "cuda" and not x.is_pinned():
+        raise ValueError(f"expected a device buffer (CUDA or pinned host memory), got pageable memory on {x.device}")
     return x.data_ptr()
 
 
@@ -261,8 +271,8 @@ class Plan:
 
     def reconstruct_host(self, n_tiles, intensity, field, zernike, tile_status=None):
         """Host-memory reconstruction, pipelined in chunks (pass pinned CPU tensors for overlap)."""
-        _check(load().apic_reconstruct_host(self.handle, n_tiles, _ptr(intensity), _ptr(field), _ptr(zernike),
-                                            _ptr(tile_status)), "apic_reconstruct_host")
+        _check(load().apic_reconstruct_host(self.handle, n_tiles, _ptr(intensity, True), _ptr(field, True),
+                                            _ptr(zernike, True), _ptr(tile_status, True)), "apic_reconstruct_host")
 
     def background(self, n_tiles, intensity, contrast2, tile_status, stream=None):
         _check(load().apic_background(self.handle, n_tiles, _ptr(intensity), _ptr(contrast2), _ptr(tile_status),

@@ -95,3 +95,17 @@ def test_host_only_plan_refuses_device_calls():
     with pytest.raises(apic.ApicError) as e:
         plan.reconstruct_batch(1, 0, 0, 0, stream=0)
     assert e.value.code == apic.APIC_EINVAL
+
+
+def test_binding_refuses_buffers_the_callee_cannot_reach():
+    torch = pytest.importorskip("torch")
+    assert apic._ptr(None) is None and apic._ptr(1234) == 1234
+    with pytest.raises(ValueError, match="contiguous"):
+        apic._ptr(torch.zeros(4, 4).t())
+    with pytest.raises(ValueError, match="device buffer"):
+        apic._ptr(torch.zeros(4))                            # pageable host memory for a device argument
+    t = torch.zeros(4)
+    assert apic._ptr(t, host=True) == t.data_ptr()
+    plan = apic.Plan.from_illumination(64, synth.illumination(), flags=apic.APIC_HOST_ONLY)
+    with pytest.raises(ValueError):
+        plan.background(1, torch.zeros(24, 64, 64), torch.zeros(1), torch.zeros(1, dtype=torch.int32))
