@@ -174,7 +174,9 @@ apic_status apic_plan_df_grid(const apic_plan* plan, int index, int32_t* h_grid)
  * rebuilds the plan's device tables (synchronises the device). APIC_EINVAL if
  * the image is skipped, the pair is unsupported or it would alias the image's
  * correlations. The plan's own choice is the cheapest exact pair; this lets a
- * caller (or a test) run any other.
+ * caller (or a test) run any other. The device tables move, so work with this
+ * plan captured in a CUDA graph before the call must be captured again; no
+ * call with the plan may be in flight on another host thread.
  */
 apic_status apic_plan_set_df_grid(apic_plan* plan, int index, int mx, int my);
 
@@ -480,7 +482,10 @@ apic_status apic_features(apic_plan* plan, int n_tiles, const float* d_intensity
  * apic_reconstruct_batch with the network: features and network forward per
  * chunk, then the stages as there, with the aberration stage per `mode`.
  * d_uv [n_tiles][2] tile positions. With APIC_NET_REPLACE low-contrast tiles
- * are never skipped. Same buffers and errors as apic_reconstruct_batch.
+ * are never skipped. Same buffers and errors as apic_reconstruct_batch. The
+ * first call on a plan allocates its feature and coefficient buffers
+ * (max_tiles tiles), so make one call before capturing this one in a CUDA
+ * graph; apic_reconstruct_batch allocates nothing after plan creation.
  */
 apic_status apic_reconstruct_learned(apic_plan* plan, apic_net* net, int mode, int n_tiles,
                                      const float* d_intensity, const float* d_uv, float* d_field,
