@@ -1,11 +1,17 @@
 // kernels_slide.cu - whole-slide tiling: windows of the plan's tile size over a
-// larger camera image, cutting them into the batch layout and pasting each
-// tile's owned part of the reconstructed field back into a slide-sized field.
+// larger camera image, cutting them into the batch layout, and joining the
+// reconstructed fields into one slide-sized field, either by pasting each
+// tile's owned part or by blending the overlaps.
 //
 // The paper reconstructs a slide patch by patch (Sec. 2.3, 3.2). No tile here is
 // ragged: windows step by `stride` and the last one of each row / column moves
 // inward to end at the slide edge, so one plan (one transform size) serves the
-// whole slide. Neighbouring windows split their overlap at its middle.
+// whole slide. Pasting splits each overlap at its middle; blending (Sec. 2.5
+// smooths the seams of overlapping fields of view without a rule) first brings
+// the tiles to one global phase - each tile keeps the arbitrary constant phase
+// of Eq. 5 - from the sums of f_t conj(f_s) over the overlaps with the left and
+// upper neighbours, chained along the window grid, then averages with linear
+// ramps across each overlap.
 #include <algorithm>
 #include <vector>
 
