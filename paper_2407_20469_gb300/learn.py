@@ -132,6 +132,40 @@ def init_params(seed: int, out_gain: float = 1.0) -> np.ndarray:
     return apic.pack_params(p)
 
 
+PARAMS_TAG = b"APICNET1"
+
+
+def save_params(path: str, flat, meta: dict | None = None):
+    """Network parameters (the flat float32 layout of apic_net_get_params) to a file: the tag
+    PARAMS_TAG, one JSON header line (count, layer shapes, caller's meta), then the values as
+    little-endian float32. Weights only: training resumes with fresh optimizer moments."""
+    import json
+    v = np.ascontiguousarray(flat, dtype="<f4").ravel()
+    head = {"count": int(v.size), "layers": [[n, list(sh)] for n, sh in apic.param_shapes()], "meta": meta or {}}
+    with open(path, "wb") as fh:
+        fh.write(PARAMS_TAG)
+        fh.write(json.dumps(head).encode() + b"\n")
+        fh.write(v.tobytes())
+
+
+def load_params(path: str):
+    """(flat float32 parameters, meta) from save_params; ValueError if the file is not such a file,
+    is truncated, or holds another layout than this library's network."""
+    import json
+    with open(path, "rb") as fh:
+        if fh.read(len(PARAMS_TAG)) != PARAMS_TAG:
+            raise ValueError(f"{path}: not a network parameter file")
+        head = json.loads(fh.readline().decode())
+        body = fh.read()
+    want = [[n, list(sh)] for n, sh in apic.param_shapes()]
+    total = sum(int(np.prod(sh)) for _, sh in apic.param_shapes())
+    if head.get("layers") != want or head.get("count") != total:
+        raise ValueError(f"{path}: layer shapes differ from this library's network")
+    if len(body) != 4 * total:
+        raise ValueError(f"{path}: expected {total} values, found {len(body) // 4}")
+    return np.frombuffer(body, dtype="<f4").astype(np.float32), head.get("meta", {})
+
+
 def train(net: apic.Net, feat, uv, zern, epochs: int = 4, batch: int = 64, lr: float = 1e-3,
           weight_decay: float = 1e-4, seed: int = 0, log=None):
     """AdamW on mean squared coefficient error; returns the mean loss of each epoch."""

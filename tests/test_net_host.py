@@ -1,5 +1,6 @@
 """CPU checks of the network's parameter layout (no GPU calls)."""
 import numpy as np
+import pytest
 
 from oracle import cnn
 from paper_2407_20469_gb300 import apic
@@ -30,3 +31,22 @@ def test_pack_unpack_round_trip_and_layout():
     # last layer: 12 rows of 256 weights + bias at the end of the vector
     assert flat[-1] == np.float32(p["b5"][11])
     assert flat[-2] == np.float32(p["w5"][11, 255])
+
+
+def test_parameter_file_round_trip_and_refusals(tmp_path):
+    from paper_2407_20469_gb300 import learn
+    flat = learn.init_params(7)
+    path = str(tmp_path / "net.bin")
+    learn.save_params(path, flat, {"epochs": 4, "loss": 0.01})
+    got, meta = learn.load_params(path)
+    assert got.dtype == np.float32 and np.array_equal(got, flat) and meta == {"epochs": 4, "loss": 0.01}
+    raw = open(path, "rb").read()
+    open(path, "wb").write(raw[:-4])                       # truncated
+    with pytest.raises(ValueError, match="expected"):
+        learn.load_params(path)
+    open(path, "wb").write(b"NOTANET1" + raw[8:])
+    with pytest.raises(ValueError, match="not a network"):
+        learn.load_params(path)
+    open(path, "wb").write(raw.replace(b'"count": 459244', b'"count": 459243'))
+    with pytest.raises(ValueError, match="layer shapes"):
+        learn.load_params(path)
