@@ -23,6 +23,15 @@ def window_positions(windows: np.ndarray, slide_h: int, slide_w: int, tile: int)
     return np.stack([u, v], axis=1).astype(np.float32)
 
 
+def _release(stream):
+    """Temporaries of these helpers are torch allocations on the current stream, safe to free
+    while work queued on that stream still uses them; with another stream the helper waits
+    for the device before returning them."""
+    if stream is not None:
+        import torch
+        torch.cuda.synchronize()
+
+
 def grid_shape(windows: np.ndarray):
     """(rows, cols) of a row-major window list from apic_slide_windows."""
     cols = int(np.sum(windows[:, 0] == windows[0, 0]))
@@ -40,8 +49,9 @@ def blend_slide(plan: apic.Plan, fields, windows: np.ndarray, slide_h: int, slid
     corr = torch.empty((n, 4), dtype=torch.float32, device=dev)
     phase = torch.empty((n, 2), dtype=torch.float32, device=dev)
     out = torch.empty((u * slide_h, 2 * u * slide_w), dtype=torch.float32, device=dev)
-    plan.blend_fields(n, fields, torch.as_tensor(windows, device=dev), rows, cols, slide_h, slide_w, corr, phase, out,
-                      stream)
+    win_d = torch.as_tensor(windows, device=dev)
+    plan.blend_fields(n, fields, win_d, rows, cols, slide_h, slide_w, corr, phase, out, stream)
+    _release(stream)
     return out, corr, phase
 
 
@@ -81,4 +91,5 @@ def reconstruct_slide(plan: apic.Plan, slide, slide_h: int, slide_w: int, stride
             plan.paste_fields(c, field, win_d[t0:t0 + c], slide_h, slide_w, out, stream)
     if blend:
         out = blend_slide(plan, kept, windows, slide_h, slide_w, stream)[0]
+    _release(stream)
     return out, zern, status, windows
