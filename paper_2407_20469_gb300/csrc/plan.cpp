@@ -146,11 +146,43 @@ struct BoolGrid {  // dense boolean map over [-half, half]^2
     }
 };
 
-// Marks {a - b : a in A, b in B} into out.
-void mark_difference(const std::vector<int>& ax, const std::vector<int>& ay, const std::vector<int>& bx,
-                     const std::vector<int>& by, BoolGrid& out) {
-    for (size_t i = 0; i < ax.size(); ++i)
-        for (size_t j = 0; j < bx.size(); ++j) out.at(ax[i] - bx[j], ay[i] - by[j]) = 1;
+// A point set ordered by (y, x) as runs of consecutive x on each row: (y, x0, x1), inclusive.
+struct Run {
+    int y, x0, x1;
+};
+
+std::vector<Run> runs_of(const std::vector<int>& xs, const std::vector<int>& ys) {
+    std::vector<Run> r;
+    for (size_t i = 0; i < xs.size(); ++i) {
+        if (!r.empty() && r.back().y == ys[i] && r.back().x1 + 1 == xs[i])
+            r.back().x1 = xs[i];
+        else
+            r.push_back({ys[i], xs[i], xs[i]});
+    }
+    return r;
+}
+
+// Marks {a - b : a in A, b in B} into out. The difference of the runs [a0, a1] on row ya
+// and [b0, b1] on row yb is the run [a0 - b1, a1 - b0] on row ya - yb, so each pair of
+// runs costs one increment and one decrement in a per-row counter; a prefix sum over each
+// row then marks every point that some pair covers.
+void mark_difference(const std::vector<Run>& A, const std::vector<Run>& B, BoolGrid& out) {
+    const int half = out.half, size = out.size;
+    std::vector<int> cnt((size_t)size * (size + 1), 0);
+    for (const Run& a : A)
+        for (const Run& b : B) {
+            int* row = cnt.data() + (size_t)(a.y - b.y + half) * (size + 1);
+            row[a.x0 - b.x1 + half] += 1;
+            row[a.x1 - b.x0 + half + 1] -= 1;
+        }
+    for (int y = 0; y < size; ++y) {
+        const int* row = cnt.data() + (size_t)y * (size + 1);
+        int c = 0;
+        for (int x = 0; x < size; ++x) {
+            c += row[x];
+            if (c > 0) out.v[(size_t)y * size + x] = 1;
+        }
+    }
 }
 
 }  // namespace
@@ -260,15 +292,15 @@ std::string build_host_plan(const GeomParams& p, HostPlan& P) {
                 d.U_pup.push_back(q);
             }
         }
-        // Q from the set differences (lags are frame independent)
+        // Q from the set differences (lags are frame independent); P - U is U - P mirrored
         const int half = 2 * dmax + 1;
-        BoolGrid up(half), pu(half), uu(half);
-        mark_difference(d.U_x, d.U_y, d.P_x, d.P_y, up);
-        mark_difference(d.P_x, d.P_y, d.U_x, d.U_y, pu);
-        mark_difference(d.U_x, d.U_y, d.U_x, d.U_y, uu);
+        BoolGrid up(half), uu(half);
+        const std::vector<Run> Ur = runs_of(d.U_x, d.U_y), Pr = runs_of(d.P_x, d.P_y);
+        mark_difference(Ur, Pr, up);
+        mark_difference(Ur, Ur, uu);
         for (int y = -half; y <= half; ++y)
             for (int x = -half; x <= half; ++x)
-                if (up.get(x, y) && !pu.get(x, y) && !uu.get(x, y)) {
+                if (up.get(x, y) && !up.get(-x, -y) && !uu.get(x, y)) {
                     d.Q_x.push_back(x);
                     d.Q_y.push_back(y);
                 }
