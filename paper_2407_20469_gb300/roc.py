@@ -141,7 +141,7 @@ def train_classifier(plan: apic.Plan, n: int, seed: int, epochs: int = 6, faint_
 def evaluate(plan: apic.Plan, net: apic.Net, n: int, seed: int, faint_frac: float, max_false_skip: float):
     """ROC summary of the variance statistic and the classifier on n fresh tiles; the library's own
     flags are those of the plan's bg_contrast."""
-    bg_contrast = float(plan.params.bg_contrast)
+    bg_contrast = round(float(plan.params.bg_contrast), 6)          # the float32 field, as set
     tiles = draw(n, seed, faint_frac=faint_frac)
     blank = tiles[2]
     c2, flag, score, _, _ = measure(plan, tiles, seed, net)
