@@ -278,11 +278,15 @@ apic_status apic_kk_spectra(apic_plan* plan, int n_tiles, const float* d_intensi
  * array, so h w <= 1,048,576 (up to 1024 x 1024); fewer grids fit at once for
  * larger tiles, which lowers parallelism but not correctness. Larger tiles
  * return APIC_EINVAL with a message (apic_last_error).
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. All calls share the array: calls that overlap on the GPU
- * (other streams, other host threads) race on it and must be serialised by
- * the caller. Nothing in it needs clearing between calls.
+ * The array comes into being (its module is loaded, 8 MiB of device memory)
+ * when the first plan with device memory is created on a device: plan creation
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so no call of this entry point is the one that loads it. Each call
+ * looks the address up again (cheap once loaded), so the entry point keeps
+ * working after cudaDeviceReset once a new plan has been made. All calls share
+ * the array: calls that overlap on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller. Nothing in it needs clearing
+ * between calls.
  * Arguments and layouts as apic_kk_spectra; n_tiles is not limited by max_tiles.
  */
 apic_status apic_kk_spectra_noalloc(apic_plan* plan, int n_tiles, const float* d_intensity, float* d_xdisc,

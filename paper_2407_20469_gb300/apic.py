@@ -283,7 +283,18 @@ class Plan:
                "apic_kk_spectra")
 
     def kk_spectra_noalloc(self, n_tiles, intensity, xdisc, stream=None):
-        """apic_kk_spectra without any allocation: scratch from the library's fixed device array."""
+        """apic_kk_spectra without any allocation: scratch from the library's fixed device array.
+
+        n_tiles is not bounded by the plan's max_tiles, so tensors are checked to hold
+        n_tiles tiles (float32) before the call."""
+        info = self.info
+        for name, t, per_tile in (("intensity", intensity, (info.n_bf + info.n_df) * info.tile_h * info.tile_w),
+                                  ("xdisc", xdisc, info.n_bf * 2 * info.n_pupil)):
+            if hasattr(t, "numel"):
+                if str(t.dtype) != "torch.float32":
+                    raise ValueError(f"{name} must be float32")
+                if t.numel() < n_tiles * per_tile:
+                    raise ValueError(f"{name} holds {t.numel()} values; {n_tiles} tiles need {n_tiles * per_tile}")
         _check(load().apic_kk_spectra_noalloc(self.handle, n_tiles, _ptr(intensity), _ptr(xdisc), _stream(stream)),
                "apic_kk_spectra_noalloc")
 

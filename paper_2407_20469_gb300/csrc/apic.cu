@@ -185,7 +185,7 @@ apic_status upload(apic_plan* plan) {
     std::vector<DevDF> dfs;
     std::vector<int> ux, uy, up, ua, px, py, pp, pa, qx, qy, rp;
     std::vector<unsigned> qmask;
-    int maxN = 1, maxM = 1, band_u = 1, band_p = 1, band_q = 1;
+    int maxN = 1, maxM = 1, band_u = 1, band_p = 1, band_q = 1, max_mx = 16, max_mxy = 256;
     const int mr = H.mr;
     for (const auto& d : H.df) {
         if (!d.used) continue;
@@ -268,17 +268,24 @@ apic_status upload(apic_plan* plan) {
         band_q = std::max(band_q, e.qy1 - e.qy0 + 1);
         e.qmask_off = (int)qmask.size();
         if (mr > 0) {   // Q membership per band row on the image's row grid, as 16-bit lane masks
-            const int Bm = e.bx, mx = 16 * e.bx;   // x index xi = t + Bm k1 sits in lane t, bit k1
-            qmask.resize(qmask.size() + (size_t)(e.qy1 - e.qy0 + 1) * 8, 0u);
+            // x index xi = t + Bm k1 sits in lane(-slot) t, bit k1; 8 words per row, 16 on
+            // the wide kernel's grids (Bm up to 20: lane-slots t + 16 s)
+            const int Bm = e.bx, mx = 16 * e.bx, words = mr == 512 ? 16 : 8;
+            qmask.resize(qmask.size() + (size_t)(e.qy1 - e.qy0 + 1) * words, 0u);
             for (size_t q = 0; q < Qs.x.size(); ++q) {
                 const int xi = ((Qs.x[q] % mx) + mx) % mx;
                 const int t = xi % Bm, k1 = xi / Bm;
-                qmask[e.qmask_off + (size_t)(Qs.y[q] - e.qy0) * 8 + (t >> 1)] |= 1u << (16 * (t & 1) + k1);
+                qmask[e.qmask_off + (size_t)(Qs.y[q] - e.qy0) * words + (t >> 1)] |= 1u << (16 * (t & 1) + k1);
             }
         }
         dfs.push_back(e);
     }
     D.n_used = (int)dfs.size();
+    D.qmask_words = mr == 512 ? 16 : 8;
+    // the wide kernel's scratch is sized for its longest grids (320 x 320), so that a
+    // grid forced with apic_plan_set_df_grid always fits the workspace made with the plan
+    D.max_mx = mr == 512 ? 320 : max_mx;
+    D.max_mxy = mr == 512 ? 320 * 320 : max_mxy;
     D.max_N = maxN;
     D.max_M = maxM;
     D.mr = mr;
@@ -294,6 +301,8 @@ apic_status upload(apic_plan* plan) {
     const size_t o_twr = A.add(twiddles(std::max(mr, 16)));
     const size_t o_ty6 = A.add(twiddles(96)), o_ty8 = A.add(twiddles(128)), o_ty9 = A.add(twiddles(144));
     const size_t o_ty10 = A.add(twiddles(160));
+    const size_t o_w12 = A.add(twiddles(192)), o_w16 = A.add(twiddles(256)), o_w18 = A.add(twiddles(288));
+    const size_t o_w20 = A.add(twiddles(320));
     const size_t o_qm = A.add(qmask);
 
     void* base = nullptr;
@@ -344,6 +353,10 @@ apic_status upload(apic_plan* plan) {
     D.tw_y8 = (const float2*)(b + o_ty8);
     D.tw_y9 = (const float2*)(b + o_ty9);
     D.tw_y10 = (const float2*)(b + o_ty10);
+    D.tw_w12 = (const float2*)(b + o_w12);
+    D.tw_w16 = (const float2*)(b + o_w16);
+    D.tw_w18 = (const float2*)(b + o_w18);
+    D.tw_w20 = (const float2*)(b + o_w20);
     D.d_qmask = (const unsigned*)(b + o_qm);
     return APIC_OK;
 }
@@ -367,7 +380,7 @@ apic_status configure(apic_plan* plan) {
     // register-FFT kernels where the sizes allow them (the default), the
     // shared-memory Stockham kernels otherwise or when asked for
     plan->kkr_ok = plan->dfr_ok = false;
-    if (D.h == D.w && (D.h == 64 || D.h == 128 || D.h == 256)) {
+    if (D.h == D.w && (D.h == 64 || D.h == 128 || D.h == 256 || D.h == 512)) {
         const size_t smem = kkr_smem_bytes(D.h / 16);
         const int occ = configure_kkr(D.h / 16, smem);
         if (occ > 0) {
@@ -379,11 +392,13 @@ apic_status configure(apic_plan* plan) {
         }
     }
     if (D.mr > 0) {
-        const size_t smem = dfr_smem_bytes(D.mr / 16, D.h / 16, D.band_u, D.band_q, D.max_N);
+        const bool wide = D.mr == 512;
+        const size_t smem = wide ? dfw_smem_bytes(D.max_N, D.band_q)
+                                 : dfr_smem_bytes(D.mr / 16, D.h / 16, D.band_u, D.band_q, D.max_N);
         int dev_max = 0;
         cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
         if (smem <= (size_t)dev_max) {
-            const int occ = configure_dfr(D.mr / 16, D.h / 16, smem);
+            const int occ = wide ? configure_dfw(smem) : configure_dfr(D.mr / 16, D.h / 16, smem);
             if (occ > 0) {
                 plan->dfr_ok = true;
                 plan->smem_dfr = smem;
@@ -423,7 +438,7 @@ apic_status alloc_workspace(apic_plan* p) {
     // darkfield scratch for two waves of blocks: a batch's last partial wave runs
     // beside the full waves (reconstruct) on blocks of its own
     if (p->use_reg) {
-        p->df_per_block = dfr_scratch_bytes(D);
+        p->df_per_block = D.mr == 512 ? dfw_scratch_bytes(D) : dfr_scratch_bytes(D);
         if ((s = dmalloc(p, &p->df_scratch, 2 * (size_t)p->grid_dfr * p->df_per_block)) != APIC_OK) return s;
     } else {
         p->df_per_block = df_scratch_bytes(D);
@@ -460,6 +475,9 @@ cudaError_t launch_df_on(apic_plan* p, int n_tiles, const float* I, const float*
                          bool second, cudaStream_t st, int grid = 0) {
     char* scratch = (char*)p->df_scratch + (second ? (size_t)df_wave(p) * p->df_per_block : 0);
     const int g = grid > 0 ? std::min(grid, df_wave(p)) : df_wave(p);
+    if (p->use_reg && p->dev.mr == 512)
+        return launch_darkfield_wide(p->dev, g, p->smem_dfr, n_tiles, I, phi, spec, scratch, p->df_per_block,
+                                     p->df_iters, p->df_tol, status, p->d_counters, st);
     if (p->use_reg)
         return launch_darkfield_reg(p->dev, g, p->smem_dfr, n_tiles, I, phi, spec, scratch, p->df_per_block,
                                     p->df_iters, p->df_tol, status, p->d_counters, st);
@@ -521,7 +539,7 @@ struct StageTimer {
 // allocated on the first learned call.
 apic_status learned_buffers(apic_plan* p) {
     if (p->feat) return APIC_OK;
-    if (!p->kkr_ok) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (!p->kkr_ok || p->dev.h > 256) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
     if (p->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
     apic_status s;
     if ((s = dmalloc(p, (void**)&p->feat, (size_t)p->max_tiles * feature_floats() * sizeof(float))) != APIC_OK)
@@ -839,6 +857,16 @@ apic_status apic_plan_create(const apic_params* pr, apic_plan** out) {
     apic_status s = upload(plan);
     if (s == APIC_OK) s = configure(plan);
     if (s == APIC_OK) s = alloc_workspace(plan);
+    if (s == APIC_OK) {
+        // load the allocation-free entry point's static array now (first look-up on a
+        // device), so that none of that entry point's calls is the one that loads it
+        float2* na = nullptr;
+        const cudaError_t e = noalloc_scratch(plan->device, &na);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s = cuda_fail(e, "static scratch address (cudaGetSymbolAddress)");
+        }
+    }
     if (s != APIC_OK) {
         apic_plan_destroy(plan);
         return s;
@@ -1011,25 +1039,39 @@ apic_status apic_plan_set_df_grid(apic_plan* plan, int index, int mx, int my) {
     if (index < 0 || index >= (int)H.df.size()) return fail(APIC_EINVAL, "darkfield index out of range");
     DarkfieldHost& d = H.df[index];
     if (!d.used) return fail(APIC_EINVAL, "darkfield image " + std::to_string(index) + " is skipped");
-    if (H.mr != 192) return fail(APIC_EINVAL, "the plan's register grid is not 192 points");
-    if (!df_grid_supported(mx, my)) return fail(APIC_EINVAL, "unsupported darkfield grid");
+    if (H.mr != 192 && H.mr != 512) return fail(APIC_EINVAL, "the plan's register grid is not 192 or 512 points");
+    if (!(H.mr == 192 ? df_grid_supported(mx, my) : df_wide_grid_supported(mx, my)))
+        return fail(APIC_EINVAL, "unsupported darkfield grid");
     int nx = 0, ny = 0;
     df_grid_needs(d, nx, ny);
     if (mx < nx || my < ny)
         return fail(APIC_EINVAL, "grid " + std::to_string(mx) + " x " + std::to_string(my) + " aliases (needs " +
                                      std::to_string(nx) + " x " + std::to_string(ny) + ")");
     if (d.solve_mx == mx && d.solve_my == my) return APIC_OK;
+    const int old_mx = d.solve_mx, old_my = d.solve_my;
     d.solve_mx = mx;
     d.solve_my = my;
     if (plan->host_only) return APIC_OK;
-    // new device tables (the grid enters the per-image records and the Q lane masks)
+    // new device tables (the grid enters the per-image records and the Q lane masks);
+    // the old ones are freed only once the new ones are in place, and kept (with the
+    // old grid) if the upload fails
     APIC_TRY_CUDA(cudaDeviceSynchronize());
-    if (plan->d_tables) {
-        cudaFree(plan->d_tables);
-        plan->allocs.erase(std::find(plan->allocs.begin(), plan->allocs.end(), plan->d_tables));
-        plan->d_tables = nullptr;
+    void* old_tables = plan->d_tables;
+    const DevPlan old_dev = plan->dev;
+    const apic_status s = upload(plan);
+    if (s != APIC_OK) {
+        plan->d_tables = old_tables;
+        plan->dev = old_dev;
+        d.solve_mx = old_mx;
+        d.solve_my = old_my;
+        return s;
     }
-    return upload(plan);
+    if (old_tables) {
+        cudaFree(old_tables);
+        auto it = std::find(plan->allocs.begin(), plan->allocs.end(), old_tables);
+        if (it != plan->allocs.end()) plan->allocs.erase(it);
+    }
+    return APIC_OK;
 }
 
 apic_status apic_background(apic_plan* plan, int n_tiles, const float* I, float* c2, int32_t* status,
@@ -1159,7 +1201,8 @@ apic_status apic_features(apic_plan* plan, int n_tiles, const float* I, float* f
     apic_status s = check_stage(plan, n_tiles);
     if (s != APIC_OK) return s;
     if (!I || !feat) return fail(APIC_EINVAL, "NULL intensity or features");
-    if (!plan->kkr_ok) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (!plan->kkr_ok || plan->dev.h > 256)
+        return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
     if (plan->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
     if (n_tiles == 0) return APIC_OK;
     APIC_TRY_LAUNCH(launch_features(plan->dev, plan->grid_kkr, n_tiles, I, feat, plan->kk_scratch,

@@ -27,7 +27,10 @@ struct DevDF {
 struct DevPlan {
     int h, w, H, W, n_bf, n_df, n_img;
     int npup, nap, nrows, m, n_used;
-    int mr;                          // register-FFT correlation grid (16 B), 0 if unsupported
+    int mr;                          // register-FFT correlation grid (16 B), 0 if unsupported; 512: the
+                                     // wide kernel of 512-pixel tiles (P * P on the camera grid)
+    int qmask_words;                 // Q membership words per band row (8; 16 for the wide kernel)
+    int max_mx, max_mxy;             // wide kernel: largest row grid and row x column grid of the used images
     int band_u, band_p, band_q;      // largest U, P and Q row bands of the used images
     int max_N, max_M;
     float Rx, Ry;
@@ -65,7 +68,8 @@ struct DevPlan {
     const int* dQ_x; const int* dQ_y;
     const int* d_rowptr;
     const unsigned* d_qmask;         // per used image: Q band rows x 8 words of two 16-bit lane masks
-                                     // (lane t, bit k1: x index t + (mr / 16) k1 is in Q)
+                                     // (lane t, bit k1: x index t + (mr / 16) k1 is in Q; the wide
+                                     // kernel: 16 words, lane-slot t + 16 s)
     // twiddles
     const float2* tw_n;              // n = h = w
     const float2* tw_m;
@@ -75,6 +79,10 @@ struct DevPlan {
     const float2* tw_y8;
     const float2* tw_y9;
     const float2* tw_y10;
+    const float2* tw_w12;            // 192, 256, 288, 320: row and column grids of the wide kernel
+    const float2* tw_w16;
+    const float2* tw_w18;
+    const float2* tw_w20;
 };
 
 // Scratch sizes and grids decided at plan creation.
@@ -126,6 +134,14 @@ int configure_dfr(int B, int BN, size_t smem);
 cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
                                  const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
+
+// wide darkfield kernel of 512-pixel tiles (kernels_dfw.cu)
+size_t dfw_smem_bytes(int max_N, int band_q);
+size_t dfw_scratch_bytes(const DevPlan& P);
+int configure_dfw(size_t smem);
+cudaError_t launch_darkfield_wide(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
+                                  const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
+                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
 
 // Network features (net.cu): feat [n_tiles][64][64][8] from the first 8 images
 // of each stack; `scratch` holds h * 64 complex values per block of `grid`.

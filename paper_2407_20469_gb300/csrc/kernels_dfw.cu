@@ -1,0 +1,602 @@
+// kernels_dfw.cu - darkfield spectrum extension (WSI-APIC Eq. 11-13) for 512-pixel
+// tiles, with the wide register FFTs (16 B points, 16 < B <= 32, two step-B rows
+// per lane).
+//
+// The method is the one of kernels_dfr.cu (CG on the normal equations of Eq. 13,
+// five passes per iteration over a band-row grid; see there), at the sizes of a
+// 512 x 512 tile (pupil radius ~85 grid points, up to ~2.8 k unknowns and ~36 k
+// equations per image):
+//  * the image transform (b = F(I_j) on Q) and P * P run on the camera grid,
+//    n = 512 = 16 x 32 (exact for the lags of Eq. 13: |P - P| <= 2 R < n / 2);
+//  * each image's CG runs on its own (row, column) grid chosen with the plan,
+//    rows of 288 or 320 points and columns of 192, 256, 288 or 320 points, the
+//    smallest on which both correlations are free of aliasing;
+//  * the band grids GU, GQ, the column-major known field p and b on Q live in the
+//    block's global scratch (L2 / HBM): a 512-pixel tile's GU alone (up to 94 rows
+//    of 320 points) exceeds what shared memory can hold beside the transform
+//    areas. Shared memory holds the half-warp transform areas and the CG vectors;
+//    the setup transforms (512-point areas, the column stage) alias both, since no
+//    CG vector is live while an image is being set up.
+// One block of 512 threads per tile (persistent); images of a tile in order.
+// Transforms, vectors and per-thread / per-warp partial sums FP32; the sums across
+// warps and the CG step lengths FP64.
+#include <math.h>
+
+#include <algorithm>
+
+#include "../../include/apic.h"
+#include "internal.cuh"
+#include "regfft.cuh"
+
+namespace apic {
+
+namespace {
+
+#ifndef APIC_DFW_THREADS
+#define APIC_DFW_THREADS 512
+#endif
+constexpr int kWThreads = APIC_DFW_THREADS;
+constexpr int kWHW = kWThreads / 16;       // half-warps per block
+constexpr int kWStageLd = 33;              // column stage: 32 columns + 1 pad
+constexpr int kWBN = 32;                   // camera grid 16 x 32 = 512
+constexpr int kWMaxB = 20;                 // longest CG grid: 16 x 20 = 320 points
+constexpr int kWQWords = 16;               // Q membership words per band row (two 16-bit masks each)
+
+__device__ __forceinline__ int sfreqw(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// Row of a band starting at signed row y0 that lives at grid index i of an m-point
+// axis; >= the band size when none. Needs |y0| < m.
+__device__ __forceinline__ int band_row_w(int i, int y0, int m) {
+    int r = i - y0;
+    if (r >= m) r -= m;
+    if (r < 0) r += m;
+    return r;
+}
+
+struct HWw {
+    int t, hw;
+    unsigned mask;
+    float2* hs;
+    __device__ HalfWarp h() const { return HalfWarp{t, mask, hs}; }
+};
+
+// ---- per-point functors (as in the 256-pixel kernel)
+struct WValKnown {      // P(c) = O_known(K) exp(j phi(c))
+    const float2* sp;
+    const float* ph;
+    const int* ap;
+    const int* pup;
+    __device__ float2 operator()(int e) const {
+        float sn, cs;
+        sincosf(ph[pup[e]], &sn, &cs);
+        return cmul(sp[ap[e]], make_float2(cs, sn));
+    }
+};
+struct WValNextDir {    // d = s + beta d (stored back)
+    const float2* sv;
+    float2* dv;
+    float beta;
+    __device__ float2 operator()(int e) const {
+        const float2 d = cadd(sv[e], cscale(dv[e], beta));
+        dv[e] = d;
+        return d;
+    }
+};
+struct WOutStart {      // s = d = C^H b, x = 0; returns |s|^2
+    float2* sv;
+    float2* dv;
+    float2* xv;
+    __device__ float operator()(int e, float2 v) const {
+        sv[e] = v;
+        dv[e] = v;
+        xv[e] = make_float2(0.f, 0.f);
+        return v.x * v.x + v.y * v.y;
+    }
+};
+struct WValB {          // b on Q
+    const float2* bq;
+    __device__ float2 operator()(int e) const { return bq[e]; }
+};
+struct WOutDot {        // w = C^H C d; returns Re <d, w>
+    float2* wv;
+    const float2* dv;
+    __device__ float operator()(int e, float2 v) const {
+        wv[e] = v;
+        const float2 d = dv[e];
+        return d.x * v.x + d.y * v.y;
+    }
+};
+
+// ---- per-column operations on a column of 16 B points: slot s of lane t holds
+// o[s][k1] = the value at y = (t + 16 s) + B k1 (valid where t + 16 s < B)
+template <int B>
+struct WMidStoreField {     // column-major p s (16 B values per column)
+    float2* PF;
+    float scale;
+    static constexpr bool kOut = false;
+    __device__ void operator()(float2 (&o)[Slots<B>::value][16], int x, int t) const {
+        float2* col = PF + (size_t)x * (16 * B);
+#pragma unroll
+        for (int s = 0; s < Slots<B>::value; ++s)
+            if (t + 16 * s < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) col[t + 16 * s + B * k1] = cscale(o[s][k1], scale);
+            }
+    }
+};
+template <int B>
+struct WMidAbs2 {           // p -> |p|^2
+    static constexpr bool kOut = true;
+    __device__ void operator()(float2 (&o)[Slots<B>::value][16], int, int) const {
+#pragma unroll
+        for (int s = 0; s < Slots<B>::value; ++s)
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) o[s][k1] = make_float2(cabs2(o[s][k1]), 0.f);
+    }
+};
+template <int B, bool CONJ>
+struct WMidTimesField {     // o *= p s or conj(p s), from the column-major copy
+    const float2* PF;
+    static constexpr bool kOut = true;
+    __device__ void operator()(float2 (&o)[Slots<B>::value][16], int x, int t) const {
+        const float2* col = PF + (size_t)x * (16 * B);
+#pragma unroll
+        for (int s = 0; s < Slots<B>::value; ++s)
+            if (t + 16 * s < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const float2 pf = col[t + 16 * s + B * k1];
+                    o[s][k1] = CONJ ? cmulc(o[s][k1], pf) : cmul(o[s][k1], pf);
+                }
+            }
+    }
+};
+
+// ---- passes (each a separate function so registers are allocated per pass)
+
+// rows of a band: scatter val(e) at x = px[e], inverse transform along x, store the
+// rows of G (row stride ld).
+template <int B, class Val>
+__device__ __noinline__ void wpass_rows_in(HWw w, const float2* tw, float2* G, int ld, int nrows, const int* rp,
+                                           const int* px, Val val) {
+    constexpr int m = 16 * B, S = Slots<B>::value;
+    const HalfWarp h = w.h();
+    for (int b = w.hw; b < nrows; b += kWHW) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) w.hs[w.t + 16 * j] = make_float2(0.f, 0.f);
+        __syncwarp(w.mask);
+        for (int e = rp[b] + w.t; e < rp[b + 1]; e += 16) w.hs[freq_index(px[e], m)] = val(e);
+        __syncwarp(w.mask);
+        float2 v[B], o[S][16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = w.hs[w.t + 16 * j];
+        __syncwarp(w.mask);
+        fft_a<B, true>(v, o, h, tw);
+        float2* row = G + (size_t)b * ld;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (w.t + 16 * s < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) row[w.t + 16 * s + B * k1] = o[s][k1];
+            }
+    }
+}
+
+// rows of a band of G: forward transform along x; returns the sum of out(e, value)
+// over this lane's points.
+template <int B, class Out>
+__device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const float2* G, int ld, int nrows,
+                                             const int* rp, const int* px, Out out) {
+    constexpr int m = 16 * B, S = Slots<B>::value;
+    const HalfWarp h = w.h();
+    float acc = 0.f;
+    for (int b = w.hw; b < nrows; b += kWHW) {
+        const float2* row = G + (size_t)b * ld;
+        float2 v[B], o[S][16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        fft_a<B, false>(v, o, h, tw);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (w.t + 16 * s < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + 16 * s + B * k1] = o[s][k1];
+            }
+        __syncwarp(w.mask);
+        for (int e = rp[b] + w.t; e < rp[b + 1]; e += 16) acc += out(e, w.hs[freq_index(px[e], m)]);
+        __syncwarp(w.mask);
+    }
+    return acc;
+}
+
+// columns x < ncols of a grid whose columns have 16 B points: band rows of Gi (row
+// r of the band at grid row (yi0 + r) mod 16 B, ni rows, row stride ldi) are the
+// input, the rest zero; inverse along y, mid, and (Mid::kOut) forward along y with
+// band rows yo0.. (no) stored to Go (row stride ldo). Each half-warp reads and
+// writes its own columns, so Gi and Go may be the same grid. Ends with __syncthreads.
+template <int B, class Mid>
+__device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0,
+                                        int ni, float2* Go, int ldo, int yo0, int no, Mid mid) {
+    constexpr int m = 16 * B, S = Slots<B>::value;
+    const HalfWarp h = w.h();
+    for (int x = w.hw; x < ncols; x += kWHW) {
+        float2 v[B], o[S][16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int bb = band_row_w(w.t + 16 * j, yi0, m);
+            v[j] = bb < ni ? Gi[(size_t)bb * ldi + x] : make_float2(0.f, 0.f);
+        }
+        fft_a<B, true>(v, o, h, tw);
+        mid(o, x, w.t);
+        if constexpr (Mid::kOut) {
+            fft_b<B, false>(o, v, h, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < B; ++k1) {
+                const int bb = band_row_w(w.t + 16 * k1, yo0, m);
+                if (bb < no) Go[(size_t)bb * ldo + x] = v[k1];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// rows of Q in place (row stride 16 B): forward along x, keep the Q lags, inverse
+// along x. qmask: per band row 16 words; the bit k1 of half (t + 16 s) & 1 of word
+// (t + 16 s) >> 1 says whether x index (t + 16 s) + B k1 is in Q. Ends with __syncthreads.
+template <int B>
+__device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G, int nrows, const unsigned* qmask) {
+    constexpr int m = 16 * B, S = Slots<B>::value;
+    const HalfWarp h = w.h();
+    for (int b = w.hw; b < nrows; b += kWHW) {
+        float2* row = G + (size_t)b * m;
+        float2 v[B], o[S][16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        fft_a<B, false>(v, o, h, tw);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int ls = w.t + 16 * s;
+            const unsigned bits = qmask[(size_t)b * kWQWords + (ls >> 1)] >> (16 * (ls & 1));
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1)
+                if (!((bits >> k1) & 1u)) o[s][k1] = make_float2(0.f, 0.f);
+        }
+        fft_b<B, true>(o, v, h, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < B; ++k1) row[w.t + 16 * k1] = v[k1];
+    }
+    __syncthreads();
+}
+
+// columns of the real image (n = 512; with tr the transposed image; read once, with
+// evict-first loads): forward along y, rows qy0.. (nQ) stored to GX (row length n).
+// Chunks of 32 columns are staged through shared memory for coalesced image reads;
+// half-warps 0..31 transform them. The stage aliases the half-warp areas: each stage
+// is consumed (or written) only between barriers that separate it from the
+// transforms. Ends with __syncthreads.
+__device__ __noinline__ void wpass_image_cols(HWw w, const float2* tw, float2* stage, const float* img, float2* GX,
+                                              int qy0, int nQ, bool tr) {
+    constexpr int BN = kWBN, n = 16 * BN, S = Slots<BN>::value;
+    const HalfWarp h = w.h();
+    float* stage_f = reinterpret_cast<float*>(stage);
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        if (tr) {   // column c of the solve frame is image row c
+            for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+                const int c = idx / n, y = idx - c * n;
+                stage_f[y * kWStageLd + c] = __ldcs(img + (size_t)(c0 + c) * n + y);
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+                const int y = idx >> 5, c = idx & 31;
+                stage_f[y * kWStageLd + c] = __ldcs(img + (size_t)y * n + c0 + c);
+            }
+        }
+        __syncthreads();
+        float2 v[BN], o[S][16];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) v[j] = make_float2(stage_f[(w.t + 16 * j) * kWStageLd + w.hw], 0.f);
+        __syncthreads();
+        fft_a<BN, false>(v, o, h, tw);
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (w.t + 16 * s < BN) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const int bb = sfreqw(w.t + 16 * s + BN * k1, n) - qy0;
+                    if (bb >= 0 && bb < nQ) stage[bb * kWStageLd + w.hw] = o[s][k1];
+                }
+            }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nQ * 32; idx += blockDim.x) {
+            const int b = idx >> 5, c = idx & 31;
+            GX[(size_t)b * n + c0 + c] = stage[b * kWStageLd + c];
+        }
+        __syncthreads();
+    }
+}
+
+// rows of GX (length n): forward along x, bq[e] = value / n^2 at the Q points. Ends
+// with __syncthreads.
+__device__ __noinline__ void wpass_image_rows(HWw w, const float2* tw, const float2* GX, int nQ, const int* qrp,
+                                              const int* Qx, float2* bq) {
+    constexpr int BN = kWBN, n = 16 * BN, S = Slots<BN>::value;
+    const HalfWarp h = w.h();
+    const float inv_n2 = 1.f / (float)(n * n);
+    for (int b = w.hw; b < nQ; b += kWHW) {
+        const float2* row = GX + (size_t)b * n;
+        float2 v[BN], o[S][16];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) v[j] = row[w.t + 16 * j];
+        fft_a<BN, false>(v, o, h, tw);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (w.t + 16 * s < BN) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + 16 * s + BN * k1] = o[s][k1];
+            }
+        __syncwarp(w.mask);
+        for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16) bq[e] = cscale(w.hs[freq_index(Qx[e], n)], inv_n2);
+        __syncwarp(w.mask);
+    }
+    __syncthreads();
+}
+
+// rows of Q holding the column-transformed |p|^2 on the camera grid: forward along
+// x, b = bq - (P * P) / n^2 on Q (kept in bq). Ends with __syncthreads.
+__device__ __noinline__ void wpass_rows_rhs(HWw w, const float2* tw, const float2* GQ, int nQ, const int* qrp,
+                                            const int* Qx, float2* bq) {
+    constexpr int B = kWBN, m = 16 * B, S = Slots<B>::value;
+    const HalfWarp h = w.h();
+    const float inv_m2 = 1.f / (float)(m * m);
+    for (int b = w.hw; b < nQ; b += kWHW) {
+        const float2* row = GQ + (size_t)b * m;
+        float2 v[B], o[S][16];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        fft_a<B, false>(v, o, h, tw);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (w.t + 16 * s < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + 16 * s + B * k1] = o[s][k1];
+            }
+        __syncwarp(w.mask);
+        for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16)
+            bq[e] = csub(bq[e], cscale(w.hs[freq_index(Qx[e], m)], inv_m2));
+        __syncwarp(w.mask);
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// Shared memory of one block (bytes, 16-aligned offsets):
+//   [0, vec)          half-warp areas of the CG grids (17 x 20 values each)
+//   [vec, vec_end)    CG vectors x, d, s, w (max_N each)
+//   [0, setup)        during an image's setup: half-warp areas of the 512-point
+//                     transforms (17 x 32 values each), or the 32-column stage
+//   [tw, tw_end)      step twiddles of the camera grid and of the image's row and
+//                     column grids
+//   [red, total)      64 doubles of reductions
+struct DFWSmem {
+    size_t vec, tw, red, total;
+};
+
+__host__ __device__ inline size_t walign16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ inline DFWSmem dfw_smem_layout(int max_N, int band_q) {
+    DFWSmem L;
+    L.vec = walign16((size_t)kWHW * hw_single_size(kWMaxB) * sizeof(float2));
+    const size_t cg_end = L.vec + walign16((size_t)4 * max_N * sizeof(float2));
+    const size_t setup_hw = (size_t)kWHW * hw_single_size(kWBN) * sizeof(float2);
+    const size_t stage_f = (size_t)16 * kWBN * kWStageLd * sizeof(float);
+    const size_t stage_c = (size_t)band_q * kWStageLd * sizeof(float2);
+    const size_t setup = std::max(setup_hw, std::max(stage_f, stage_c));
+    L.tw = walign16(std::max(cg_end, setup));
+    L.red = walign16(L.tw + (size_t)2 * 16 * (kWBN + 2 * kWMaxB) * sizeof(float2));
+    L.total = walign16(L.red + 64 * sizeof(double));
+    return L;
+}
+
+size_t dfw_smem_bytes(int max_N, int band_q) { return dfw_smem_layout(max_N, band_q).total; }
+
+// Global scratch of one block: GQ (Q or P band rows on the camera grid), PF (the
+// column-major known field of the CG grid, or the image's Q rows), GU (U band rows
+// of the CG grid), b on Q.
+size_t dfw_scratch_bytes(const DevPlan& P) {
+    const int n = P.h;
+    size_t s = (size_t)std::max(P.band_q, P.band_p) * n;                                  // GQ
+    s += std::max((size_t)P.max_mxy, (size_t)P.band_q * n);                               // PF / F(I) rows
+    s += (size_t)P.band_u * P.max_mx;                                                     // GU
+    s += (size_t)P.max_M;                                                                 // b on Q
+    return (s * sizeof(float2) + 255) & ~(size_t)255;
+}
+
+namespace {
+
+struct DFWCtx {
+    HWw w;                  // half-warp areas of the CG grids
+    HWw ws;                 // half-warp areas of the 512-point setup transforms
+    const float2* tw_n;     // step twiddles of the camera grid
+    float2* tw_x;           // step twiddles of the image's row grid (filled per image)
+    float2* tw_y;           // step twiddles of the image's column grid (filled per image)
+    float2 *GU, *GQ, *PF, *bq;
+    float2 *dv, *sv, *wv, *xv;
+    float2* stage;
+    double* red;
+};
+
+// plain twiddle table of a 16 G-point grid of the wide solve
+__device__ __forceinline__ const float2* wgrid_table(const DevPlan& P, int G) {
+    return G == 12 ? P.tw_w12 : G == 16 ? P.tw_w16 : G == 18 ? P.tw_w18 : P.tw_w20;
+}
+
+// Solve of one darkfield image once b = F(I) on Q is in bq, on a grid of 16 BX row
+// points x 16 BY column points; P * P on the camera grid. Returns the CG iterations
+// (negative: did not converge).
+template <int BX, int BY>
+__device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, const DevDF& D, float2* sp,
+                                         const float* ph, int iters, float tol) {
+    constexpr int n = 16 * kWBN, mx = 16 * BX;
+    const HWw& w = c.w;
+    const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
+    const int uy0 = D.uy0, qy0 = D.qy0, py0 = D.py0;
+    const int N = D.N, nU = D.uy1 - uy0 + 1, nQ = D.qy1 - qy0 + 1, nP = D.py1 - py0 + 1;
+    const int *urp = P.d_rowptr + D.urp, *qrp = P.d_rowptr + D.qrp, *prp = P.d_rowptr + D.prp;
+    const unsigned* qmask = P.d_qmask + D.qmask_off;
+    const WValKnown pval{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off};
+    make_step_twiddles(c.tw_x, wgrid_table(P, BX), BX);
+    make_step_twiddles(c.tw_y, wgrid_table(P, BY), BY);
+    __syncthreads();
+    // P * P on the camera grid: band rows of P along x, |p|^2 per column and back
+    // along y on the Q band rows, then rows forward: b -= P * P on Q
+    wpass_rows_in<kWBN>(c.ws, c.tw_n, c.GQ, n, nP, prp, P.dP_x + p_off, pval);
+    __syncthreads();
+    wpass_cols<kWBN>(c.ws, c.tw_n, n, c.GQ, n, py0, nP, c.GQ, n, qy0, nQ, WMidAbs2<kWBN>{});
+    wpass_rows_rhs(c.ws, c.tw_n, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
+    // band rows of the known field P (Eq. 11) along x on the row grid, then p s on
+    // the column grid, column-major in PF (s = 1 / (mx my): the two unnormalised
+    // transforms around each product)
+    const float scale = 1.f / ((float)mx * (float)(16 * BY));
+    wpass_rows_in<BX>(w, c.tw_x, c.GQ, mx, nP, prp, P.dP_x + p_off, pval);
+    __syncthreads();
+    wpass_cols<BY>(w, c.tw_y, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, WMidStoreField<BY>{c.PF, scale});
+    // rows of b inverse along x on the row grid; s = d = C^H b
+    wpass_rows_in<BX>(w, c.tw_x, c.GQ, mx, nQ, qrp, P.dQ_x + q_off, WValB{c.bq});
+    __syncthreads();
+    wpass_cols<BY>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
+    const float g0 = wpass_rows_out<BX>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutStart{c.sv, c.dv, c.xv});
+    int par = 0;
+    const double gamma0 = block_sum2f(g0, c.red, par);
+    // CGNR
+    double gamma = gamma0;
+    bool conv = !(gamma0 > 1e-300);
+    const double stop = (double)tol * (double)tol * gamma0;
+    int it = 0;
+    float bf = 0.f;
+    for (; it < iters && !conv; ++it) {
+        wpass_rows_in<BX>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WValNextDir{c.sv, c.dv, bf});
+        __syncthreads();
+        wpass_cols<BY>(w, c.tw_y, mx, c.GU, mx, uy0, nU, c.GQ, mx, qy0, nQ, WMidTimesField<BY, true>{c.PF});
+        wpass_rows_mask<BX>(w, c.tw_x, c.GQ, nQ, qmask);
+        wpass_cols<BY>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
+        const float dw = wpass_rows_out<BX>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutDot{c.wv, c.dv});
+        const double delta = block_sum2f(dw, c.red, par);
+        if (!(delta > 0)) break;
+        const double alpha = gamma / delta;
+        const float af = (float)alpha;
+        float g2 = 0.f;
+        for (int e = threadIdx.x; e < N; e += blockDim.x) {
+            const float2 d = c.dv[e];
+            float2 x = c.xv[e];
+            x.x += af * d.x;
+            x.y += af * d.y;
+            c.xv[e] = x;
+            const float2 sv = csub(c.sv[e], cscale(c.wv[e], af));
+            c.sv[e] = sv;
+            g2 += sv.x * sv.x + sv.y * sv.y;
+        }
+        const double gnew = block_sum2f(g2, c.red, par);
+        bf = (float)(gnew / gamma);
+        gamma = gnew;
+        conv = gnew <= stop;
+    }
+    // corrected unknown spectrum into the tile's spectrum
+    const int* Upup = P.dU_pup + u_off;
+    const int* Uap = P.dU_ap + u_off;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        float sn, cs;
+        sincosf(ph[Upup[e]], &sn, &cs);
+        sp[Uap[e]] = cmul(c.xv[e], make_float2(cs, -sn));
+    }
+    __syncthreads();
+    return conv ? it : -1 - it;
+}
+
+__global__ void __launch_bounds__(kWThreads, 1)
+k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
+                 float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
+                 int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
+    constexpr int n = 16 * kWBN;
+    extern __shared__ float4 smem4[];
+    char* sbase = reinterpret_cast<char*>(smem4);
+    const DFWSmem SL = dfw_smem_layout(P.max_N, P.band_q);
+    DFWCtx c;
+    c.dv = reinterpret_cast<float2*>(sbase + SL.vec);
+    c.sv = c.dv + P.max_N;
+    c.wv = c.sv + P.max_N;
+    c.xv = c.wv + P.max_N;
+    c.stage = reinterpret_cast<float2*>(sbase);
+    float2* tw_n = reinterpret_cast<float2*>(sbase + SL.tw);
+    c.tw_n = tw_n;
+    c.tw_x = tw_n + 2 * 16 * kWBN;
+    c.tw_y = c.tw_x + 2 * 16 * kWMaxB;
+    c.red = reinterpret_cast<double*>(sbase + SL.red);
+    make_step_twiddles(tw_n, P.tw_n, kWBN);
+
+    c.w.hw = c.ws.hw = threadIdx.x >> 4;
+    c.w.t = c.ws.t = threadIdx.x & 15;
+    c.w.mask = c.ws.mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
+    c.w.hs = reinterpret_cast<float2*>(sbase) + c.w.hw * hw_single_size(kWMaxB);
+    c.ws.hs = reinterpret_cast<float2*>(sbase) + c.ws.hw * hw_single_size(kWBN);
+
+    char* base = scratch + (size_t)blockIdx.x * per_block;
+    c.GQ = reinterpret_cast<float2*>(base);
+    c.PF = c.GQ + (size_t)max(P.band_q, P.band_p) * n;
+    c.GU = c.PF + max((size_t)P.max_mxy, (size_t)P.band_q * n);
+    c.bq = c.GU + (size_t)P.band_u * P.max_mx;
+    __syncthreads();
+
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
+        const float* ph = phi + (size_t)tile * P.npup;
+        float2* sp = spec + (size_t)tile * P.nap;
+        bool notconv = false;
+        for (int di = 0; di < P.n_used; ++di) {
+            const DevDF& D = P.df[di];
+            const int nQ = D.qy1 - D.qy0 + 1;
+            const float* img = I + ((size_t)tile * P.n_img + D.led) * n * n;
+            // b = F(I_j) on Q (F(I) rows staged in PF)
+            wpass_image_cols(c.ws, c.tw_n, c.stage, img, c.PF, D.qy0, nQ, D.tr != 0);
+            wpass_image_rows(c.ws, c.tw_n, c.PF, nQ, P.d_rowptr + D.qrp, P.dQ_x + D.q_off, c.bq);
+            int r;
+            switch (16 * D.bx + D.by) {
+                case 16 * 18 + 12: r = dfw_solve<18, 12>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 18 + 16: r = dfw_solve<18, 16>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 18 + 18: r = dfw_solve<18, 18>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 20 + 12: r = dfw_solve<20, 12>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 20 + 16: r = dfw_solve<20, 16>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 20 + 18: r = dfw_solve<20, 18>(c, P, D, sp, ph, iters, tol); break;
+                default: r = dfw_solve<20, 20>(c, P, D, sp, ph, iters, tol); break;
+            }
+            if (r < 0) notconv = true;
+            if (threadIdx.x == 0 && counters) {
+                atomicAdd(counters + 1, (unsigned long long)(r < 0 ? -1 - r : r));
+                atomicAdd(counters + 2, 1ull);
+            }
+        }
+        if (threadIdx.x == 0 && notconv && status) atomicOr(status + tile, APIC_TILE_NOTCONV);
+    }
+}
+
+}  // namespace
+
+int configure_dfw(size_t smem) {
+    if (raise_smem_limit((const void*)k_darkfield_wide, smem) != cudaSuccess) return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_darkfield_wide, kWThreads, smem) != cudaSuccess)
+        return 0;
+    return occ;
+}
+
+cudaError_t launch_darkfield_wide(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
+                                  const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
+                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st) {
+    if (P.h != 16 * kWBN || P.w != P.h) return cudaErrorInvalidValue;
+    k_darkfield_wide<<<min(grid, n_tiles), kWThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch,
+                                                                  per_block, iters, tol, status, counters);
+    return cudaGetLastError();
+}
+
+}  // namespace apic

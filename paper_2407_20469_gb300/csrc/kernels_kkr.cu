@@ -1,5 +1,6 @@
 // kernels_kkr.cu - Kramers-Kronig recovery (WSI-APIC Eq. 4-7) with
-// register-resident half-warp FFTs (n = 16 BN).
+// register-resident half-warp FFTs (n = 16 BN; BN = 32 for 512-pixel tiles uses the
+// wide form, two step-B rows per lane).
 //
 // One block per (tile, NA-matching image) problem, persistent over problems;
 // an n x n complex scratch grid per block (L2-resident). Each half-warp
@@ -34,7 +35,7 @@ __device__ __forceinline__ int sfreq_kk(int i, int n) { return i < n / 2 ? i : i
 }  // namespace
 
 size_t kkr_smem_bytes(int BN) {
-    const int hws = std::max(17 * BN, 16 * (BN + 1));
+    const int hws = hw_single_size(BN);
     return (size_t)kKKHW * hws * sizeof(float2) + (size_t)2 * 16 * BN * sizeof(float2) + 64 * sizeof(double);
 }
 
@@ -42,7 +43,7 @@ template <int BN>
 __global__ void __launch_bounds__(kKKThreads, 1)
 k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict__ xdisc, float2* __restrict__ scratch,
          const int32_t* __restrict__ status) {
-    constexpr int n = 16 * BN, HWS = HWSize<BN>::value;
+    constexpr int n = 16 * BN, HWS = HWSize<BN>::value, S = Slots<BN>::value;
     extern __shared__ float4 smem4[];
     float2* hw_area = reinterpret_cast<float2*>(smem4);
     float2* tw = hw_area + kKKHW * HWS;
@@ -76,34 +77,38 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
         // P1: rows, log then forward along x
         for (int r = hw; r < n; r += kKKHW) {
             const float* row = img + (size_t)r * n;
-            float2 v[BN], o[16];
+            float2 v[BN], o[S][16];
 #pragma unroll
             for (int j = 0; j < BN; ++j)      // last read of the image: evict first from L2
                 v[j] = make_float2(__logf(fmaxf(__ldcs(row + t + 16 * j), eps)), 0.f);
-            fft_alpha<BN, false>(v, o, h, tw);
-            if (t < BN) {
-                float2* gr = G + (size_t)r * n;
+            fft_a<BN, false>(v, o, h, tw);
+            float2* gr = G + (size_t)r * n;
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) gr[t + BN * k1] = o[k1];
-            }
+            for (int s = 0; s < S; ++s)
+                if (t + 16 * s < BN) {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) gr[t + 16 * s + BN * k1] = o[s][k1];
+                }
         }
         __syncthreads();
         // P2: columns, forward along y, Eq. 5 mask, inverse along y
         for (int x = hw; x < n; x += kKKHW) {
-            float2 v[BN], o[16];
+            float2 v[BN], o[S][16];
 #pragma unroll
             for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * n + x];
-            fft_alpha<BN, false>(v, o, h, tw);
-            if (t < BN) {
-                const long long kxp = (long long)sfreq_kk(x, n) * kix * hh;
+            fft_a<BN, false>(v, o, h, tw);
+            const long long kxp = (long long)sfreq_kk(x, n) * kix * hh;
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) {
-                    const long long dot = kxp + (long long)sfreq_kk(t + BN * k1, n) * kiy * ww;
-                    const float f = dot < 0 ? 1.f : (dot == 0 ? 0.5f : 0.f);
-                    o[k1] = cscale(o[k1], f);
+            for (int s = 0; s < S; ++s)
+                if (t + 16 * s < BN) {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) {
+                        const long long dot = kxp + (long long)sfreq_kk(t + 16 * s + BN * k1, n) * kiy * ww;
+                        const float f = dot < 0 ? 1.f : (dot == 0 ? 0.5f : 0.f);
+                        o[s][k1] = cscale(o[s][k1], f);
+                    }
                 }
-            }
-            fft_beta<BN, true>(o, v, h, tw);
+            fft_b<BN, true>(o, v, h, tw);
 #pragma unroll
             for (int k1 = 0; k1 < BN; ++k1) G[(size_t)(t + 16 * k1) * n + x] = v[k1];
         }
@@ -115,21 +120,23 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
         // P3: rows, inverse along x, exp, forward along x; the band columns are stored
         for (int r = hw; r < n; r += kKKHW) {
             float2* gr = G + (size_t)r * n;
-            float2 v[BN], o[16];
+            float2 v[BN], o[S][16];
 #pragma unroll
             for (int j = 0; j < BN; ++j) v[j] = gr[t + 16 * j];
-            fft_alpha<BN, true>(v, o, h, tw);
-            if (t < BN) {
+            fft_a<BN, true>(v, o, h, tw);
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) {
-                    const float2 z = cscale(o[k1], inv_n2);
-                    float sn, cs;
-                    __sincosf(z.y, &sn, &cs);
-                    const float e = __expf(z.x);
-                    o[k1] = make_float2(e * cs, e * sn);
+            for (int s = 0; s < S; ++s)
+                if (t + 16 * s < BN) {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) {
+                        const float2 z = cscale(o[s][k1], inv_n2);
+                        float sn, cs;
+                        __sincosf(z.y, &sn, &cs);
+                        const float e = __expf(z.x);
+                        o[s][k1] = make_float2(e * cs, e * sn);
+                    }
                 }
-            }
-            fft_beta<BN, false>(o, v, h, tw);
+            fft_b<BN, false>(o, v, h, tw);
 #pragma unroll
             for (int k1 = 0; k1 < BN; ++k1) {
                 const int x = t + 16 * k1;
@@ -140,18 +147,20 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
         // P4: band columns, forward along y, series normalisation, band rows stored
         for (int c = hw; c < nbx; c += kKKHW) {
             const int x = freq_index(kx0 + c, n);
-            float2 v[BN], o[16];
+            float2 v[BN], o[S][16];
 #pragma unroll
             for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * n + x];
-            fft_alpha<BN, false>(v, o, h, tw);
-            if (t < BN) {
+            fft_a<BN, false>(v, o, h, tw);
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) {
-                    const int y = t + BN * k1;
-                    if ((unsigned)(sfreq_kk(y, n) - ky0 + n) % (unsigned)n < (unsigned)nby)
-                        G[(size_t)y * n + x] = cscale(o[k1], inv_n2);
+            for (int s = 0; s < S; ++s)
+                if (t + 16 * s < BN) {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) {
+                        const int y = t + 16 * s + BN * k1;
+                        if ((unsigned)(sfreq_kk(y, n) - ky0 + n) % (unsigned)n < (unsigned)nby)
+                            G[(size_t)y * n + x] = cscale(o[s][k1], inv_n2);
+                    }
                 }
-            }
         }
         __syncthreads();
         float2* out = xdisc + ((size_t)tile * P.n_bf + i) * P.npup;
@@ -170,6 +179,7 @@ static KKRKernel kkr_kernel(int BN) {
         case 4: return k_kk_reg<4>;
         case 8: return k_kk_reg<8>;
         case 16: return k_kk_reg<16>;
+        case 32: return k_kk_reg<32>;
         default: return nullptr;
     }
 }

@@ -34,8 +34,20 @@ const DFGrid kDFGrids[] = {{192, 192, 2.0}, {192, 144, 1.68}, {192, 128, 1.13}, 
                            {160, 128, 1.13}, {160, 96, 1.0},  {144, 144, 1.68}};
 }  // namespace
 
+// Wide kernel (512-point camera grid): rows of 288 or 320 points, columns of 192,
+// 256, 288 or 320 points (a column of more than 256 points costs two DFT_16 steps
+// per lane instead of one).
+const DFGrid kDFWideGrids[] = {{288, 192, 1.0}, {288, 256, 1.12}, {288, 288, 1.62},
+                               {320, 192, 1.0}, {320, 256, 1.12}, {320, 288, 1.62}, {320, 320, 1.65}};
+
 bool df_grid_supported(int mx, int my) {
     for (const DFGrid& g : kDFGrids)
+        if (g.mx == mx && g.my == my) return true;
+    return false;
+}
+
+bool df_wide_grid_supported(int mx, int my) {
+    for (const DFGrid& g : kDFWideGrids)
         if (g.mx == mx && g.my == my) return true;
     return false;
 }
@@ -70,22 +82,27 @@ void df_grid_needs(const DarkfieldHost& d, int& nx, int& ny) {
 //   exact one (df_grid_needs) with the least estimated work per iteration
 //   (columns x relative cost of a column) is used. Other register grids use
 //   mr x mr.
-static void solve_grid(DarkfieldHost& d, int mr) {
+// - on the wide kernel's 512-point grid (512-pixel tiles) the row and column grids
+//   come from kDFWideGrids alone; returns false when none is exact for the image.
+static bool solve_grid(DarkfieldHost& d, int mr) {
     auto extent = [](const std::vector<int>& v) {
         return v.empty() ? 0 : *std::max_element(v.begin(), v.end()) - *std::min_element(v.begin(), v.end()) + 1;
     };
     d.solve_tr = extent(d.Q_x) < extent(d.Q_y) ? 1 : 0;
     d.solve_mx = d.solve_my = mr;
-    if (mr != 192 || d.U_x.empty() || d.P_x.empty() || d.Q_x.empty()) return;
+    if ((mr != 192 && mr != 512) || d.U_x.empty() || d.P_x.empty() || d.Q_x.empty()) return true;
     int nx = 0, ny = 0;
     df_grid_needs(d, nx, ny);
     double best = 1e300;
-    for (const DFGrid& g : kDFGrids)
+    bool found = mr != 512;
+    for (const DFGrid& g : (mr == 512 ? kDFWideGrids : kDFGrids))
         if (g.mx >= nx && g.my >= ny && g.mx * g.col_cost < best) {
             best = g.mx * g.col_cost;
             d.solve_mx = g.mx;
             d.solve_my = g.my;
+            found = true;
         }
+    return found;
 }
 namespace {
 
@@ -405,8 +422,15 @@ std::string build_host_plan(const GeomParams& p, HostPlan& P) {
             P.mr = 16 * B;
             break;
         }
+    // 512-pixel tiles: the wide kernel (P * P on the camera grid, per-image CG grids)
+    if (P.mr == 0 && p.h == 512 && p.w == 512 && 4 * rint + 1 <= 512) P.mr = 512;
+    bool grids_ok = true;
     for (auto& d : P.df)
-        if (d.used) solve_grid(d, P.mr);
+        if (d.used) grids_ok = solve_grid(d, P.mr) && grids_ok;
+    if (!grids_ok) {     // some image needs a longer grid than the wide kernel has
+        P.mr = 0;
+        for (auto& d : P.df) d.solve_mx = d.solve_my = 0;
+    }
     for (auto& d : P.df)
         for (size_t q = 0; q < d.Q_x.size(); ++q)
             if (2 * std::abs(d.Q_x[q]) >= p.w || 2 * std::abs(d.Q_y[q]) >= p.h)

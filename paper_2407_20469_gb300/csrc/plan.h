@@ -53,15 +53,18 @@ struct HostPlan {
     // darkfield images in processing order (increasing |k|, then angle)
     std::vector<DarkfieldHost> df;
     int m = 0;                                // grid of the darkfield correlations (power of two)
-    int mr = 0;                               // register-FFT grid 16 B (B in 4, 6, 8, 12, 16), 0 if none
+    int mr = 0;                               // register-FFT grid 16 B (B in 4, 6, 8, 12, 16; 512 for the
+                                              // wide kernel of 512-pixel tiles), 0 if none
 
     int pupil_index(int kx, int ky) const;
 };
 
 // Builds the plan; returns an empty string on success, else the reason.
 std::string build_host_plan(const GeomParams& p, HostPlan& out);
-// Supported (row, column) grids of the register darkfield solve on the 192-point grid.
+// Supported (row, column) grids of the register darkfield solve on the 192-point grid,
+// and of the wide kernel's solve (512-pixel tiles).
 bool df_grid_supported(int mx, int my);
+bool df_wide_grid_supported(int mx, int my);
 // Least alias-free grid lengths of a used darkfield image along its solve frame's rows and columns.
 void df_grid_needs(const DarkfieldHost& d, int& nx, int& ny);
 

@@ -312,3 +312,81 @@ __device__ __forceinline__ void fft_beta2(float2 (&o)[16], float2 (&va)[B], floa
 }
 
 }  // namespace apic
+
+namespace apic {
+
+// ---- wide transforms: N = 16 B with 16 < B <= 32 (288, 320, 384, 512 points).
+// Step A is the same DFT_B in registers; step B has B DFT_16s, so lane t runs two
+// of them, rows k2 = t and k2 = t + 16 (slot 0 and slot 1; slot 1 only where t + 16 < B,
+// other lanes transform a copy of row t and discard it). Outputs and inputs of the
+// second orientation are therefore held in two slots per lane: value o[s][k1] of lane
+// t is X[(t + 16 s) + B k1]. Same step twiddles and half-warp area (17 B values) as
+// the single form.
+template <int B>
+struct Slots {
+    static constexpr int value = B > 16 ? 2 : 1;
+};
+
+// alpha_w: v[j] = x[t + 16 j] (j < B) -> o[s][k1] = X[(t + 16 s) + B k1].
+template <int B, bool INV>
+__device__ __forceinline__ void fft_alpha_w(float2 (&v)[B], float2 (&o)[2][16], const HalfWarp& h,
+                                            const float2* tw) {
+    static_assert(B > 16 && B <= 32, "alpha_w needs 16 < B <= 32");
+    DFT<B, INV>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) h.hs[k2 * 17 + h.t] = cmul(v[k2], tw_get(tw, k2 * 16 + h.t, INV));
+    __syncwarp(h.mask);
+    const int r1 = h.t + 16 < B ? h.t + 16 : h.t;
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        o[0][n1] = h.hs[h.t * 17 + n1];
+        o[1][n1] = h.hs[r1 * 17 + n1];
+    }
+    DFT<16, INV>::run(o[0]);
+    DFT<16, INV>::run(o[1]);
+    __syncwarp(h.mask);
+}
+
+// beta_w: slot s of lane t (u = t + 16 s < B) holds o[s][j] = x[u + B j] (j < 16) ->
+// every lane: v[k1] = X[t + 16 k1] (k1 < B).
+template <int B, bool INV>
+__device__ __forceinline__ void fft_beta_w(float2 (&o)[2][16], float2 (&v)[B], const HalfWarp& h,
+                                           const float2* tw) {
+    static_assert(B > 16 && B <= 32, "beta_w needs 16 < B <= 32");
+    DFT<16, INV>::run(o[0]);
+    DFT<16, INV>::run(o[1]);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int u = h.t + 16 * s;
+        if (u < B) {
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) h.hs[k2 * (B + 1) + u] = cmul(o[s][k2], tw_get(tw, 16 * B + k2 * B + u, INV));
+        }
+    }
+    __syncwarp(h.mask);
+#pragma unroll
+    for (int u = 0; u < B; ++u) v[u] = h.hs[h.t * (B + 1) + u];
+    DFT<B, INV>::run(v);
+    __syncwarp(h.mask);
+}
+
+// One interface for both forms: o[Slots<B>][16], slot s of lane t carrying the row
+// t + 16 s of step B (valid where t + 16 s < B).
+template <int B, bool INV>
+__device__ __forceinline__ void fft_a(float2 (&v)[B], float2 (&o)[Slots<B>::value][16], const HalfWarp& h,
+                                      const float2* tw) {
+    if constexpr (B > 16)
+        fft_alpha_w<B, INV>(v, o, h, tw);
+    else
+        fft_alpha<B, INV>(v, o[0], h, tw);
+}
+template <int B, bool INV>
+__device__ __forceinline__ void fft_b(float2 (&o)[Slots<B>::value][16], float2 (&v)[B], const HalfWarp& h,
+                                      const float2* tw) {
+    if constexpr (B > 16)
+        fft_beta_w<B, INV>(o, v, h, tw);
+    else
+        fft_beta<B, INV>(o[0], v, h, tw);
+}
+
+}  // namespace apic

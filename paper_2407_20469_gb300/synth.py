@@ -128,3 +128,46 @@ def tile_grid_uv(rows: int, cols: int) -> np.ndarray:
     """Tile-centre coordinates in [-1, 1]^2 for a rows x cols grid, [rows*cols, 2] (u, v)."""
     v, u = np.meshgrid(np.linspace(-1, 1, rows), np.linspace(-1, 1, cols), indexing="ij")
     return np.stack([u.ravel(), v.ravel()], axis=1).astype(np.float32)
+
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (Steele, Lea and Flood, 2014) on uint64 arrays."""
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def counter_uniform(seed: int, shape, stream: int = 0) -> np.ndarray:
+    """Uniform numbers in (0, 1), one per element, from a counter-based generator:
+    element i is mix64(key + (i + 1) * golden) with key = mix64(seed, stream), so it
+    depends on (seed, stream, i) only and uses integer arithmetic alone (the same
+    bits on every platform)."""
+    n = int(np.prod(shape))
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([(seed & 0xFFFFFFFF) | ((stream & 0xFFFFFFFF) << 32)], dtype=np.uint64))[0]
+        i = np.arange(1, n + 1, dtype=np.uint64)
+        z = _mix64(key + i * _GOLDEN)
+    return (((z >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53).reshape(shape)
+
+
+def poisson_counts(lam: np.ndarray, seed: int, stream: int = 0) -> np.ndarray:
+    """Poisson(lam) photon counts by inversion of the Poisson distribution function
+    at one counter-based uniform per element (``counter_uniform``). Each count
+    depends only on its own uniform and mean, so inputs regenerated on another
+    platform agree element by element (a count can differ only where its uniform
+    falls within rounding of a distribution-function step)."""
+    from scipy import stats
+    lam = np.asarray(lam, dtype=np.float64)
+    u = counter_uniform(seed, lam.shape, stream)
+    out = np.zeros(lam.shape, dtype=np.float64)
+    m = lam > 0
+    out[m] = stats.poisson.ppf(u[m], lam[m])
+    return out
+
+
+def noisy_stack(I: np.ndarray, photons: float, seed: int, stream: int = 0) -> np.ndarray:
+    """Shot-noise version of a noise-free intensity stack: poisson_counts(photons I) / photons."""
+    return poisson_counts(np.asarray(I, np.float64) * photons, seed, stream) / photons

@@ -37,12 +37,24 @@ def test_noalloc_kk_spectra_match_regular_entry_point_on_two_calls(n, count):
         I = torch.from_numpy(make_tiles(n, count, seed=seed + n)[0]).cuda()
         ref = _regular(plan, I)
         out = torch.full_like(ref, float("nan"))
+        torch.cuda.synchronize()
+        free0, used0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         plan.kk_spectra_noalloc(count, I, out)
         torch.cuda.synchronize()
+        # the call allocated nothing: neither device memory as a whole nor torch's pool moved
+        assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == used0, f"call {call}"
         a, b = as_complex(out), as_complex(ref)
         assert np.all(np.isfinite(a)), f"call {call}: unwritten output"
         err = np.linalg.norm(a - b) / np.linalg.norm(b)
         assert err < 1e-6, f"call {call}: relative difference {err:.2e}"
+
+
+def test_noalloc_wrapper_refuses_short_buffers():
+    plan = apic.Plan.from_illumination(64, synth.illumination(), max_tiles=1)
+    I = torch.zeros((1, 24, 64, 64), dtype=torch.float32, device="cuda")
+    out = torch.zeros((1, 8, 2 * plan.info.n_pupil), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        plan.kk_spectra_noalloc(2, I, out)                 # two tiles in buffers of one
 
 
 def test_noalloc_rejects_host_only_plan():
