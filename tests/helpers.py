@@ -72,3 +72,26 @@ def to_interleaved(z):
     out[..., 0::2] = z.real
     out[..., 1::2] = z.imag
     return out
+
+
+GOLDEN_512_SEED = 3
+
+
+def golden_512_inputs(seed=GOLDEN_512_SEED):
+    """The seeded 512 x 512 tile with 8 + 24 images of the mixed-precision workload:
+    amplitude 0.8-1.0, phase 0-pi, Noll 4..15 uniform in +-1 rad, shot noise at 1e4
+    photons per unit intensity (counter-based, so the same on every platform).
+    Returns (intensity float32 [32, 512, 512], c15, geometry, snapped LEDs, illumination)."""
+    n, ill = 512, synth.illumination_8_24()
+    g = geometry(n)
+    k = grid.snap_leds(ill.kx, ill.ky, ill.n_bf, g)
+    rng = np.random.default_rng(seed)
+    obj = synth.sample_object(rng, g.H, g.W, 4.0)
+    c = synth.zernike_coefficients(rng, 1.0)
+    I = forward.intensity_stack(obj, g, k, c)
+    I = synth.noisy_stack(I, synth.PHOTONS, seed).astype(np.float32)
+    return I, c, g, k, ill
+
+
+def unpack_mask(bits, shape):
+    return np.unpackbits(bits, count=int(np.prod(shape))).reshape(shape).astype(bool)
