@@ -1,24 +1,29 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the GB300 APIC library (one JSON line on stdout).
 
-Workload (one step): 512 tiles of 256 x 256 low-resolution pixels, 8 NA-matching
-+ 16 darkfield images each (illumination NA 0.30 / 0.38), 0.25 NA, 0.52 um,
-0.345 um pixels, 2x upsampling to 512 x 512, per-tile Zernike coefficients
-varying as a 2-D quadratic across a 16 x 32 tile grid, Poisson noise at 1e4
+Default workload (one step, the mixed-precision configuration): 2048 tiles of
+512 x 512 low-resolution pixels (the paper's patch size), 8 NA-matching + 24
+darkfield images each (illumination NA 0.29 / 0.34 / 0.40), 0.25 NA, 0.52 um,
+0.345 um pixels, 2x upsampling to 1024 x 1024, per-tile Zernike coefficients
+varying as a 2-D quadratic across a 32 x 64 tile grid, Poisson noise at 1e4
 photons per pixel; the sample is a smoothed random transmission (amplitude
 0.8-1.0, phase 0-pi). Inputs are synthesised on the device before timing and
-are larger than L2 (3.2 GB of intensities per step).
+are far larger than L2 (68.7 GB of intensities per step).
+--workload cfg2: 512 tiles of 256 x 256 with 8 + 16 images (NA 0.30 / 0.38).
 
-value: output Mpx/s = tiles * 512^2 * steps / timed seconds, all ranks.
-e2e:   the same through host buffers (pinned H2D of the intensities and D2H of
-       the fields inside the timed region).
-roofline: the darkfield kernel (the dominant one) against the FP32 ALU peak.
-cpu_baseline: the float64 checker on one tile of the same workload, on the
-       host cores; the GPU result of that tile is compared with it (parity).
+value: output Mpx/s = tiles * 1024^2 * steps / timed seconds, all ranks.
+e2e:   the same through host buffers (apic_reconstruct_host: pinned H2D of the
+       intensities and D2H of the fields inside the timed region).
+roofline: the darkfield kernel (the dominant one) against the measured FP32
+       FMA rate of this GPU (apic_measure_fma_rate); hbm_frac: the step's
+       algorithmic bytes (inputs + fields) over the step time against the
+       measured HBM copy rate.
+cpu_baseline: the float64 checker on a bounded sample of one tile of the same
+       workload, on the host cores.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-Multi-GPU (torchrun): each rank reconstructs its own 512 tiles (weak scaling,
-no collective on the data path); barrier + max-over-ranks timing.
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload cfg2|rgb|blend]
+Multi-GPU (torchrun): each rank reconstructs its own tiles (weak scaling, no
+collective on the data path); barrier + max-over-ranks timing.
 """
 from __future__ import annotations
 
@@ -40,15 +45,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "APIC output Mpx/s at <=1e-3 rel L2 vs FP64 oracle; % of HBM roofline"
-WORKLOAD = ("512 tiles x 256x256 low-res (512x512 output), 8 NA-matching + 16 darkfield images, "
-            "quadratic field-dependent Zernike over a 16x32 tile grid, Poisson 1e4 photons/px")
+WORKLOADS = {
+    # name: (tile, tiles, images, zernike grid rows x cols)
+    "cfg3": (512, 2048, "8+24", (32, 64)),
+    "cfg2": (256, 512, "8+16", (16, 32)),
+}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC = os.path.join(ROOT, "profiles", "darkfield_traffic.json")
+PROFILES = os.path.join(ROOT, "profiles")
 DEFAULT_DF_TOL = 3e-4          # the library's darkfield CG tolerance (apic_params.df_tol <= 0)
-DF_SOURCES = ["kernels_dfr.cu", "regfft.cuh", "common.cuh", "internal.cuh"]
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
-SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+DF_SOURCES = {256: ["kernels_dfr.cu", "regfft.cuh", "common.cuh", "internal.cuh"],
+              512: ["kernels_dfw.cu", "regfft.cuh", "common.cuh", "internal.cuh"]}
+DF_KERNEL = {256: "k_darkfield_reg", 512: "k_darkfield_wide"}
+HOST_TILES_E2E = 512           # pinned host buffers of the end-to-end leg hold this many tiles at most
 
 
 def parse():
@@ -57,23 +65,30 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["apic", "reference"], default="apic")
-    ap.add_argument("--tiles", type=int, default=512)
-    ap.add_argument("--tile", type=int, default=256)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--tiles", type=int, default=None, help="tiles per step (default: the workload's)")
+    ap.add_argument("--tile", type=int, default=None, help="tile side (default: the workload's)")
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-assisted timing")
     ap.add_argument("--per-tile", type=int, default=32,
                     help="tiles timed one call at a time for the unbatched comparison (0: skip)")
-    ap.add_argument("--images", choices=["8+16", "8+24", "12+22"], default="8+16",
+    ap.add_argument("--images", choices=["8+16", "8+24", "12+22"], default=None,
                     help="illumination set (8+24: rings at NA 0.29 / 0.34 / 0.40; 12+22: the paper's set-up size, "
                          "darkfield rings at NA 0.31 / 0.375 / 0.44)")
-    ap.add_argument("--workload", choices=["tiles", "rgb", "blend"], default="tiles",
-                    help="tiles: the batch reconstruction (default line); rgb: the same batch at three wavelengths, "
-                         "one plan each; blend: overlap blending of a 16 x 32 window grid with 6 %% overlap")
+    ap.add_argument("--workload", choices=["cfg3", "cfg2", "rgb", "blend"], default="cfg3",
+                    help="cfg3: 2048 tiles of 512 x 512 with 8 + 24 images (default line); cfg2: 512 tiles of "
+                         "256 x 256 with 8 + 16 images; rgb: the cfg2 batch at three wavelengths, one plan each; "
+                         "blend: overlap blending of a 16 x 32 window grid with 6 %% overlap")
     ap.add_argument("--seed", type=int, default=2407)
     ap.add_argument("--df-tol", type=float, default=0.0, help="CGLS tolerance (0: library default)")
     ap.add_argument("--df-iters", type=int, default=0, help="CGLS iteration cap (0: library default)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    tile, tiles, images, grid = WORKLOADS["cfg2" if a.workload in ("cfg2", "rgb", "blend") else "cfg3"]
+    a.tile = a.tile or tile
+    a.tiles = a.tiles or tiles
+    a.images = a.images or images
+    a.zgrid = grid if a.tile == tile and a.tiles == tiles else (16, 32)
+    return a
 
 
 # ----------------------------------------------------------------------------- inputs
@@ -169,50 +184,172 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- reference arm
 
-def oracle_tile_sample(n, seed):
+def oracle_tile_sample(n, images, seed, zgrid=(16, 32)):
     """One tile of the workload from the checker's forward model (float64 on the host)."""
     from oracle import forward, grid
     from paper_2407_20469_gb300 import synth
-    ill = synth.illumination()
+    ill = illumination_for(images)
     g = grid.Geometry(n, n, float(synth.NA), float(synth.WAVELENGTH_UM), float(synth.PIXEL_UM), 2)
     k = grid.snap_leds(ill.kx, ill.ky, ill.n_bf, g)
     rng = np.random.default_rng(seed)
     obj = synth.sample_object(rng, g.H, g.W, 4.0)
-    c = field_zernike()[0].astype(np.float64)
+    c = field_zernike(*zgrid)[0].astype(np.float64)
     I = forward.intensity_stack(obj, g, k, c, photons=synth.PHOTONS, rng=rng).astype(np.float32)
     return I, g, k, ill
 
 
-def run_oracle(I, g, k, n_bf):
-    from oracle import apic as oapic
-    t0 = time.perf_counter()
-    res = oapic.reconstruct_tile(I.astype(np.float64), g, k, n_bf)
-    return res, time.perf_counter() - t0
+class OracleTile:
+    """The float64 checker run on one tile in the paper's order, one piece at a time:
+    the brightfield stages (Kramers-Kronig, aberration solve, stitch), then the
+    darkfield solves one image at a time (each on the spectrum the previous ones
+    left). Only oracle/ functions compute; this class times them."""
+
+    def __init__(self, I, g, k, n_bf):
+        from oracle import grid
+        self.I, self.g, self.k, self.n_bf = I.astype(np.float64), g, k, n_bf
+        self.order = [int(j) for j in grid.darkfield_order(k[n_bf:])]
+        self.next = 0
+        self.spec = None
+        self.sizes = self._sizes()
+
+    def _sizes(self):
+        """(|U|, |Q|) of every darkfield image in order (geometry only: the known set
+        grows by each used image's U)."""
+        from oracle import grid
+        from oracle import apic as oapic
+        spec = oapic.Spectrum(self.g)
+        for kb in self.k[:self.n_bf]:
+            spec.put(grid.disc_points(self.g, kb), 1.0)
+        out = []
+        for j in self.order:
+            kj = self.k[self.n_bf + j]
+            sets = grid.darkfield_sets(grid.disc_points(self.g, kj), spec.known_set(), j, kj)
+            out.append((len(sets.U), len(sets.Q)) if sets.used else (0, 0))
+            if sets.used:
+                spec.put(sets.U, 1.0)
+        return out
+
+    def brightfield(self):
+        from oracle import apic as oapic
+        t0 = time.perf_counter()
+        g, k, nb = self.g, self.k, self.n_bf
+        X = [oapic.kk_spectrum(self.I[i], k[i], g) for i in range(nb)]
+        rows = oapic.overlap_rows(g, k[:nb])
+        self.c15 = oapic.aberration_solve(oapic.phase_differences(X, rows), rows)
+        self.spec = oapic.stitch_brightfield(X, g, k[:nb], self.c15)
+        self.next = 0
+        return time.perf_counter() - t0
+
+    def darkfield_next(self):
+        """Solves the next darkfield image; returns (build seconds, solve seconds, index in order)."""
+        from oracle import apic as oapic
+        from oracle import grid
+        if self.spec is None or self.next >= len(self.order):
+            self.brightfield()
+        idx = self.next
+        j = self.order[idx]
+        self.next += 1
+        kj = self.k[self.n_bf + j]
+        t0 = time.perf_counter()
+        sets = grid.darkfield_sets(grid.disc_points(self.g, kj), self.spec.known_set(), j, kj)
+        if not sets.used:
+            return time.perf_counter() - t0, 0.0, idx
+        C, b, _ = oapic.darkfield_system(sets, self.I[self.n_bf + j], self.spec, self.g, self.c15)
+        t1 = time.perf_counter()
+        x = oapic.lstsq_normal(C, b)
+        U = sets.U
+        phiU = oapic.pupil_phase(self.g, self.c15, U[:, 0] + kj[0], U[:, 1] + kj[1])
+        self.spec.put(U, x * np.exp(-1j * phiU))
+        return t1 - t0, time.perf_counter() - t1, idx
+
+    def tile_seconds(self, t_bf, measured):
+        """Per-tile time: the brightfield stages plus every darkfield solve, measured ones
+        as measured and the others estimated from them (the dense system build taken as
+        constant per image - its cost is |Q| |P|, nearly the same for every image - and
+        the normal-equation solve scaled by |U|^2 |Q|)."""
+        builds = [b for b, _, _ in measured]
+        rate = sum(s for _, s, _ in measured) / max(1e-300, sum(self.sizes[i][0] ** 2 * self.sizes[i][1]
+                                                                for _, _, i in measured))
+        done = {i: b + s for b, s, i in measured}
+        total = t_bf
+        for i, (N, M) in enumerate(self.sizes):
+            if N == 0:
+                continue
+            total += done[i] if i in done else statistics.mean(builds) + rate * N * N * M
+        return total
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def oracle_baseline(n, images, seed, zgrid, df_solves):
+    """cpu_baseline dict: the checker on one tile of the workload, the brightfield stages
+    and the first `df_solves` darkfield solves timed (all of them if df_solves <= 0)."""
+    I, g, k, ill = oracle_tile_sample(n, images, seed, zgrid)
+    ot = OracleTile(I, g, k, ill.n_bf)
+    t_bf = ot.brightfield()
+    count = len(ot.order) if df_solves <= 0 else min(df_solves, len(ot.order))
+    measured = [ot.darkfield_next() for _ in range(count)]
+    secs = ot.tile_seconds(t_bf, measured)
+    work = t_bf + sum(b + s for b, s, _ in measured)
+    est = "" if count == len(ot.order) else (f"; the other {len(ot.order) - count} solves estimated from the "
+                                             f"measured one(s) (build time per image, solve time scaled by |U|^2 |Q|)")
+    return {"value": (2 * n) ** 2 / secs / 1e6, "unit": "Mpx/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"1 tile of {n}x{n} ({images} images), numpy float64: brightfield stages and "
+                      f"{count} of {len(ot.order)} darkfield solves timed ({work:.1f} s of CPU work){est}; "
+                      f"tile time {secs:.1f} s",
+            "tile_seconds": secs}
 
 
 def reference_arm(args):
+    """The float64 checker on the host cores. 256-pixel tiles: one whole tile per step.
+    512-pixel tiles: one darkfield solve per step, in order on one tile (the brightfield
+    stages of the tile run, timed, before the first step); value from the per-tile time
+    of OracleTile.tile_seconds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     n = args.tile
-    I, g, k, ill = oracle_tile_sample(n, args.seed)
-    for _ in range(args.warmup):
-        run_oracle(I, g, k, ill.n_bf)
-    times = []
-    for _ in range(args.steps):
-        times.append(run_oracle(I, g, k, ill.n_bf)[1])
-    total = sum(times)
-    out_px = (2 * n) ** 2
-    value = args.steps * out_px / total / 1e6
-    cores = os.cpu_count()
+    I, g, k, ill = oracle_tile_sample(n, args.images, args.seed, args.zgrid)
+    ot = OracleTile(I, g, k, ill.n_bf)
+    if n <= 256:
+        def step():
+            t0 = time.perf_counter()
+            t_bf = ot.brightfield()
+            meas = [ot.darkfield_next() for _ in range(len(ot.order))]
+            return time.perf_counter() - t0, t_bf, meas
+        for _ in range(args.warmup):
+            step()
+        runs = [step() for _ in range(args.steps)]
+        times = [r[0] for r in runs]
+        tile_s = statistics.mean(times)
+        sample = f"1 whole tile of {n}x{n} ({args.images} images) per step"
+    else:
+        t_bf = ot.brightfield()
+        for _ in range(args.warmup):
+            ot.darkfield_next()
+        meas, times = [], []
+        for _ in range(args.steps):
+            if ot.next >= len(ot.order):
+                t_bf = ot.brightfield()
+            t0 = time.perf_counter()
+            meas.append(ot.darkfield_next())
+            times.append(time.perf_counter() - t0)
+        tile_s = ot.tile_seconds(t_bf, meas)
+        sample = (f"one darkfield solve per step, in order on one {n}x{n} tile ({args.images} images); "
+                  f"per-tile time {tile_s:.1f} s = brightfield stages {t_bf:.1f} s + the {len(ot.order)} solves "
+                  f"(measured or estimated from the measured ones)")
+    value = (2 * n) ** 2 / tile_s / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"1 tile of {n}x{n} per step", "tiles_per_step": 1},
-        "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": cores, "kind": "oracle",
-                         "sample": f"1 tile of {n}x{n} (8+16 images) per step, numpy float64"},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.tiles, n, 2 * n, args.images, args.zgrid), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -220,21 +357,37 @@ def reference_arm(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def df_flops_per_solve(n, m, iters):
-    """Algorithmic FP32 flops of darkfield solves: 5 N log2 N per complex N-point 2-D FFT.
-
-    Per solve: F(I_j) (one n x n transform), the known field and P*P (two m x m),
-    the first C^H r (two); per CGLS iteration C d and C^H r (four m x m).
-    """
-    fft = lambda s: 5.0 * s * s * math.log2(s * s)
-    return fft(n) + 4 * fft(m), 4 * fft(m) * iters
+def fft2_flops(a, b):
+    """Algorithmic flops of one complex a x b 2-D FFT: 5 N log2 N, N = a b."""
+    N = a * b
+    return 5.0 * N * math.log2(N)
 
 
-def source_sha():
+def df_flops(plan, n):
+    """Per used darkfield image: (setup flops per solve, flops per CG iteration), dense-grid counts.
+
+    Setup: the image's n x n transform, P * P (two transforms on the P * P grid: the
+    camera grid for 512-pixel tiles, the register grid otherwise), the known field and
+    C^H b on the image's grid (three); per CG iteration C d and C^H r (four transforms
+    on the image's grid)."""
+    m = plan.info.fft_m
+    pp = n if n == 512 else m
+    out = []
+    for i in range(plan.info.n_df):
+        _, meta = plan.df_set(i, 0)
+        if not meta[1]:
+            continue
+        _, mx, my = plan.df_grid(i)
+        mx, my = (mx or m), (my or m)
+        out.append((fft2_flops(n, n) + 2 * fft2_flops(pp, pp) + 3 * fft2_flops(mx, my), 4 * fft2_flops(mx, my)))
+    return out
+
+
+def source_sha(n):
     """Hash of the darkfield kernel's code (comments and whitespace left out, so that
-    only a code change invalidates the recorded DRAM traffic)."""
+    only a code change invalidates the recorded counters)."""
     h = hashlib.sha256()
-    for f in DF_SOURCES:
+    for f in DF_SOURCES[512 if n == 512 else 256]:
         with open(os.path.join(ROOT, "paper_2407_20469_gb300", "csrc", f)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
@@ -243,11 +396,38 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
-def workload_name(T, n, H, images):
-    if (T, n, images) == (512, 256, "8+16"):
-        return WORKLOAD
-    return (f"{T} tiles x {n}x{n} low-res ({H}x{H} output), {images} images, quadratic field-dependent "
-            f"Zernike, Poisson 1e4 photons/px")
+def recorded_counters(n, T, images, tol, iters):
+    """ncu figures of the darkfield kernel recorded under profiles/ for this workload and
+    this kernel source, or {}: DRAM bytes per launch (scaled to the bench's launch) and
+    the FMA-pipe share (executed work)."""
+    path = os.path.join(PROFILES, f"darkfield_counters_{n}.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        tr = json.load(fh)
+    if (tr.get("source_sha") != source_sha(n) or tr.get("tile") != n or tr.get("images") != images
+            or abs(tr.get("df_tol", 0) - tol) > 1e-12 or iters):
+        return {}
+    out = {}
+    if tr.get("dram_bytes_per_tile"):
+        out["traffic"] = tr["dram_bytes_per_tile"] * T
+    if tr.get("fma_pipe_frac") is not None:
+        out["frac_executed"] = tr["fma_pipe_frac"]
+    return out
+
+
+def workload_name(T, n, H, images, zgrid):
+    na = {"8+16": "NA 0.30/0.38", "8+24": "NA 0.29/0.34/0.40", "12+22": "NA 0.31/0.375/0.44"}[images]
+    return (f"{T} tiles x {n}x{n} low-res ({H}x{H} output), {images} images (darkfield {na}), quadratic "
+            f"field-dependent Zernike over a {zgrid[0]}x{zgrid[1]} tile grid, Poisson 1e4 photons/px")
+
+
+def measured_peaks():
+    """(HBM GB/s, kind) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    if os.path.exists(PEAKS):
+        with open(PEAKS) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    return 6800.0, "fallback"
 
 
 def learned_timing(args, plan, ill, T, n, H, I, field, zern, status, device):
@@ -309,15 +489,21 @@ def gpu_arm(args):
     n_img = info.n_bf + info.n_df
 
     # ---- inputs (device), outside the timed region
-    zern_true = torch.from_numpy(np.resize(field_zernike(), (T, 15))).to(device)
-    obj = device_objects(T, H, args.seed + 7919 * rank, device)
+    zern_true = torch.from_numpy(np.resize(field_zernike(*args.zgrid), (T, 15))).to(device)
     I = torch.empty((T, n_img, n, n), dtype=torch.float32, device=device)
-    plan.simulate(T, obj, zern_true, synth.PHOTONS, args.seed + rank, I)
-    del obj
+    for t0 in range(0, T, 256):         # objects in slices: (2n)^2 complex values per tile
+        t1 = min(T, t0 + 256)
+        obj = device_objects(t1 - t0, H, args.seed + 7919 * rank + t0, device)
+        plan.simulate(t1 - t0, obj, zern_true[t0:t1], synth.PHOTONS, args.seed + rank + t0, I[t0:t1])
+        del obj
     field = torch.empty((T, H, 2 * H), dtype=torch.float32, device=device)
     zern = torch.empty((T, 15), dtype=torch.float32, device=device)
     status = torch.empty((T,), dtype=torch.int32, device=device)
     torch.cuda.synchronize()
+    # roofline denominators measured on this GPU (before the timed region)
+    fp32_peak = apic.measure_fma_rate(32) / 1e12
+    fp64_peak = apic.measure_fma_rate(64) / 1e12
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
 
     for _ in range(args.warmup):
         plan.reconstruct_batch(T, I, field, zern, None, status)
@@ -326,10 +512,7 @@ def gpu_arm(args):
     plan.stage_ms(reset=True)
     plan.counters(reset=True)
 
-    props = torch.cuda.get_device_properties(device)
-    uuid = str(getattr(props, "uuid", ""))
-    gpu_id = ("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(device.index))
-    clocks = ClockSampler(gpu_id)
+    clocks = ClockSampler(clock_id(device))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -374,25 +557,31 @@ def gpu_arm(args):
         per_tile = {"value": pt_value, "unit": "Mpx/s", "tiles": k, "ms_per_tile": pt_ms / k,
                     "batched_over_per_tile": None}
 
-    # ---- learned-assisted reconstruction on the same inputs: a network trained
-    # here for a few seconds on simulated tiles, warm-starting the aberration
-    # solve (features + network forward + second refinement inside the timing)
+    # ---- learned-assisted reconstruction on the same inputs (the network takes tiles of
+    # up to 256 pixels): a network trained here for a few seconds on simulated tiles,
+    # warm-starting the aberration solve (features + network forward + second refinement
+    # inside the timing)
     learned = None
-    if not args.no_learned:
+    if not args.no_learned and n <= 256:
         learned = learned_timing(args, plan, ill, T, n, H, I, field, zern, status, device)
 
-    # ---- end to end through host buffers: apic_reconstruct_host pipelines the
-    # pinned host->device copies, the reconstruction and the device->host copies
+    # ---- end to end through host buffers: apic_reconstruct_host pipelines the pinned
+    # host->device copies, the reconstruction and the device->host copies. The pinned
+    # buffers hold at most HOST_TILES_E2E tiles (a step of 2048 512-pixel tiles would pin
+    # 86 GB of host memory); a step is then several calls over consecutive tile ranges,
+    # each copying its inputs in and its fields out.
     e2e = None
     if args.e2e_steps > 0:
-        I_host = torch.empty(I.shape, dtype=torch.float32, pin_memory=True)
-        I_host.copy_(I)
-        f_host = torch.empty(field.shape, dtype=torch.float32, pin_memory=True)
-        z_host = torch.empty(zern.shape, dtype=torch.float32, pin_memory=True)
-        s_host = torch.empty(status.shape, dtype=torch.int32, pin_memory=True)
+        Th = min(T, HOST_TILES_E2E)
+        I_host = torch.empty((Th,) + tuple(I.shape[1:]), dtype=torch.float32, pin_memory=True)
+        I_host.copy_(I[:Th])
+        f_host = torch.empty((Th,) + tuple(field.shape[1:]), dtype=torch.float32, pin_memory=True)
+        z_host = torch.empty((Th, 15), dtype=torch.float32, pin_memory=True)
+        s_host = torch.empty((Th,), dtype=torch.int32, pin_memory=True)
         del I
         torch.cuda.synchronize()
-        plan.reconstruct_host(T, I_host, f_host, z_host, s_host)      # first call sets up the pipeline
+        chunks = [(a, min(T, a + Th)) for a in range(0, T, Th)]
+        plan.reconstruct_host(Th, I_host, f_host, z_host, s_host)      # first call sets up the pipeline
         # host link bandwidth for context: one pinned host->device copy of the inputs
         probe = torch.empty(I_host.shape, dtype=torch.float32, device=device)
         c0 = torch.cuda.Event(enable_timing=True)
@@ -413,53 +602,64 @@ def gpu_arm(args):
         step_ms = []
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
-            plan.reconstruct_host(T, I_host, f_host, z_host, s_host)
+            for a, b in chunks:
+                plan.reconstruct_host(b - a, I_host, f_host, z_host, s_host)
             step_ms.append((time.perf_counter() - t0) * 1e3)
         ems = sum(step_ms)
         if world > 1:
             t = torch.tensor([ems], dtype=torch.float64, device=device)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
+        per_tile_in = I_host[0].numel() * 4
+        per_tile_out = f_host[0].numel() * 4 + 15 * 4 + 4
         e2e = {"value": world * T * H * H * args.e2e_steps / (ems / 1e3) / 1e6, "unit": "Mpx/s",
-               "h2d_bytes_per_step": int(I_host.numel() * 4),
-               "d2h_bytes_per_step": int(f_host.numel() * 4 + z_host.numel() * 4 + s_host.numel() * 4),
-               "steps": args.e2e_steps, "api": "apic_reconstruct_host (pinned host buffers)",
+               "h2d_bytes_per_step": int(T * per_tile_in), "d2h_bytes_per_step": int(T * per_tile_out),
+               "steps": args.e2e_steps,
+               "api": f"apic_reconstruct_host (pinned host buffers of {Th} tiles, {len(chunks)} call(s) per step)",
                "h2d_gbs_measured": h2d_gbs, "d2h_gbs_measured": d2h_gbs,
-               "step_ms": [round(v, 2) for v in step_ms]}
+               "step_ms": [round(v, 2) for v in step_ms], "step_ms_median": statistics.median(step_ms)}
         del I_host, f_host, z_host, s_host
 
-    # ---- roofline of the darkfield kernel (algorithmic flops / live event time)
+    # ---- roofline of the darkfield kernel: dense-grid algorithmic flops of its launches
+    # (per image: setup per solve + CG iterations x per-iteration flops) over their live
+    # event time, against the measured FP32 FMA rate
     df_ms = stage["darkfield"] / max(calls, 1)
-    setup, per_it = df_flops_per_solve(n, info.fft_m, 1)
-    solves = cnt["df_solves"] / max(calls, 1)
-    iters = cnt["cg_iterations"] / max(calls, 1)
-    flops = solves * setup + iters * per_it
+    per_img = df_flops(plan, n)
+    iters_img = cnt["cg_iterations_per_image"]
+    solves_per_img = cnt["df_solves"] / max(1, len(per_img))
+    flops = sum(solves_per_img * s + it * p for (s, p), it in zip(per_img, iters_img)) / max(calls, 1)
     achieved = flops / (df_ms / 1e3) / 1e12
-    traffic = None
-    if os.path.exists(TRAFFIC):
-        with open(TRAFFIC) as fh:
-            tr = json.load(fh)
-        tol = args.df_tol if args.df_tol > 0 else DEFAULT_DF_TOL
-        if (tr.get("source_sha") == source_sha() and tr.get("tile") == n and tr.get("tiles") == T
-                and tr.get("images", "8+16") == args.images
-                and abs(tr.get("df_tol", 0) - tol) < 1e-12 and not args.df_iters):
-            traffic = tr.get("dram_bytes_per_launch")
-    roofline = {"bound": "alu", "kernel": "k_darkfield_reg", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_kind": "derived FP32 CUDA-core peak (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                "launch_ms": df_ms, "cg_iterations_per_launch": iters, "solves_per_launch": solves,
-                "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage.items()}}
+    tol = args.df_tol if args.df_tol > 0 else DEFAULT_DF_TOL
+    rec = recorded_counters(n, T, args.images, tol, args.df_iters)
+    hbm_gbs, hbm_kind = measured_peaks()
+    bytes_per_step = T * (n_img * n * n * 4 + H * H * 8)
+    roofline = {"bound": "alu", "kernel": DF_KERNEL[512 if n == 512 else 256], "achieved": achieved,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": rec.get("traffic"),
+                "peak_kind": f"measured FP32 FMA rate of this GPU (apic_measure_fma_rate; {sms} SMs)",
+                "flops_kind": "dense-grid count: 5 N log2 N per 2-D transform of each image's own grid; the kernel "
+                              "transforms only band rows, so it executes fewer",
+                "frac_executed": rec.get("frac_executed"),
+                "fp64_peak_tflops": fp64_peak,
+                "launch_ms": df_ms, "cg_iterations_per_launch": cnt["cg_iterations"] / max(calls, 1),
+                "solves_per_launch": cnt["df_solves"] / max(calls, 1),
+                "stage_ms_per_step": {k: v / max(calls, 1) for k, v in stage.items()},
+                "hbm_frac": bytes_per_step / (ms / args.steps / 1e3) / (hbm_gbs * 1e9),
+                "hbm_frac_kind": f"algorithmic bytes per step (intensities in + fields out, "
+                                 f"{bytes_per_step / 1e9:.1f} GB) / step time / {hbm_gbs:.0f} GB/s {hbm_kind}"}
 
     value = world * T * H * H * args.steps / (ms / 1e3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(T, n, H, args.images), "tiles_per_gpu": T, "tile": n, "output": H,
-                   "images": n_img,
-                   "l2": "inputs_larger_than_l2 (3.2 GB intensities per step)", "launch": "direct C-ABI calls",
-                   "tiles_per_s": world * T * args.steps / (ms / 1e3),
+        "config": {"workload": workload_name(T, n, H, args.images, args.zgrid), "tiles_per_gpu": T, "tile": n,
+                   "output": H, "images": n_img,
+                   "l2": f"inputs_larger_than_l2 ({T * n_img * n * n * 4 / 1e9:.1f} GB intensities per step)",
+                   "launch": "direct C-ABI calls", "tiles_per_s": world * T * args.steps / (ms / 1e3),
                    "df_tol": args.df_tol or "library default", "fft_m": info.fft_m,
+                   "precision": "FFTs, elementwise math and CG vectors FP32; aberration normal equations and "
+                                "darkfield CG step lengths / cross-warp sums FP64",
                    "tiles_status_nonzero": int(np.count_nonzero(status_np))},
         "roofline": roofline, "e2e": e2e, "gpu_launches": cnt["launches"], "clocks": clk,
     }
@@ -468,29 +668,11 @@ def gpu_arm(args):
     if per_tile is not None:
         per_tile["batched_over_per_tile"] = value / per_tile["value"]
         line["per_tile_calls"] = per_tile
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.images == "8+16":
-        I1, g1, k1, ill1 = oracle_tile_sample(n, args.seed)
-        res, secs = run_oracle(I1, g1, k1, ill1.n_bf)
-        line["cpu_baseline"] = {"value": (2 * n) ** 2 / secs / 1e6, "unit": "Mpx/s", "cores": os.cpu_count(),
-                                "kind": "oracle",
-                                "sample": f"1 tile of {n}x{n} (8+16 images) of the workload, numpy float64, "
-                                          f"{secs:.1f} s"}
-        # parity of the GPU path on that same tile
-        Id = torch.from_numpy(I1).to(device)[None].contiguous()
-        f1 = torch.empty((1, H, 2 * H), dtype=torch.float32, device=device)
-        z1 = torch.empty((1, 15), dtype=torch.float32, device=device)
-        plan.reconstruct_batch(1, Id, f1, z1, None, None)
-        torch.cuda.synchronize()
-        a = f1[0].cpu().numpy().astype(np.float64)
-        est = a[:, 0::2] + 1j * a[:, 1::2]
-        zr = np.vdot(est, res.field)
-        est = est * (zr / abs(zr))
-        line["parity"] = {"field_rel_l2": float(np.linalg.norm(est - res.field) / np.linalg.norm(res.field)),
-                          "pupil_rms_rad": float(np.sqrt(np.sum((z1[0].cpu().numpy()[3:] - res.c15[3:]) ** 2))),
-                          "sample": "the cpu_baseline tile"}
+    plan.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(n, args.images, args.seed, args.zgrid, 1 if n > 256 else 0)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -541,7 +723,7 @@ def rgb_arm(args):
     C = len(RGB_UM)
     info = cp.plan(RGB_UM[0]).info
     H = info.out_h
-    zern_true = torch.from_numpy(np.resize(field_zernike(), (T, 15))).to(device)
+    zern_true = torch.from_numpy(np.resize(field_zernike(*args.zgrid), (T, 15))).to(device)
     I, F, Z, S = [], [], [], []
     for c, w in enumerate(RGB_UM):
         p = cp.plan(w)
@@ -561,6 +743,7 @@ def rgb_arm(args):
         cp.plan(w).timing(True)
         cp.plan(w).stage_ms(reset=True)
         cp.plan(w).counters(reset=True)
+    fp32_peak = apic.measure_fma_rate(32) / 1e12
     ms, clk = timed(step, args.steps, device)
     df_ms = flops = launches = 0.0
     per_channel = {}
@@ -569,8 +752,9 @@ def rgb_arm(args):
         stage, calls = p.stage_ms(reset=True)
         cnt = p.counters(reset=True)
         p.timing(False)
-        setup, per_it = df_flops_per_solve(n, p.info.fft_m, 1)
-        f = (cnt["df_solves"] * setup + cnt["cg_iterations"] * per_it) / max(calls, 1)
+        per_img = df_flops(p, n)
+        spi = cnt["df_solves"] / max(1, len(per_img))
+        f = sum(spi * a + it * b for (a, b), it in zip(per_img, cnt["cg_iterations_per_image"])) / max(calls, 1)
         d = stage["darkfield"] / max(calls, 1)
         df_ms += d
         flops += f
@@ -588,8 +772,9 @@ def rgb_arm(args):
                                f"{list(RGB_UM)} um, 8+16 images each, one plan per wavelength",
                    "channels": C, "tiles_per_channel": T, "l2": "inputs_larger_than_l2",
                    "tiles_status_nonzero": int(np.count_nonzero(st)), "per_channel": per_channel},
-        "roofline": {"bound": "alu", "kernel": "k_darkfield_reg", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "k_darkfield_reg", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_kind": "measured FP32 FMA rate of this GPU (apic_measure_fma_rate)",
                      "launch_ms": df_ms},
         "e2e": None, "gpu_launches": int(launches), "clocks": clk,
     }

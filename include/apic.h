@@ -118,6 +118,17 @@ const char* apic_status_string(apic_status s);
 const char* apic_last_error(void);
 
 /*
+ * Measured FMA throughput of the current device's CUDA cores, in flop/s (one
+ * FMA = 2 flops), for precision 32 (FP32) or 64 (FP64): a kernel of
+ * independent multiply-add chains on every SM, the best of three timed
+ * launches after one warm-up (CUDA events on the legacy default stream, which
+ * it synchronises). The denominator of the rooflines of the library's
+ * ALU-bound kernels; the paper has no counterpart. Changes no device setting.
+ * Errors: APIC_EINVAL (other precision, NULL output), APIC_ECUDA.
+ */
+apic_status apic_measure_fma_rate(int precision, double* h_flops_per_s);
+
+/*
  * Build a plan: snap the illumination to the grid (NA-matching LEDs keep the
  * DC term on the edge of the shifted pupil, Sec. 2.3), enumerate the overlap
  * sets S_il (Eq. 8), the darkfield sets U, P, Q (Eq. 11-13, images taken by
@@ -205,7 +216,11 @@ apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* d_
 /*
  * Work counters of a plan since creation or the last reset, for throughput
  * accounting: h_out[0] kernel launches issued, h_out[1] CGLS iterations run,
- * h_out[2] darkfield least-squares solves run. Up to n values are written.
+ * h_out[2] darkfield least-squares solves run, h_out[3 + i] the CGLS
+ * iterations of the i-th used darkfield image (in the processing order of
+ * apic_plan_df_set / apic_plan_df_grid, skipped images not counted; the first
+ * 256 used images).
+ * Up to n values are written.
  * Synchronises the device (reads a device counter); reset != 0 zeroes them.
  */
 apic_status apic_plan_counters(apic_plan* plan, int64_t* h_out, int n, int reset);

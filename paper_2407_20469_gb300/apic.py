@@ -36,6 +36,7 @@ EXPORTS = [
     "apic_net_destroy", "apic_net_set_params", "apic_net_get_params", "apic_net_get_grads", "apic_net_forward",
     "apic_net_backward", "apic_net_adamw", "apic_net_activation", "apic_features", "apic_reconstruct_learned",
     "apic_slide_windows", "apic_cut_tiles", "apic_paste_fields", "apic_blend_fields", "apic_plan_autotune",
+    "apic_measure_fma_rate",
 ]
 
 
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_status_string": (C.c_char_p, [i32]),
         "apic_last_error": (C.c_char_p, []),
         "apic_plan_create": (i32, [C.POINTER(apic_params), C.POINTER(vp)]),
+        "apic_measure_fma_rate": (i32, [i32, C.POINTER(C.c_double)]),
         "apic_plan_destroy": (i32, [vp]),
         "apic_plan_query": (i32, [vp, C.POINTER(apic_plan_info)]),
         "apic_plan_table": (i32, [vp, i32, C.POINTER(C.c_int32), sz]),
@@ -161,6 +163,13 @@ def _stream(stream) -> int | None:
     return stream.cuda_stream
 
 
+def measure_fma_rate(precision: int = 32) -> float:
+    """Measured FMA throughput (flop/s) of the current device's CUDA cores, FP32 or FP64."""
+    out = C.c_double()
+    _check(load().apic_measure_fma_rate(int(precision), C.byref(out)), "apic_measure_fma_rate")
+    return float(out.value)
+
+
 def slide_windows(slide_h: int, slide_w: int, tile: int, stride: int) -> np.ndarray:
     """Windows [n, 6] int32 (y0, x0, oy0, ox0, oy1, ox1) covering a slide (apic_slide_windows)."""
     lib = load()
@@ -244,11 +253,14 @@ class Plan:
         _check(load().apic_plan_set_df_grid(self.handle, index, mx, my), "apic_plan_set_df_grid")
 
     def counters(self, reset: bool = False) -> dict:
-        """Work counters: kernel launches, CGLS iterations, darkfield solves (synchronises)."""
-        out = np.zeros(3, dtype=np.int64)
-        _check(load().apic_plan_counters(self.handle, out.ctypes.data_as(C.POINTER(C.c_int64)), 3, int(reset)),
+        """Work counters: kernel launches, CGLS iterations, darkfield solves, and the CGLS
+        iterations of each used darkfield image (synchronises)."""
+        k = 3 + min(self.info.n_df_used, 256)
+        out = np.zeros(k, dtype=np.int64)
+        _check(load().apic_plan_counters(self.handle, out.ctypes.data_as(C.POINTER(C.c_int64)), k, int(reset)),
                "apic_plan_counters")
-        return {"launches": int(out[0]), "cg_iterations": int(out[1]), "df_solves": int(out[2])}
+        return {"launches": int(out[0]), "cg_iterations": int(out[1]), "df_solves": int(out[2]),
+                "cg_iterations_per_image": [int(v) for v in out[3:]]}
 
     STAGES = ("background", "kk", "aberration", "stitch", "darkfield", "synthesize", "pupil")
 

@@ -119,7 +119,7 @@ struct apic_plan {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr, ev_pre = nullptr, ev_mbe = nullptr;
     float* feat = nullptr;                       // learned path: features, network coefficients
     float* c_net = nullptr;
-    unsigned long long* d_counters = nullptr;   // [0] unused, [1] CGLS iterations, [2] solves
+    unsigned long long* d_counters = nullptr;   // kCounters: [1] CG iterations, [2] solves, [4 + i] per image
     long long launches = 0;                      // kernel launches issued
     // stage timing: ring of kTimingSlots calls x kStages x {start, stop}
     bool timing = false;
@@ -429,8 +429,8 @@ apic_status alloc_workspace(apic_plan* p) {
     if ((s = dmalloc(p, (void**)&p->spec, T * D.nap * sizeof(float2))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->status, T * sizeof(int32_t))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->c2, T * sizeof(float))) != APIC_OK) return s;
-    if ((s = dmalloc(p, (void**)&p->d_counters, 4 * sizeof(unsigned long long))) != APIC_OK) return s;
-    APIC_TRY_CUDA(cudaMemset(p->d_counters, 0, 4 * sizeof(unsigned long long)));
+    if ((s = dmalloc(p, (void**)&p->d_counters, kCounters * sizeof(unsigned long long))) != APIC_OK) return s;
+    APIC_TRY_CUDA(cudaMemset(p->d_counters, 0, kCounters * sizeof(unsigned long long)));
     const size_t kk_blocks = (size_t)std::max(p->L.grid_kk, p->grid_kkr);
     if ((s = dmalloc(p, (void**)&p->kk_scratch, kk_blocks * D.h * D.h * sizeof(float2))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->beta_scratch, (size_t)p->L.grid_ab * D.nrows * sizeof(float))) != APIC_OK)
@@ -795,6 +795,14 @@ const char* apic_status_string(apic_status s) {
 
 const char* apic_last_error(void) { return g_last_error.c_str(); }
 
+apic_status apic_measure_fma_rate(int precision, double* h_flops_per_s) {
+    if (!h_flops_per_s) return fail(APIC_EINVAL, "NULL output");
+    if (precision != 32 && precision != 64) return fail(APIC_EINVAL, "precision must be 32 or 64");
+    const cudaError_t e = measure_fma_rate(precision, h_flops_per_s);
+    if (e != cudaSuccess) return cuda_fail(e, "FMA rate kernel");
+    return APIC_OK;
+}
+
 apic_status apic_plan_create(const apic_params* pr, apic_plan** out) {
     if (!pr || !out) return fail(APIC_EINVAL, "NULL params or out");
     *out = nullptr;
@@ -981,14 +989,15 @@ apic_status apic_plan_stage_ms(apic_plan* plan, double* ms, int n, int32_t* call
 
 apic_status apic_plan_counters(apic_plan* plan, int64_t* out, int n, int reset) {
     if (!plan || (!out && n > 0)) return fail(APIC_EINVAL, "NULL plan or output");
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[kCounters] = {};
     if (!plan->host_only) {
         APIC_TRY_CUDA(cudaDeviceSynchronize());
         APIC_TRY_CUDA(cudaMemcpy(c, plan->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
         if (reset) APIC_TRY_CUDA(cudaMemset(plan->d_counters, 0, sizeof(c)));
     }
-    const int64_t v[3] = {plan->launches, (int64_t)c[1], (int64_t)c[2]};
-    for (int i = 0; i < n && i < 3; ++i) out[i] = v[i];
+    const int used = std::min(plan->dev.n_used, kCountedImages);
+    for (int i = 0; i < n && i < 3 + used; ++i)
+        out[i] = i == 0 ? plan->launches : i < 3 ? (int64_t)c[i] : (int64_t)c[4 + (i - 3)];
     if (reset) plan->launches = 0;
     return APIC_OK;
 }

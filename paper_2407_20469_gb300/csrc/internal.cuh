@@ -10,6 +10,10 @@ namespace apic {
 
 constexpr int kThreads = 512;        // threads per block of the transform kernels
 constexpr int kChunk = 4096;         // complex elements per shared-memory chunk buffer
+// Work counters of a plan (unsigned long long): [1] CG iterations, [2] darkfield solves,
+// [4 + i] CG iterations of used darkfield image i (processing order), i < kCountedImages.
+constexpr int kCountedImages = 256;
+constexpr int kCounters = 4 + kCountedImages;
 
 // One darkfield image admitted by the geometry, in processing order.
 struct DevDF {
@@ -105,6 +109,8 @@ size_t kkr_smem_bytes(int BN);
 int configure_kkr(int BN, size_t smem);
 cudaError_t launch_kk_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I, float2* xdisc,
                           float2* scratch, const int32_t* status, cudaStream_t st);
+// Measured FMA throughput (flop/s) of the current device's CUDA cores, FP32 or FP64 (kernels_peak.cu).
+cudaError_t measure_fma_rate(int precision, double* flops_per_s);
 // Static scratch of the allocation-free entry point (kernels_noalloc.cu).
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(int device, float2** out);

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kThreads) k_darkfield(DevPlan P, int n_tiles, 
             if (threadIdx.x == 0 && counters) {
                 atomicAdd(counters + 1, (unsigned long long)it);
                 atomicAdd(counters + 2, 1ull);
+                if (di < kCountedImages) atomicAdd(counters + 4 + di, (unsigned long long)it);
             }
             // ---- O(K) = u(c) exp(-j phi(c)) on U
             for (int e = threadIdx.x; e < N; e += blockDim.x) {

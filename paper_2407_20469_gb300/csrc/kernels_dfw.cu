@@ -574,6 +574,7 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
             if (threadIdx.x == 0 && counters) {
                 atomicAdd(counters + 1, (unsigned long long)(r < 0 ? -1 - r : r));
                 atomicAdd(counters + 2, 1ull);
+                if (di < kCountedImages) atomicAdd(counters + 4 + di, (unsigned long long)(r < 0 ? -1 - r : r));
             }
         }
         if (threadIdx.x == 0 && notconv && status) atomicOr(status + tile, APIC_TILE_NOTCONV);

@@ -39,10 +39,31 @@ def test_image_sets_behind_the_images_option():
 
 
 def test_default_options_keep_the_timing_contract(monkeypatch):
+    """The default line is the largest single-GPU workload: 2048 tiles of 512 x 512
+    with 8 + 24 images; --workload cfg2 is 512 tiles of 256 x 256 with 8 + 16."""
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
-    assert (a.gpus, a.impl, a.workload, a.images, a.tiles, a.tile) == (1, "apic", "tiles", "8+16", 512, 256)
-    assert a.warmup >= 3 and a.steps >= 1
+    assert (a.gpus, a.impl, a.workload, a.images, a.tiles, a.tile) == (1, "apic", "cfg3", "8+24", 2048, 512)
+    assert a.zgrid == (32, 64) and a.warmup >= 3 and a.steps >= 1 and a.e2e_steps >= 10
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "cfg2"])
+    a = bench.parse()
+    assert (a.images, a.tiles, a.tile, a.zgrid) == ("8+16", 512, 256, (16, 32))
+
+
+def test_oracle_tile_pieces_reproduce_the_checker_and_its_sets():
+    """bench.OracleTile runs the checker's functions in the checker's order: on a small
+    tile its spectrum equals oracle reconstruct_tile's and its geometry-only set sizes
+    equal the sets the checker used; the per-tile estimate with every solve measured is
+    the plain sum."""
+    from oracle import apic as oapic
+    I, g, k, ill = bench.oracle_tile_sample(64, "8+16", 5)
+    ot = bench.OracleTile(I, g, k, ill.n_bf)
+    t_bf = ot.brightfield()
+    meas = [ot.darkfield_next() for _ in range(len(ot.order))]
+    ref = oapic.reconstruct_tile(I.astype(np.float64), g, k, ill.n_bf)
+    assert np.array_equal(ot.spec.values, ref.spectrum.values)
+    assert ot.sizes == [(len(s.U), len(s.Q)) if s.used else (0, 0) for s in ref.df_sets]
+    assert ot.tile_seconds(t_bf, meas) == pytest.approx(t_bf + sum(b + s for b, s, _ in meas))
 
 
 def test_reference_arm_prints_one_line_on_the_host():
