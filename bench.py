@@ -56,7 +56,7 @@ DEFAULT_DF_TOL = 3e-4          # the library's darkfield CG tolerance (apic_para
 DF_SOURCES = {256: ["kernels_dfr.cu", "regfft.cuh", "common.cuh", "internal.cuh"],
               512: ["kernels_dfw.cu", "regfft.cuh", "common.cuh", "internal.cuh"]}
 DF_KERNEL = {256: "k_darkfield_reg", 512: "k_darkfield_wide"}
-HOST_TILES_E2E = 512           # pinned host buffers of the end-to-end leg hold this many tiles at most
+HOST_E2E_RAM_FRAC = 0.45       # pinned host buffers of the end-to-end leg: at most this share of host RAM
 
 
 def parse():
@@ -567,15 +567,28 @@ def gpu_arm(args):
 
     # ---- end to end through host buffers: apic_reconstruct_host pipelines the pinned
     # host->device copies, the reconstruction and the device->host copies. The pinned
-    # buffers hold at most HOST_TILES_E2E tiles (a step of 2048 512-pixel tiles would pin
-    # 86 GB of host memory); a step is then several calls over consecutive tile ranges,
-    # each copying its inputs in and its fields out.
+    # buffers hold the whole step when that fits HOST_E2E_RAM_FRAC of the host's RAM
+    # (86 GB for 2048 512-pixel tiles); otherwise a step is several calls over
+    # consecutive tile ranges, each copying its inputs in and its fields out.
     e2e = None
     if args.e2e_steps > 0:
-        Th = min(T, HOST_TILES_E2E)
-        I_host = torch.empty((Th,) + tuple(I.shape[1:]), dtype=torch.float32, pin_memory=True)
+        per_tile_bytes = n_img * n * n * 4 + H * H * 8
+        try:
+            ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+        except (ValueError, OSError, AttributeError):
+            ram = 0
+        Th = max(1, min(T, int(HOST_E2E_RAM_FRAC * ram // per_tile_bytes))) if ram else min(T, 512)
+        while True:          # a pinned allocation the host refuses: halve the buffers
+            try:
+                I_host = torch.empty((Th,) + tuple(I.shape[1:]), dtype=torch.float32, pin_memory=True)
+                f_host = torch.empty((Th,) + tuple(field.shape[1:]), dtype=torch.float32, pin_memory=True)
+                break
+            except RuntimeError:
+                I_host = f_host = None
+                if Th == 1:
+                    raise
+                Th = max(1, Th // 2)
         I_host.copy_(I[:Th])
-        f_host = torch.empty((Th,) + tuple(field.shape[1:]), dtype=torch.float32, pin_memory=True)
         z_host = torch.empty((Th, 15), dtype=torch.float32, pin_memory=True)
         s_host = torch.empty((Th,), dtype=torch.int32, pin_memory=True)
         del I

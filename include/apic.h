@@ -51,7 +51,11 @@ typedef enum {
     APIC_ENOMEM = 2,      /* device or host allocation failed                    */
     APIC_ECUDA = 3,       /* a CUDA call or kernel launch failed                 */
     APIC_EGEOMETRY = 4,   /* illumination geometry unusable for this tile size  */
-    APIC_EINTERNAL = 5    /* library bug (an invariant did not hold)             */
+    APIC_EINTERNAL = 5,   /* library bug (an invariant did not hold)             */
+    APIC_ENOTCONV = 6     /* all outputs written, but a darkfield solve of some
+                             tile stopped above its tolerance (its status word
+                             has APIC_TILE_NOTCONV); returned by the synchronous
+                             host call apic_reconstruct_host only              */
 } apic_status;
 
 /* Per-tile status words written to d_tile_status (bit flags, 0 = clean). */
@@ -254,6 +258,9 @@ apic_status apic_plan_stage_ms(apic_plan* plan, double* h_ms, int n, int32_t* h_
  * serialise. Returns when all results are in host memory.
  *   h_intensity [n_tiles][n_bf + n_df][h][w] f32, h_field [n_tiles][u h][u w]
  *   complex64, h_zernike [n_tiles][15] f32, h_tile_status [n_tiles] or NULL.
+ * Returns APIC_ENOTCONV (outputs complete) when h_tile_status is given and some
+ * tile's word has APIC_TILE_NOTCONV: its field is the darkfield solve's last
+ * iterate, usable but above the CG tolerance.
  */
 apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_intensity, float* h_field,
                                   float* h_zernike, int32_t* h_tile_status);
@@ -359,8 +366,12 @@ apic_status apic_simulate(apic_plan* plan, int n_tiles, const float* d_object,
  * the register-FFT and the shared-memory Stockham variants of the
  * Kramers-Kronig and darkfield stages (best of two runs after a warm-up, CUDA
  * events) and keeps the faster variant of each for the plan's later calls.
+ * For 512-pixel tiles the register darkfield kernel is also timed with 1, 2
+ * and 4 blocks (a thread-block cluster) per tile, and the fastest kept.
  * h_ms [n_ms] (may be NULL): milliseconds of KK register, KK Stockham,
- * darkfield register, darkfield Stockham (-1 where a variant does not apply).
+ * darkfield register (the best cluster size), darkfield Stockham, and the
+ * 512-pixel register darkfield kernel with 1, 2, 4 blocks per tile (-1 where
+ * a variant does not apply); up to 7 values.
  * Synchronous; uses the plan's workspace, so it must not overlap other calls
  * on the plan.
  */
@@ -458,6 +469,20 @@ size_t apic_net_feature_count(void);
 apic_status apic_net_create(int max_batch, apic_net** out);
 /* Free the network (synchronises the device first). NULL is a no-op. */
 apic_status apic_net_destroy(apic_net* net);
+
+/*
+ * Load parameters from a BF16 checkpoint blob in host memory (checkpoint /
+ * resume of a trained network; the paper has no network). Layout: the 8 bytes
+ * "APICNB16", a little-endian uint32 L, L bytes of a UTF-8 JSON header holding
+ * at least "format": "apic-net-bf16" and "count": apic_net_param_count(), then
+ * count little-endian BF16 values (the upper 16 bits of IEEE float32) in the
+ * apic_net_set_params layout; nothing after them. The values are widened to the
+ * network's FP32 master copy (and its BF16 copy), and the AdamW moments zeroed,
+ * as apic_net_set_params does. net == NULL only validates the blob. Synchronous.
+ * Errors: APIC_EINVAL with a message (short or truncated blob, wrong magic,
+ * header, format, count or size), APIC_ECUDA.
+ */
+apic_status apic_net_load(apic_net* net, const void* h_blob, size_t bytes);
 
 /* Copy parameters from / to host memory (count must be apic_net_param_count());
  * set_params also clears the optimizer moments. Synchronous. */

@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libapic.so")
 
-APIC_OK, APIC_EINVAL, APIC_ENOMEM, APIC_ECUDA, APIC_EGEOMETRY, APIC_EINTERNAL = range(6)
+APIC_OK, APIC_EINVAL, APIC_ENOMEM, APIC_ECUDA, APIC_EGEOMETRY, APIC_EINTERNAL, APIC_ENOTCONV = range(7)
 APIC_TILE_OK, APIC_TILE_BACKGROUND, APIC_TILE_NOTCONV, APIC_TILE_BADINPUT = 0, 1, 2, 4
 APIC_TILE_LEARNED, APIC_TILE_WARM = 8, 16
 APIC_NET_WARM, APIC_NET_REPLACE = 1, 2
@@ -36,7 +36,7 @@ EXPORTS = [
     "apic_net_destroy", "apic_net_set_params", "apic_net_get_params", "apic_net_get_grads", "apic_net_forward",
     "apic_net_backward", "apic_net_adamw", "apic_net_activation", "apic_features", "apic_reconstruct_learned",
     "apic_slide_windows", "apic_cut_tiles", "apic_paste_fields", "apic_blend_fields", "apic_plan_autotune",
-    "apic_measure_fma_rate",
+    "apic_measure_fma_rate", "apic_net_load",
 ]
 
 
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "apic_last_error": (C.c_char_p, []),
         "apic_plan_create": (i32, [C.POINTER(apic_params), C.POINTER(vp)]),
         "apic_measure_fma_rate": (i32, [i32, C.POINTER(C.c_double)]),
+        "apic_net_load": (i32, [vp, C.c_char_p, sz]),
         "apic_plan_destroy": (i32, [vp]),
         "apic_plan_query": (i32, [vp, C.POINTER(apic_plan_info)]),
         "apic_plan_table": (i32, [vp, i32, C.POINTER(C.c_int32), sz]),
@@ -161,6 +162,12 @@ def _stream(stream) -> int | None:
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def validate_net_blob(blob: bytes):
+    """Checks a BF16 network checkpoint blob without a network (apic_net_load with NULL); raises
+    ApicError (APIC_EINVAL) with the library's reason if it is malformed."""
+    _check(load().apic_net_load(None, bytes(blob), len(blob)), "apic_net_load")
 
 
 def measure_fma_rate(precision: int = 32) -> float:
@@ -281,10 +288,15 @@ class Plan:
                                              _ptr(pupil), _ptr(tile_status), _stream(stream)),
                "apic_reconstruct_batch")
 
-    def reconstruct_host(self, n_tiles, intensity, field, zernike, tile_status=None):
-        """Host-memory reconstruction, pipelined in chunks (pass pinned CPU tensors for overlap)."""
-        _check(load().apic_reconstruct_host(self.handle, n_tiles, _ptr(intensity, True), _ptr(field, True),
-                                            _ptr(zernike, True), _ptr(tile_status, True)), "apic_reconstruct_host")
+    def reconstruct_host(self, n_tiles, intensity, field, zernike, tile_status=None) -> int:
+        """Host-memory reconstruction, pipelined in chunks (pass pinned CPU tensors for overlap).
+        Returns APIC_OK, or APIC_ENOTCONV when every output was written but some tile's darkfield
+        solve stopped above its tolerance (reported only with tile_status); raises otherwise."""
+        code = load().apic_reconstruct_host(self.handle, n_tiles, _ptr(intensity, True), _ptr(field, True),
+                                            _ptr(zernike, True), _ptr(tile_status, True))
+        if code != APIC_ENOTCONV:
+            _check(code, "apic_reconstruct_host")
+        return code
 
     def background(self, n_tiles, intensity, contrast2, tile_status, stream=None):
         _check(load().apic_background(self.handle, n_tiles, _ptr(intensity), _ptr(contrast2), _ptr(tile_status),
@@ -334,12 +346,14 @@ class Plan:
                                     _ptr(intensity), _stream(stream)), "apic_simulate")
 
     def autotune(self, n_tiles, intensity) -> dict:
-        """Times the register and Stockham variants of the transform stages on a sample; keeps the faster."""
-        ms = np.full(4, -1.0)
+        """Times the register and Stockham variants of the transform stages (and, for 512-pixel
+        tiles, the darkfield kernel with 1, 2, 4 blocks per tile) on a sample; keeps the fastest."""
+        ms = np.full(7, -1.0)
         _check(load().apic_plan_autotune(self.handle, n_tiles, _ptr(intensity),
-                                         ms.ctypes.data_as(C.POINTER(C.c_double)), 4), "apic_plan_autotune")
+                                         ms.ctypes.data_as(C.POINTER(C.c_double)), 7), "apic_plan_autotune")
         return {"kk_register": ms[0], "kk_stockham": ms[1], "darkfield_register": ms[2],
-                "darkfield_stockham": ms[3]}
+                "darkfield_stockham": ms[3], "darkfield_wide_1": ms[4], "darkfield_wide_2": ms[5],
+                "darkfield_wide_4": ms[6]}
 
     def cut_tiles(self, n_tiles, slide, slide_h, slide_w, windows, intensity, stream=None):
         _check(load().apic_cut_tiles(self.handle, n_tiles, _ptr(slide), slide_h, slide_w, _ptr(windows),
@@ -435,6 +449,10 @@ class Net:
             self.close()
         except Exception:
             pass
+
+    def load_blob(self, blob: bytes):
+        """Parameters from a BF16 checkpoint blob (apic_net_load; learn.bf16_blob writes one)."""
+        _check(load().apic_net_load(self.handle, bytes(blob), len(blob)), "apic_net_load")
 
     def set_params(self, flat: np.ndarray):
         v = np.ascontiguousarray(flat, dtype=np.float32)

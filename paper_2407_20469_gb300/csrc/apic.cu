@@ -94,7 +94,11 @@ struct apic_plan {
     bool host_only = false;
     bool use_reg = false;        // register-FFT darkfield kernel
     size_t smem_dfr = 0;
-    int grid_dfr = 0;
+    int grid_dfr = 0;            // tile slots of the register darkfield kernel (blocks, or clusters of
+                                 // df_cluster blocks for the wide kernel)
+    int df_cluster = 1;          // blocks per tile of the wide darkfield kernel
+    int dfw_slots[3] = {0, 0, 0};   // wide kernel: tile slots with 1, 2, 4 blocks per tile
+    int df_slots_alloc = 0;      // tile slots of each half of the darkfield scratch
     // host-buffer pipeline (apic_reconstruct_host), created on first use
     struct HostIO {
         bool ready = false;
@@ -393,12 +397,28 @@ apic_status configure(apic_plan* plan) {
     }
     if (D.mr > 0) {
         const bool wide = D.mr == 512;
-        const size_t smem = wide ? dfw_smem_bytes(D.max_N, D.band_q)
+        const size_t smem = wide ? dfw_smem_bytes(D.max_N, std::max({D.band_q, D.band_p, D.band_u}))
                                  : dfr_smem_bytes(D.mr / 16, D.h / 16, D.band_u, D.band_q, D.max_N);
         int dev_max = 0;
         cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device);
-        if (smem <= (size_t)dev_max) {
-            const int occ = wide ? configure_dfw(smem) : configure_dfr(D.mr / 16, D.h / 16, smem);
+        if (smem <= (size_t)dev_max && wide) {
+            // blocks per tile: 1 by default (measured fastest: with 2 or 4 blocks per tile
+            // fewer tiles are in flight, but the cluster barriers and the passes' rows and
+            // columns split over more half-warps cost more than L2 residency gains); the
+            // autotuner times 1, 2 and 4
+            for (int i = 0; i < 3; ++i) {
+                plan->dfw_slots[i] = configure_dfw(smem, 1 << i);
+                cudaGetLastError();
+            }
+            const int pick = plan->dfw_slots[0] > 0 ? 0 : 1;
+            if (plan->dfw_slots[pick] > 0) {
+                plan->dfr_ok = true;
+                plan->smem_dfr = smem;
+                plan->df_cluster = 1 << pick;
+                plan->grid_dfr = plan->dfw_slots[pick];
+            }
+        } else if (smem <= (size_t)dev_max) {
+            const int occ = configure_dfr(D.mr / 16, D.h / 16, smem);
             if (occ > 0) {
                 plan->dfr_ok = true;
                 plan->smem_dfr = smem;
@@ -438,9 +458,12 @@ apic_status alloc_workspace(apic_plan* p) {
     // darkfield scratch for two waves of blocks: a batch's last partial wave runs
     // beside the full waves (reconstruct) on blocks of its own
     if (p->use_reg) {
+        // the wide kernel's scratch covers the most tile slots of any cluster size
+        p->df_slots_alloc = D.mr == 512 ? std::max({p->dfw_slots[0], p->dfw_slots[1], p->dfw_slots[2]}) : p->grid_dfr;
         p->df_per_block = D.mr == 512 ? dfw_scratch_bytes(D) : dfr_scratch_bytes(D);
-        if ((s = dmalloc(p, &p->df_scratch, 2 * (size_t)p->grid_dfr * p->df_per_block)) != APIC_OK) return s;
+        if ((s = dmalloc(p, &p->df_scratch, 2 * (size_t)p->df_slots_alloc * p->df_per_block)) != APIC_OK) return s;
     } else {
+        p->df_slots_alloc = p->L.grid_df;
         p->df_per_block = df_scratch_bytes(D);
         if ((s = dmalloc(p, &p->df_scratch, 2 * (size_t)p->L.grid_df * p->df_per_block)) != APIC_OK) return s;
     }
@@ -468,16 +491,19 @@ cudaError_t launch_kk_any(apic_plan* p, int blocks, int n_tiles, const float* I,
 // Darkfield blocks of one full wave (the grid of the selected kernel).
 int df_wave(const apic_plan* p) { return std::max(1, p->use_reg ? p->grid_dfr : p->L.grid_df); }
 
+// SMs that `slots` darkfield tile slots occupy (the wide kernel: df_cluster blocks each)
+int df_sms(const apic_plan* p, int slots) { return slots * (p->use_reg && p->dev.mr == 512 ? p->df_cluster : 1); }
+
 // Darkfield stage on the tiles whose phase table starts at phi, on `grid` blocks
 // (<= 0: a full wave); `second` selects the second wave of scratch blocks (for a
 // launch that runs beside another one).
 cudaError_t launch_df_on(apic_plan* p, int n_tiles, const float* I, const float* phi, float2* spec, int32_t* status,
                          bool second, cudaStream_t st, int grid = 0) {
-    char* scratch = (char*)p->df_scratch + (second ? (size_t)df_wave(p) * p->df_per_block : 0);
+    char* scratch = (char*)p->df_scratch + (second ? (size_t)p->df_slots_alloc * p->df_per_block : 0);
     const int g = grid > 0 ? std::min(grid, df_wave(p)) : df_wave(p);
     if (p->use_reg && p->dev.mr == 512)
-        return launch_darkfield_wide(p->dev, g, p->smem_dfr, n_tiles, I, phi, spec, scratch, p->df_per_block,
-                                     p->df_iters, p->df_tol, status, p->d_counters, st);
+        return launch_darkfield_wide(p->dev, p->df_cluster, g, p->smem_dfr, n_tiles, I, phi, spec, scratch,
+                                     p->df_per_block, p->df_iters, p->df_tol, status, p->d_counters, st);
     if (p->use_reg)
         return launch_darkfield_reg(p->dev, g, p->smem_dfr, n_tiles, I, phi, spec, scratch, p->df_per_block,
                                     p->df_iters, p->df_tol, status, p->d_counters, st);
@@ -697,8 +723,8 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                 APIC_TRY_LAUNCH(launch_background(D, b - a, It + (size_t)a * in_tile, plan->c2 + a, stt + a, thresh2,
                                                   st, replace ? 1 : 0));
                 if (last && g == parts - 1) tm.mark(0, 1);
-                if ((s = learned_part(a, b - a, W - r)) != APIC_OK) return s;
-                if ((s = pre_df(a, b - a, g == parts - 1, W - r)) != APIC_OK) return s;
+                if ((s = learned_part(a, b - a, df_sms(plan, W - r))) != APIC_OK) return s;
+                if ((s = pre_df(a, b - a, g == parts - 1, df_sms(plan, W - r))) != APIC_OK) return s;
                 a = b;
             }
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
@@ -789,6 +815,7 @@ const char* apic_status_string(apic_status s) {
         case APIC_ECUDA: return "APIC_ECUDA: CUDA error";
         case APIC_EGEOMETRY: return "APIC_EGEOMETRY: unusable illumination geometry";
         case APIC_EINTERNAL: return "APIC_EINTERNAL: internal error";
+        case APIC_ENOTCONV: return "APIC_ENOTCONV: a darkfield solve stopped above its tolerance";
     }
     return "unknown apic_status";
 }
@@ -1219,6 +1246,21 @@ apic_status apic_features(apic_plan* plan, int n_tiles, const float* I, float* f
     return APIC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// APIC_ENOTCONV if a (host) status word of the batch has APIC_TILE_NOTCONV.
+apic_status host_status_word(const int32_t* h_status, int n_tiles) {
+    if (!h_status) return APIC_OK;
+    for (int t = 0; t < n_tiles; ++t)
+        if (h_status[t] & APIC_TILE_NOTCONV)
+            return fail(APIC_ENOTCONV, "tile " + std::to_string(t) + ": a darkfield solve stopped above its tolerance");
+    return APIC_OK;
+}
+}  // namespace
+
+extern "C" {
+
 apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I, float* h_field, float* h_zern,
                                   int32_t* h_status) {
     apic_status s = check_plan(plan, n_tiles);
@@ -1351,7 +1393,7 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
                                           cudaMemcpyDeviceToHost, io.s_out));
         APIC_TRY_CUDA(cudaStreamSynchronize(io.s_out));
         APIC_TRY_CUDA(cudaStreamSynchronize(io.s_comp));
-        return APIC_OK;
+        return host_status_word(h_status, n_tiles);
     }
     int k = 0;
     for (int t0 = 0, nt = 0; t0 < n_tiles; t0 += nt, ++k) {
@@ -1382,7 +1424,7 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
     }
     APIC_TRY_CUDA(cudaStreamSynchronize(io.s_out));
     APIC_TRY_CUDA(cudaStreamSynchronize(io.s_comp));
-    return APIC_OK;
+    return host_status_word(h_status, n_tiles);
 }
 
 apic_status apic_plan_autotune(apic_plan* plan, int n_tiles, const float* I, double* h_ms, int n_ms) {
@@ -1395,7 +1437,8 @@ apic_status apic_plan_autotune(apic_plan* plan, int n_tiles, const float* I, dou
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    double ms[4] = {-1.0, -1.0, -1.0, -1.0};   // KK register / Stockham, darkfield register / Stockham
+    // KK register / Stockham, darkfield register / Stockham, wide darkfield kernel with 1, 2, 4 blocks per tile
+    double ms[7] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0};
     const DevPlan& D = plan->dev;
     int32_t* stt = plan->status;
     auto timed = [&](auto&& launch, double& out) -> cudaError_t {
@@ -1432,41 +1475,69 @@ apic_status apic_plan_autotune(apic_plan* plan, int n_tiles, const float* I, dou
     // darkfield variants, each with its own scratch; the solve is idempotent on the
     // stitched spectrum, so repeated runs see the same system
     const bool had_reg = plan->use_reg;
+    const bool wide = D.mr == 512;
+    const int had_k = plan->df_cluster, had_grid = plan->grid_dfr;
     void* scratch[2] = {nullptr, nullptr};
-    size_t per_block[2] = {dfr_scratch_bytes(D), df_scratch_bytes(D)};
+    size_t per_block[2] = {wide ? dfw_scratch_bytes(D) : dfr_scratch_bytes(D), df_scratch_bytes(D)};
+    const int slots_alloc[2] = {
+        wide ? std::max({plan->dfw_slots[0], plan->dfw_slots[1], plan->dfw_slots[2]}) : plan->grid_dfr,
+        plan->L.grid_df};
     scratch[had_reg ? 0 : 1] = plan->df_scratch;
+    int best_k = had_k, best_grid = had_grid;
     for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
         if (v == 0 && !plan->dfr_ok) continue;
         if (!scratch[v]) {
-            const size_t bytes = 2 * (size_t)(v == 0 ? plan->grid_dfr : plan->L.grid_df) * per_block[v];
+            const size_t bytes = 2 * (size_t)slots_alloc[v] * per_block[v];
             if ((s = dmalloc(plan, &scratch[v], bytes)) != APIC_OK) break;
         }
         plan->use_reg = v == 0;
         plan->df_scratch = scratch[v];
         plan->df_per_block = per_block[v];
-        err = timed([&] { return launch_df(plan, n_tiles, I, plan->spec, stt, st); }, ms[2 + v]);
+        plan->df_slots_alloc = slots_alloc[v];
+        if (v == 0 && wide) {      // the wide kernel at each cluster size: blocks per tile 1, 2, 4
+            for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
+                if (plan->dfw_slots[i] <= 0) continue;
+                plan->df_cluster = 1 << i;
+                plan->grid_dfr = plan->dfw_slots[i];
+                err = timed([&] { return launch_df(plan, n_tiles, I, plan->spec, stt, st); }, ms[4 + i]);
+                if (err == cudaSuccess && (ms[2] < 0 || ms[4 + i] < ms[2])) {
+                    ms[2] = ms[4 + i];
+                    best_k = plan->df_cluster;
+                    best_grid = plan->grid_dfr;
+                }
+            }
+            plan->df_cluster = best_k;
+            plan->grid_dfr = best_grid;
+        } else {
+            err = timed([&] { return launch_df(plan, n_tiles, I, plan->spec, stt, st); }, ms[2 + v]);
+        }
     }
     if (s == APIC_OK && err == cudaSuccess) {
         const int pick = plan->dfr_ok && !(ms[3] >= 0 && ms[3] < ms[2]) ? 0 : 1;
         plan->use_reg = pick == 0;
         plan->df_scratch = scratch[pick];
         plan->df_per_block = per_block[pick];
+        plan->df_slots_alloc = slots_alloc[pick];
         void* loser = scratch[1 - pick];
         if (loser) {
             cudaFree(loser);
-            plan->allocs.erase(std::find(plan->allocs.begin(), plan->allocs.end(), loser));
+            auto it = std::find(plan->allocs.begin(), plan->allocs.end(), loser);
+            if (it != plan->allocs.end()) plan->allocs.erase(it);
         }
     } else {   // keep the plan's original darkfield selection
         plan->use_reg = had_reg;
         plan->df_scratch = scratch[had_reg ? 0 : 1];
         plan->df_per_block = per_block[had_reg ? 0 : 1];
+        plan->df_slots_alloc = slots_alloc[had_reg ? 0 : 1];
+        plan->df_cluster = had_k;
+        plan->grid_dfr = had_grid;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
     if (s != APIC_OK) return s;
     if (err != cudaSuccess) return cuda_fail(err, "apic_plan_autotune");
-    for (int i = 0; i < n_ms && i < 4; ++i) h_ms[i] = ms[i];
+    for (int i = 0; i < n_ms && i < 7; ++i) h_ms[i] = ms[i];
     return APIC_OK;
 }
 

@@ -142,10 +142,11 @@ cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_
                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
 
 // wide darkfield kernel of 512-pixel tiles (kernels_dfw.cu)
-size_t dfw_smem_bytes(int max_N, int band_q);
+size_t dfw_smem_bytes(int max_N, int band);   // band: max of the U, P and Q row bands
 size_t dfw_scratch_bytes(const DevPlan& P);
-int configure_dfw(size_t smem);
-cudaError_t launch_darkfield_wide(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
+// tile slots (clusters of K blocks, K in 1, 2, 4) that run at once; grid = tile slots
+int configure_dfw(size_t smem, int K);
+cudaError_t launch_darkfield_wide(const DevPlan& P, int K, int grid, size_t smem, int n_tiles, const float* I,
                                   const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
                                   float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
 

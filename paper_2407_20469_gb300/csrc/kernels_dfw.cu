@@ -17,9 +17,16 @@
 //    areas. Shared memory holds the half-warp transform areas and the CG vectors;
 //    the setup transforms (512-point areas, the column stage) alias both, since no
 //    CG vector is live while an image is being set up.
-// One block of 512 threads per tile (persistent); images of a tile in order.
+// A tile is solved by a cluster of K blocks of 512 threads (persistent over tiles;
+// images of a tile in order): every pass splits its rows or columns over the K x 32
+// half-warps of the cluster, each block owning a fixed share (and with it the CG
+// vector entries of its U rows); passes end at cluster barriers and inner products
+// are summed across the blocks through distributed shared memory, in rank order, so
+// every block takes the same steps. With K blocks per tile only 1/K as many tiles are
+// in flight, so their band grids stay in L2 instead of going to HBM. Data another
+// block wrote is read with L2-only loads (no stale L1 lines).
 // Transforms, vectors and per-thread / per-warp partial sums FP32; the sums across
-// warps and the CG step lengths FP64.
+// warps and blocks and the CG step lengths FP64.
 #include <math.h>
 
 #include <algorithm>
@@ -53,15 +60,79 @@ __device__ __forceinline__ int band_row_w(int i, int y0, int m) {
     return r;
 }
 
+// Half-warp of a cluster: t lane, hw index in the block, gh index in the cluster
+// (rank x 32 + hw), ghs half-warps in the cluster.
 struct HWw {
-    int t, hw;
+    int t, hw, gh, ghs;
     unsigned mask;
     float2* hs;
     __device__ HalfWarp h() const { return HalfWarp{t, mask, hs}; }
 };
 
+__device__ __forceinline__ unsigned cta_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Barrier of all threads of the K blocks of a tile (release / acquire at cluster
+// scope); a block barrier when K = 1.
+template <int K>
+__device__ __forceinline__ void tile_sync() {
+    if constexpr (K == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+}
+
+// Load of scratch data that another block of the cluster may have written: from L2.
+template <int K>
+__device__ __forceinline__ float2 ldx(const float2* p) {
+    if constexpr (K == 1)
+        return *p;
+    else
+        return __ldcg(p);
+}
+
+// Sum over the tile's K blocks of FP32 per-thread values: FP32 within warps, FP64
+// across the block's warps (warp 0) and across the blocks (each block's total stored
+// into slot `rank` of every block's area through distributed shared memory, then
+// summed in rank order, so all blocks hold the same value). red: 96 doubles;
+// `parity` alternates so that a slot is never rewritten while a block still reads it.
+template <int K>
+__device__ __forceinline__ double tile_sum(float v, double* red, int& parity) {
+    if constexpr (K == 1) {
+        return block_sum2f(v, red, parity);
+    } else {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+        double* r = red + parity * 32;
+        double* slots = red + 64 + parity * 16;
+        if (lane == 0) r[warp] = (double)v;
+        __syncthreads();
+        if (warp == 0) {
+            double t = lane < nw ? r[lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane < K) {          // lane q stores this block's total into block q's slot
+                const unsigned a = (unsigned)__cvta_generic_to_shared(slots + cta_rank());
+                unsigned ra;
+                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"((unsigned)lane));
+                asm volatile("st.shared::cluster.f64 [%0], %1;" :: "r"(ra), "d"(t) : "memory");
+            }
+        }
+        tile_sync<K>();
+        double total = 0.0;
+#pragma unroll
+        for (int q = 0; q < K; ++q) total += slots[q];
+        parity ^= 1;
+        return total;
+    }
+}
+
 // ---- per-point functors (as in the 256-pixel kernel)
-struct WValKnown {      // P(c) = O_known(K) exp(j phi(c))
+template <int K>
+struct WValKnown {      // P(c) = O_known(K) exp(j phi(c)) (the spectrum: written by any block of the tile)
     const float2* sp;
     const float* ph;
     const int* ap;
@@ -69,7 +140,7 @@ struct WValKnown {      // P(c) = O_known(K) exp(j phi(c))
     __device__ float2 operator()(int e) const {
         float sn, cs;
         sincosf(ph[pup[e]], &sn, &cs);
-        return cmul(sp[ap[e]], make_float2(cs, sn));
+        return cmul(ldx<K>(sp + ap[e]), make_float2(cs, sn));
     }
 };
 struct WValNextDir {    // d = s + beta d (stored back)
@@ -161,7 +232,7 @@ __device__ __noinline__ void wpass_rows_in(HWw w, const float2* tw, float2* G, i
                                            const int* px, Val val) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
-    for (int b = w.hw; b < nrows; b += kWHW) {
+    for (int b = w.gh; b < nrows; b += w.ghs) {
 #pragma unroll
         for (int j = 0; j < B; ++j) w.hs[w.t + 16 * j] = make_float2(0.f, 0.f);
         __syncwarp(w.mask);
@@ -184,17 +255,17 @@ __device__ __noinline__ void wpass_rows_in(HWw w, const float2* tw, float2* G, i
 
 // rows of a band of G: forward transform along x; returns the sum of out(e, value)
 // over this lane's points.
-template <int B, class Out>
+template <int B, int K, class Out>
 __device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const float2* G, int ld, int nrows,
                                              const int* rp, const int* px, Out out) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
     float acc = 0.f;
-    for (int b = w.hw; b < nrows; b += kWHW) {
+    for (int b = w.gh; b < nrows; b += w.ghs) {
         const float2* row = G + (size_t)b * ld;
         float2 v[B], o[S][16];
 #pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + w.t + 16 * j);
         fft_a<B, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -209,22 +280,27 @@ __device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const floa
     return acc;
 }
 
-// columns x < ncols of a grid whose columns have 16 B points: band rows of Gi (row
-// r of the band at grid row (yi0 + r) mod 16 B, ni rows, row stride ldi) are the
-// input, the rest zero; inverse along y, mid, and (Mid::kOut) forward along y with
-// band rows yo0.. (no) stored to Go (row stride ldo). Each half-warp reads and
-// writes its own columns, so Gi and Go may be the same grid. Ends with __syncthreads.
-template <int B, class Mid>
+// columns x < ncols of a grid whose columns have 16 B points: band rows of Gi (row r
+// of the band at grid row (yi0 + r) mod 16 B, ni rows, row stride ldi) are the input,
+// the rest zero; inverse along y, mid, and (Mid::kOut) forward along y with band rows
+// yo0.. (no) stored to Go (row stride ldo). Each half-warp reads and writes its own
+// columns, so Gi and Go may be the same grid. Ends with a tile barrier.
+// (Measured and left out: staging strips of 32 columns through shared memory for
+// 256-byte row accesses, and issuing the next column's loads before the current
+// transform; both slowed the kernel by ~10 %: the first adds block barriers between
+// half-warps that otherwise overlap one another's loads and transforms, the second
+// spills.)
+template <int B, int K, class Mid>
 __device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0,
                                         int ni, float2* Go, int ldo, int yo0, int no, Mid mid) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
-    for (int x = w.hw; x < ncols; x += kWHW) {
+    for (int x = w.gh; x < ncols; x += w.ghs) {
         float2 v[B], o[S][16];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             const int bb = band_row_w(w.t + 16 * j, yi0, m);
-            v[j] = bb < ni ? Gi[(size_t)bb * ldi + x] : make_float2(0.f, 0.f);
+            v[j] = bb < ni ? ldx<K>(Gi + (size_t)bb * ldi + x) : make_float2(0.f, 0.f);
         }
         fft_a<B, true>(v, o, h, tw);
         mid(o, x, w.t);
@@ -237,21 +313,21 @@ __device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, cons
             }
         }
     }
-    __syncthreads();
+    tile_sync<K>();
 }
 
 // rows of Q in place (row stride 16 B): forward along x, keep the Q lags, inverse
 // along x. qmask: per band row 16 words; the bit k1 of half (t + 16 s) & 1 of word
 // (t + 16 s) >> 1 says whether x index (t + 16 s) + B k1 is in Q. Ends with __syncthreads.
-template <int B>
+template <int B, int K>
 __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G, int nrows, const unsigned* qmask) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
-    for (int b = w.hw; b < nrows; b += kWHW) {
+    for (int b = w.gh; b < nrows; b += w.ghs) {
         float2* row = G + (size_t)b * m;
         float2 v[B], o[S][16];
 #pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + w.t + 16 * j);
         fft_a<B, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -265,7 +341,7 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
 #pragma unroll
         for (int k1 = 0; k1 < B; ++k1) row[w.t + 16 * k1] = v[k1];
     }
-    __syncthreads();
+    tile_sync<K>();
 }
 
 // columns of the real image (n = 512; with tr the transposed image; read once, with
@@ -274,12 +350,13 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
 // half-warps 0..31 transform them. The stage aliases the half-warp areas: each stage
 // is consumed (or written) only between barriers that separate it from the
 // transforms. Ends with __syncthreads.
+template <int K>
 __device__ __noinline__ void wpass_image_cols(HWw w, const float2* tw, float2* stage, const float* img, float2* GX,
                                               int qy0, int nQ, bool tr) {
     constexpr int BN = kWBN, n = 16 * BN, S = Slots<BN>::value;
     const HalfWarp h = w.h();
     float* stage_f = reinterpret_cast<float*>(stage);
-    for (int c0 = 0; c0 < n; c0 += 32) {
+    for (int c0 = 32 * (w.gh / kWHW); c0 < n; c0 += 32 * K) {     // this block's chunks of 32 columns
         if (tr) {   // column c of the solve frame is image row c
             for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
                 const int c = idx / n, y = idx - c * n;
@@ -314,20 +391,22 @@ __device__ __noinline__ void wpass_image_cols(HWw w, const float2* tw, float2* s
         }
         __syncthreads();
     }
+    tile_sync<K>();
 }
 
 // rows of GX (length n): forward along x, bq[e] = value / n^2 at the Q points. Ends
 // with __syncthreads.
+template <int K>
 __device__ __noinline__ void wpass_image_rows(HWw w, const float2* tw, const float2* GX, int nQ, const int* qrp,
                                               const int* Qx, float2* bq) {
     constexpr int BN = kWBN, n = 16 * BN, S = Slots<BN>::value;
     const HalfWarp h = w.h();
     const float inv_n2 = 1.f / (float)(n * n);
-    for (int b = w.hw; b < nQ; b += kWHW) {
+    for (int b = w.gh; b < nQ; b += w.ghs) {
         const float2* row = GX + (size_t)b * n;
         float2 v[BN], o[S][16];
 #pragma unroll
-        for (int j = 0; j < BN; ++j) v[j] = row[w.t + 16 * j];
+        for (int j = 0; j < BN; ++j) v[j] = ldx<K>(row + w.t + 16 * j);
         fft_a<BN, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -339,21 +418,22 @@ __device__ __noinline__ void wpass_image_rows(HWw w, const float2* tw, const flo
         for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16) bq[e] = cscale(w.hs[freq_index(Qx[e], n)], inv_n2);
         __syncwarp(w.mask);
     }
-    __syncthreads();
+    tile_sync<K>();
 }
 
 // rows of Q holding the column-transformed |p|^2 on the camera grid: forward along
 // x, b = bq - (P * P) / n^2 on Q (kept in bq). Ends with __syncthreads.
+template <int K>
 __device__ __noinline__ void wpass_rows_rhs(HWw w, const float2* tw, const float2* GQ, int nQ, const int* qrp,
                                             const int* Qx, float2* bq) {
     constexpr int B = kWBN, m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
     const float inv_m2 = 1.f / (float)(m * m);
-    for (int b = w.hw; b < nQ; b += kWHW) {
+    for (int b = w.gh; b < nQ; b += w.ghs) {
         const float2* row = GQ + (size_t)b * m;
         float2 v[B], o[S][16];
 #pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = row[w.t + 16 * j];
+        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + w.t + 16 * j);
         fft_a<B, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -366,7 +446,7 @@ __device__ __noinline__ void wpass_rows_rhs(HWw w, const float2* tw, const float
             bq[e] = csub(bq[e], cscale(w.hs[freq_index(Qx[e], m)], inv_m2));
         __syncwarp(w.mask);
     }
-    __syncthreads();
+    tile_sync<K>();
 }
 
 }  // namespace
@@ -378,28 +458,29 @@ __device__ __noinline__ void wpass_rows_rhs(HWw w, const float2* tw, const float
 //                     transforms (17 x 32 values each), or the 32-column stage
 //   [tw, tw_end)      step twiddles of the camera grid and of the image's row and
 //                     column grids
-//   [red, total)      64 doubles of reductions
+//   [red, total)      96 doubles of reductions (block partials, then the blocks' totals)
 struct DFWSmem {
     size_t vec, tw, red, total;
 };
 
 __host__ __device__ inline size_t walign16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-__host__ __device__ inline DFWSmem dfw_smem_layout(int max_N, int band_q) {
+// band: the most band rows a column pass stages (max of the U, P and Q bands)
+__host__ __device__ inline DFWSmem dfw_smem_layout(int max_N, int band) {
     DFWSmem L;
-    L.vec = walign16((size_t)kWHW * hw_single_size(kWMaxB) * sizeof(float2));
+    L.vec = walign16(std::max((size_t)kWHW * hw_single_size(kWMaxB), (size_t)band * kWStageLd) * sizeof(float2));
     const size_t cg_end = L.vec + walign16((size_t)4 * max_N * sizeof(float2));
     const size_t setup_hw = (size_t)kWHW * hw_single_size(kWBN) * sizeof(float2);
     const size_t stage_f = (size_t)16 * kWBN * kWStageLd * sizeof(float);
-    const size_t stage_c = (size_t)band_q * kWStageLd * sizeof(float2);
+    const size_t stage_c = (size_t)band * kWStageLd * sizeof(float2);
     const size_t setup = std::max(setup_hw, std::max(stage_f, stage_c));
     L.tw = walign16(std::max(cg_end, setup));
     L.red = walign16(L.tw + (size_t)2 * 16 * (kWBN + 2 * kWMaxB) * sizeof(float2));
-    L.total = walign16(L.red + 64 * sizeof(double));
+    L.total = walign16(L.red + 96 * sizeof(double));
     return L;
 }
 
-size_t dfw_smem_bytes(int max_N, int band_q) { return dfw_smem_layout(max_N, band_q).total; }
+size_t dfw_smem_bytes(int max_N, int band) { return dfw_smem_layout(max_N, band).total; }
 
 // Global scratch of one block: GQ (Q or P band rows on the camera grid), PF (the
 // column-major known field of the CG grid, or the image's Q rows), GU (U band rows
@@ -433,43 +514,44 @@ __device__ __forceinline__ const float2* wgrid_table(const DevPlan& P, int G) {
 }
 
 // Solve of one darkfield image once b = F(I) on Q is in bq, on a grid of 16 BX row
-// points x 16 BY column points; P * P on the camera grid. Returns the CG iterations
-// (negative: did not converge).
-template <int BX, int BY>
+// points x 16 BY column points; P * P on the camera grid; by the K blocks of the
+// cluster. Returns the CG iterations (negative: did not converge).
+template <int BX, int BY, int K>
 __device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, const DevDF& D, float2* sp,
-                                         const float* ph, int iters, float tol) {
+                                      const float* ph, int iters, float tol) {
     constexpr int n = 16 * kWBN, mx = 16 * BX;
     const HWw& w = c.w;
     const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
     const int uy0 = D.uy0, qy0 = D.qy0, py0 = D.py0;
-    const int N = D.N, nU = D.uy1 - uy0 + 1, nQ = D.qy1 - qy0 + 1, nP = D.py1 - py0 + 1;
+    const int nU = D.uy1 - uy0 + 1, nQ = D.qy1 - qy0 + 1, nP = D.py1 - py0 + 1;
     const int *urp = P.d_rowptr + D.urp, *qrp = P.d_rowptr + D.qrp, *prp = P.d_rowptr + D.prp;
     const unsigned* qmask = P.d_qmask + D.qmask_off;
-    const WValKnown pval{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off};
+    const WValKnown<K> pval{sp, ph, P.dP_ap + p_off, P.dP_pup + p_off};
     make_step_twiddles(c.tw_x, wgrid_table(P, BX), BX);
     make_step_twiddles(c.tw_y, wgrid_table(P, BY), BY);
     __syncthreads();
     // P * P on the camera grid: band rows of P along x, |p|^2 per column and back
     // along y on the Q band rows, then rows forward: b -= P * P on Q
     wpass_rows_in<kWBN>(c.ws, c.tw_n, c.GQ, n, nP, prp, P.dP_x + p_off, pval);
-    __syncthreads();
-    wpass_cols<kWBN>(c.ws, c.tw_n, n, c.GQ, n, py0, nP, c.GQ, n, qy0, nQ, WMidAbs2<kWBN>{});
-    wpass_rows_rhs(c.ws, c.tw_n, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
+    tile_sync<K>();
+    wpass_cols<kWBN, K>(c.ws, c.tw_n, n, c.GQ, n, py0, nP, c.GQ, n, qy0, nQ, WMidAbs2<kWBN>{});
+    wpass_rows_rhs<K>(c.ws, c.tw_n, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
     // band rows of the known field P (Eq. 11) along x on the row grid, then p s on
     // the column grid, column-major in PF (s = 1 / (mx my): the two unnormalised
     // transforms around each product)
     const float scale = 1.f / ((float)mx * (float)(16 * BY));
     wpass_rows_in<BX>(w, c.tw_x, c.GQ, mx, nP, prp, P.dP_x + p_off, pval);
-    __syncthreads();
-    wpass_cols<BY>(w, c.tw_y, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, WMidStoreField<BY>{c.PF, scale});
+    tile_sync<K>();
+    wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, WMidStoreField<BY>{c.PF, scale});
     // rows of b inverse along x on the row grid; s = d = C^H b
     wpass_rows_in<BX>(w, c.tw_x, c.GQ, mx, nQ, qrp, P.dQ_x + q_off, WValB{c.bq});
-    __syncthreads();
-    wpass_cols<BY>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
-    const float g0 = wpass_rows_out<BX>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutStart{c.sv, c.dv, c.xv});
+    tile_sync<K>();
+    wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
+    const float g0 =
+        wpass_rows_out<BX, K>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutStart{c.sv, c.dv, c.xv});
     int par = 0;
-    const double gamma0 = block_sum2f(g0, c.red, par);
-    // CGNR
+    const double gamma0 = tile_sum<K>(g0, c.red, par);
+    // CGNR; each block updates the vector entries of its own U rows
     double gamma = gamma0;
     bool conv = !(gamma0 > 1e-300);
     const double stop = (double)tol * (double)tol * gamma0;
@@ -477,17 +559,17 @@ __device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, cons
     float bf = 0.f;
     for (; it < iters && !conv; ++it) {
         wpass_rows_in<BX>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WValNextDir{c.sv, c.dv, bf});
-        __syncthreads();
-        wpass_cols<BY>(w, c.tw_y, mx, c.GU, mx, uy0, nU, c.GQ, mx, qy0, nQ, WMidTimesField<BY, true>{c.PF});
-        wpass_rows_mask<BX>(w, c.tw_x, c.GQ, nQ, qmask);
-        wpass_cols<BY>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
-        const float dw = wpass_rows_out<BX>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutDot{c.wv, c.dv});
-        const double delta = block_sum2f(dw, c.red, par);
+        tile_sync<K>();
+        wpass_cols<BY, K>(w, c.tw_y, mx, c.GU, mx, uy0, nU, c.GQ, mx, qy0, nQ, WMidTimesField<BY, true>{c.PF});
+        wpass_rows_mask<BX, K>(w, c.tw_x, c.GQ, nQ, qmask);
+        wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
+        const float dw = wpass_rows_out<BX, K>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutDot{c.wv, c.dv});
+        const double delta = tile_sum<K>(dw, c.red, par);
         if (!(delta > 0)) break;
         const double alpha = gamma / delta;
         const float af = (float)alpha;
         float g2 = 0.f;
-        for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        auto update = [&](int e) {
             const float2 d = c.dv[e];
             float2 x = c.xv[e];
             x.x += af * d.x;
@@ -496,24 +578,37 @@ __device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, cons
             const float2 sv = csub(c.sv[e], cscale(c.wv[e], af));
             c.sv[e] = sv;
             g2 += sv.x * sv.x + sv.y * sv.y;
+        };
+        if constexpr (K == 1) {           // all entries are this block's: every thread an even share
+            for (int e = threadIdx.x; e < D.N; e += blockDim.x) update(e);
+        } else {                          // the entries of this block's U rows
+            for (int b = w.gh; b < nU; b += w.ghs)
+                for (int e = urp[b] + w.t; e < urp[b + 1]; e += 16) update(e);
         }
-        const double gnew = block_sum2f(g2, c.red, par);
+        const double gnew = tile_sum<K>(g2, c.red, par);
         bf = (float)(gnew / gamma);
         gamma = gnew;
         conv = gnew <= stop;
     }
-    // corrected unknown spectrum into the tile's spectrum
+    // corrected unknown spectrum into the tile's spectrum (this block's U rows)
     const int* Upup = P.dU_pup + u_off;
     const int* Uap = P.dU_ap + u_off;
-    for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    auto put = [&](int e) {
         float sn, cs;
         sincosf(ph[Upup[e]], &sn, &cs);
         sp[Uap[e]] = cmul(c.xv[e], make_float2(cs, -sn));
+    };
+    if constexpr (K == 1) {
+        for (int e = threadIdx.x; e < D.N; e += blockDim.x) put(e);
+    } else {
+        for (int b = w.gh; b < nU; b += w.ghs)
+            for (int e = urp[b] + w.t; e < urp[b + 1]; e += 16) put(e);
     }
-    __syncthreads();
+    tile_sync<K>();
     return conv ? it : -1 - it;
 }
 
+template <int K>
 __global__ void __launch_bounds__(kWThreads, 1)
 k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
                  float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
@@ -521,7 +616,7 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
     constexpr int n = 16 * kWBN;
     extern __shared__ float4 smem4[];
     char* sbase = reinterpret_cast<char*>(smem4);
-    const DFWSmem SL = dfw_smem_layout(P.max_N, P.band_q);
+    const DFWSmem SL = dfw_smem_layout(P.max_N, max(P.band_q, max(P.band_p, P.band_u)));
     DFWCtx c;
     c.dv = reinterpret_cast<float2*>(sbase + SL.vec);
     c.sv = c.dv + P.max_N;
@@ -535,20 +630,24 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
     c.red = reinterpret_cast<double*>(sbase + SL.red);
     make_step_twiddles(tw_n, P.tw_n, kWBN);
 
+    const int rank = K > 1 ? (int)cta_rank() : 0;
+    const int slot = blockIdx.x / K, nslots = gridDim.x / K;      // tile slot = the cluster
     c.w.hw = c.ws.hw = threadIdx.x >> 4;
+    c.w.gh = c.ws.gh = rank * kWHW + c.w.hw;
+    c.w.ghs = c.ws.ghs = K * kWHW;
     c.w.t = c.ws.t = threadIdx.x & 15;
     c.w.mask = c.ws.mask = (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu;
     c.w.hs = reinterpret_cast<float2*>(sbase) + c.w.hw * hw_single_size(kWMaxB);
     c.ws.hs = reinterpret_cast<float2*>(sbase) + c.ws.hw * hw_single_size(kWBN);
 
-    char* base = scratch + (size_t)blockIdx.x * per_block;
+    char* base = scratch + (size_t)slot * per_block;
     c.GQ = reinterpret_cast<float2*>(base);
     c.PF = c.GQ + (size_t)max(P.band_q, P.band_p) * n;
     c.GU = c.PF + max((size_t)P.max_mxy, (size_t)P.band_q * n);
     c.bq = c.GU + (size_t)P.band_u * P.max_mx;
-    __syncthreads();
+    tile_sync<K>();
 
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int tile = slot; tile < n_tiles; tile += nslots) {
         if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
         const float* ph = phi + (size_t)tile * P.npup;
         float2* sp = spec + (size_t)tile * P.nap;
@@ -558,46 +657,98 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
             const int nQ = D.qy1 - D.qy0 + 1;
             const float* img = I + ((size_t)tile * P.n_img + D.led) * n * n;
             // b = F(I_j) on Q (F(I) rows staged in PF)
-            wpass_image_cols(c.ws, c.tw_n, c.stage, img, c.PF, D.qy0, nQ, D.tr != 0);
-            wpass_image_rows(c.ws, c.tw_n, c.PF, nQ, P.d_rowptr + D.qrp, P.dQ_x + D.q_off, c.bq);
+            wpass_image_cols<K>(c.ws, c.tw_n, c.stage, img, c.PF, D.qy0, nQ, D.tr != 0);
+            wpass_image_rows<K>(c.ws, c.tw_n, c.PF, nQ, P.d_rowptr + D.qrp, P.dQ_x + D.q_off, c.bq);
             int r;
             switch (16 * D.bx + D.by) {
-                case 16 * 18 + 12: r = dfw_solve<18, 12>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 18 + 16: r = dfw_solve<18, 16>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 18 + 18: r = dfw_solve<18, 18>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 20 + 12: r = dfw_solve<20, 12>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 20 + 16: r = dfw_solve<20, 16>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 20 + 18: r = dfw_solve<20, 18>(c, P, D, sp, ph, iters, tol); break;
-                default: r = dfw_solve<20, 20>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 18 + 12: r = dfw_solve<18, 12, K>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 18 + 16: r = dfw_solve<18, 16, K>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 18 + 18: r = dfw_solve<18, 18, K>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 20 + 12: r = dfw_solve<20, 12, K>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 20 + 16: r = dfw_solve<20, 16, K>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 20 + 18: r = dfw_solve<20, 18, K>(c, P, D, sp, ph, iters, tol); break;
+                default: r = dfw_solve<20, 20, K>(c, P, D, sp, ph, iters, tol); break;
             }
             if (r < 0) notconv = true;
-            if (threadIdx.x == 0 && counters) {
+            if (threadIdx.x == 0 && rank == 0 && counters) {
                 atomicAdd(counters + 1, (unsigned long long)(r < 0 ? -1 - r : r));
                 atomicAdd(counters + 2, 1ull);
                 if (di < kCountedImages) atomicAdd(counters + 4 + di, (unsigned long long)(r < 0 ? -1 - r : r));
             }
         }
-        if (threadIdx.x == 0 && notconv && status) atomicOr(status + tile, APIC_TILE_NOTCONV);
+        if (threadIdx.x == 0 && rank == 0 && notconv && status) atomicOr(status + tile, APIC_TILE_NOTCONV);
     }
 }
 
 }  // namespace
 
-int configure_dfw(size_t smem) {
-    if (raise_smem_limit((const void*)k_darkfield_wide, smem) != cudaSuccess) return 0;
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_darkfield_wide, kWThreads, smem) != cudaSuccess)
-        return 0;
-    return occ;
+using DFWKernel = void (*)(DevPlan, int, const float*, const float*, float2*, char*, size_t, int, float, int32_t*,
+                           unsigned long long*);
+
+static DFWKernel dfw_kernel(int K) {
+    switch (K) {
+        case 1: return k_darkfield_wide<1>;
+        case 2: return k_darkfield_wide<2>;
+        case 4: return k_darkfield_wide<4>;
+        default: return nullptr;
+    }
 }
 
-cudaError_t launch_darkfield_wide(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
+// Tile slots (clusters of K blocks) that run at once, 0 on error.
+int configure_dfw(size_t smem, int K) {
+    DFWKernel f = dfw_kernel(K);
+    if (!f || raise_smem_limit((const void*)f, smem) != cudaSuccess) return 0;
+    if (K == 1) {
+        int occ = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kWThreads, smem) != cudaSuccess) return 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        return occ * sms;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(K * 256, 1, 1);
+    cfg.blockDim = dim3(kWThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess) return 0;
+    return clusters;
+}
+
+// grid: tile slots (clusters); each gets K blocks.
+cudaError_t launch_darkfield_wide(const DevPlan& P, int K, int grid, size_t smem, int n_tiles, const float* I,
                                   const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
                                   float tol, int32_t* status, unsigned long long* counters, cudaStream_t st) {
-    if (P.h != 16 * kWBN || P.w != P.h) return cudaErrorInvalidValue;
-    k_darkfield_wide<<<min(grid, n_tiles), kWThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch,
-                                                                  per_block, iters, tol, status, counters);
-    return cudaGetLastError();
+    DFWKernel f = dfw_kernel(K);
+    if (!f || P.h != 16 * kWBN || P.w != P.h) return cudaErrorInvalidValue;
+    const int slots = min(grid, n_tiles);
+    if (slots < 1) return cudaErrorInvalidConfiguration;
+    if (K == 1) {
+        f<<<slots, kWThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol, status,
+                                          counters);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(K * slots, 1, 1);
+    cfg.blockDim = dim3(kWThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, f, P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol, status,
+                              counters);
 }
 
 }  // namespace apic

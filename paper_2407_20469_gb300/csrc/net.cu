@@ -795,6 +795,49 @@ apic_status apic_net_set_params(apic_net* n, const float* h, size_t count) {
     return APIC_OK;
 }
 
+// Value of key `key` in a flat JSON object: the string after it ("...") or the
+// digits of a number; empty when absent. Enough for the checkpoint header, whose
+// writer emits plain keys, strings and integers.
+static std::string json_value(const std::string& js, const std::string& key) {
+    const std::string k = "\"" + key + "\"";
+    size_t p = js.find(k);
+    if (p == std::string::npos) return "";
+    p += k.size();
+    while (p < js.size() && (js[p] == ' ' || js[p] == ':' || js[p] == '\t' || js[p] == '\n')) ++p;
+    if (p >= js.size()) return "";
+    if (js[p] == '"') {
+        const size_t e = js.find('"', p + 1);
+        return e == std::string::npos ? "" : js.substr(p + 1, e - p - 1);
+    }
+    size_t e = p;
+    while (e < js.size() && js[e] >= '0' && js[e] <= '9') ++e;
+    return js.substr(p, e - p);
+}
+
+apic_status apic_net_load(apic_net* n, const void* blob, size_t bytes) {
+    static const char kMagic[8] = {'A', 'P', 'I', 'C', 'N', 'B', '1', '6'};
+    if (!blob) return net_fail(APIC_EINVAL, "NULL blob");
+    const unsigned char* b = static_cast<const unsigned char*>(blob);
+    if (bytes < 12 || std::memcmp(b, kMagic, 8) != 0) return net_fail(APIC_EINVAL, "not an APICNB16 checkpoint");
+    const size_t L = (size_t)b[8] | ((size_t)b[9] << 8) | ((size_t)b[10] << 16) | ((size_t)b[11] << 24);
+    if (L > bytes - 12) return net_fail(APIC_EINVAL, "checkpoint header runs past the blob");
+    const std::string head(reinterpret_cast<const char*>(b + 12), L);
+    if (json_value(head, "format") != "apic-net-bf16") return net_fail(APIC_EINVAL, "checkpoint format is not apic-net-bf16");
+    const std::string cs = json_value(head, "count");
+    const Layout lay;
+    if (cs.empty() || cs.size() > 12 || std::stoull(cs) != (unsigned long long)lay.total)
+        return net_fail(APIC_EINVAL, "checkpoint count differs from apic_net_param_count()");
+    if (bytes != 12 + L + 2 * lay.total) return net_fail(APIC_EINVAL, "checkpoint size does not match its count");
+    if (!n) return APIC_OK;                          // validation only
+    std::vector<float> v(lay.total);
+    const unsigned char* q = b + 12 + L;
+    for (size_t i = 0; i < lay.total; ++i) {
+        const uint32_t bits = ((uint32_t)q[2 * i] | ((uint32_t)q[2 * i + 1] << 8)) << 16;
+        std::memcpy(&v[i], &bits, 4);
+    }
+    return apic_net_set_params(n, v.data(), v.size());
+}
+
 apic_status apic_net_get_params(const apic_net* n, float* h, size_t count) {
     if (!n || !h || count != n->L.total) return net_fail(APIC_EINVAL, "expected apic_net_param_count() floats");
     NET_TRY(cudaDeviceSynchronize());

@@ -148,6 +148,38 @@ def save_params(path: str, flat, meta: dict | None = None):
         fh.write(v.tobytes())
 
 
+BLOB_MAGIC = b"APICNB16"
+
+
+def bf16_bits(flat) -> np.ndarray:
+    """float32 -> BF16 bit patterns (uint16), rounded to nearest, ties to even."""
+    u = np.ascontiguousarray(flat, dtype="<f4").ravel().view("<u4").astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype("<u2")
+
+
+def bf16_values(flat) -> np.ndarray:
+    """The float32 values a BF16 checkpoint of `flat` holds (what apic_net_load restores)."""
+    return (bf16_bits(flat).astype("<u4") << 16).view("<f4").astype(np.float32)
+
+
+def bf16_blob(flat, meta: dict | None = None) -> bytes:
+    """A BF16 checkpoint of the network parameters in the layout apic_net_load reads: BLOB_MAGIC,
+    the little-endian uint32 length of a JSON header (format, count, layer shapes, caller's meta),
+    the header, then the values as little-endian BF16."""
+    import json
+    v = bf16_bits(flat)
+    head = json.dumps({"format": "apic-net-bf16", "count": int(v.size),
+                       "layers": [[n, list(sh)] for n, sh in apic.param_shapes()], "meta": meta or {}}).encode()
+    return BLOB_MAGIC + np.uint32(len(head)).astype("<u4").tobytes() + head + v.tobytes()
+
+
+def save_params_bf16(path: str, flat, meta: dict | None = None):
+    """bf16_blob to a file (half the size of save_params; values rounded to BF16)."""
+    with open(path, "wb") as fh:
+        fh.write(bf16_blob(flat, meta))
+
+
 def load_params(path: str):
     """(flat float32 parameters, meta) from save_params; ValueError if the file is not such a file,
     is truncated, or holds another layout than this library's network."""

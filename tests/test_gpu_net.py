@@ -161,3 +161,29 @@ def test_network_rejects_bad_arguments(lib):
     fresh = apic.Net(1)
     with pytest.raises(apic.ApicError):
         fresh.backward(torch.zeros((1, 15), device="cuda"))
+
+
+def test_checkpoint_blob_round_trip_through_the_c_abi(lib):
+    """A BF16 checkpoint written by learn.bf16_blob and read by apic_net_load gives the
+    network exactly the BF16-rounded parameters, and the same forward pass as setting
+    those values directly."""
+    from paper_2407_20469_gb300 import learn
+    rng = np.random.default_rng(17)
+    p = apic.pack_params(cnn.init_params(rng)) + rng.standard_normal(459244).astype(np.float32) * 1e-3
+    a, b = apic.Net(4), apic.Net(4)
+    a.load_blob(learn.bf16_blob(p))
+    got = a.get_params()
+    assert np.array_equal(got, learn.bf16_values(p))
+    b.set_params(learn.bf16_values(p))
+    feat = torch.randn((4, 64, 64, 8), device="cuda")
+    uv = torch.rand((4, 2), device="cuda") * 2 - 1
+    oa = torch.zeros((4, 15), device="cuda")
+    ob = torch.ones((4, 15), device="cuda")
+    a.forward(4, feat, uv, oa)
+    b.forward(4, feat, uv, ob)
+    torch.cuda.synchronize()
+    assert torch.equal(oa, ob)
+    with pytest.raises(apic.ApicError):
+        a.load_blob(learn.bf16_blob(p)[:-2])
+    a.close()
+    b.close()

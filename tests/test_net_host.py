@@ -50,3 +50,37 @@ def test_parameter_file_round_trip_and_refusals(tmp_path):
     open(path, "wb").write(raw.replace(b'"count": 459244', b'"count": 459243'))
     with pytest.raises(ValueError, match="layer shapes"):
         learn.load_params(path)
+
+
+def test_bf16_rounding_is_nearest_even():
+    from paper_2407_20469_gb300 import learn
+    f = np.array([1.0, 1.00390625, 1.01171875, -2.5, 3.0e-39, np.float32(np.inf)], dtype=np.float32)
+    # 1.00390625 = 0x3F808000 is a tie -> even 0x3F80; 1.01171875 = 0x3F818000 -> 0x3F82
+    assert list(learn.bf16_bits(f)) == [0x3F80, 0x3F80, 0x3F82, 0xC020, 0x0021, 0x7F80]
+    v = learn.bf16_values(f)
+    assert v[0] == 1.0 and v[2] == np.float32(1.015625) and v[3] == -2.5
+
+
+def test_checkpoint_blob_validation():
+    """apic_net_load's checks, run without a network (NULL): a well-formed BF16 blob is
+    accepted; truncated, extended, mislabelled or miscounted blobs are refused."""
+    from paper_2407_20469_gb300 import learn
+    p = apic.pack_params(cnn.init_params(np.random.default_rng(3)))
+    blob = learn.bf16_blob(p, {"epochs": 4})
+    apic.validate_net_blob(blob)
+    assert len(blob) == 12 + int.from_bytes(blob[8:12], "little") + 2 * p.size
+    L = int.from_bytes(blob[8:12], "little")
+    head = blob[12:12 + L]
+    bad = {
+        "truncated": blob[:-2],
+        "trailing bytes": blob + b"\0\0",
+        "magic": b"APICNB17" + blob[8:],
+        "header length": blob[:8] + (len(blob)).to_bytes(4, "little") + blob[12:],
+        "format": blob[:12] + head.replace(b"apic-net-bf16", b"apic-net-fp16") + blob[12 + L:],
+        "count": blob[:12] + head.replace(str(p.size).encode(), str(p.size - 1).encode()) + blob[12 + L:],
+        "short": blob[:11],
+    }
+    for why, b in bad.items():
+        with pytest.raises(apic.ApicError) as e:
+            apic.validate_net_blob(b)
+        assert e.value.code == apic.APIC_EINVAL, why
