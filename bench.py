@@ -75,15 +75,19 @@ def parse():
     ap.add_argument("--images", choices=["8+16", "8+24", "12+22"], default=None,
                     help="illumination set (8+24: rings at NA 0.29 / 0.34 / 0.40; 12+22: the paper's set-up size, "
                          "darkfield rings at NA 0.31 / 0.375 / 0.44)")
-    ap.add_argument("--workload", choices=["cfg3", "cfg2", "rgb", "blend"], default="cfg3",
+    ap.add_argument("--workload", choices=["cfg3", "cfg2", "rgb", "blend", "learned", "slide"], default="cfg3",
                     help="cfg3: 2048 tiles of 512 x 512 with 8 + 24 images (default line); cfg2: 512 tiles of "
                          "256 x 256 with 8 + 16 images; rgb: the cfg2 batch at three wavelengths, one plan each; "
-                         "blend: overlap blending of a 16 x 32 window grid with 6 %% overlap")
+                         "blend: overlap blending of a 16 x 32 window grid with 6 %% overlap; learned: the network "
+                         "trained on 20,000 tiles and evaluated on 4096 (30 %% near-blank); slide: a strip of the "
+                         "whole-slide stream (512-pixel windows, 40 %% background)")
+    ap.add_argument("--slide-rows", type=int, default=32)
+    ap.add_argument("--slide-cols", type=int, default=64)
     ap.add_argument("--seed", type=int, default=2407)
     ap.add_argument("--df-tol", type=float, default=0.0, help="CGLS tolerance (0: library default)")
     ap.add_argument("--df-iters", type=int, default=0, help="CGLS iteration cap (0: library default)")
     a = ap.parse_args()
-    tile, tiles, images, grid = WORKLOADS["cfg2" if a.workload in ("cfg2", "rgb", "blend") else "cfg3"]
+    tile, tiles, images, grid = WORKLOADS["cfg2" if a.workload in ("cfg2", "rgb", "blend", "learned") else "cfg3"]
     a.tile = a.tile or tile
     a.tiles = a.tiles or tiles
     a.images = a.images or images
@@ -861,6 +865,154 @@ def blend_arm(args):
     plan.close()
 
 
+def learned_arm(args):
+    """The learned-aberration configuration: the network trained on 20,000 simulated tiles of
+    256 x 256 (30 % near-blank), then 4096 fresh tiles (30 % near-blank) reconstructed with the
+    closed-form aberration solve, with the network's warm start, and with warm start plus
+    replacement on low-contrast tiles; the pupil error of each against the true coefficients,
+    per class, and the output rate of each."""
+    import torch
+    from paper_2407_20469_gb300 import apic, build, learn, synth
+    build.build()
+    device = torch.device("cuda", torch.cuda.current_device())
+    n, n_train, n_eval, blank_frac = 256, 20000, 4096, 0.3
+    ill = synth.illumination()
+    table = learn.field_table(args.seed)
+    bf = apic.Plan(n, ill.kx[:ill.n_bf], ill.ky[:ill.n_bf], ill.n_bf, max_tiles=256)
+    t0 = time.perf_counter()
+    feat, uv, zt, _ = learn.dataset(bf, n_train, args.seed, table, blank_frac=blank_frac)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = apic.Net(256)
+    net.set_params(learn.init_params(args.seed))
+    hist = learn.train(net, feat, uv, zt, epochs=8, batch=64, lr=3e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del feat, uv, zt
+    bf.close()
+    plan = apic.Plan.from_illumination(n, ill, max_tiles=n_eval, bg_contrast=0.02)
+    H = plan.info.out_h
+    uv_e, z_true, blank = learn.draw_tiles(n_eval, args.seed + 1, table, blank_frac)
+    I = learn.simulate(plan, z_true, blank, args.seed + 1)
+    uv_d = torch.as_tensor(uv_e, device=device)
+    field = torch.empty((n_eval, H, 2 * H), dtype=torch.float32, device=device)
+    zern = torch.empty((n_eval, 15), dtype=torch.float32, device=device)
+    status = torch.empty((n_eval,), dtype=torch.int32, device=device)
+    modes = {"closed_form": None, "warm": apic.APIC_NET_WARM,
+             "warm_and_replace": apic.APIC_NET_WARM | apic.APIC_NET_REPLACE}
+    out, clk = {}, None
+    for name, mode in modes.items():
+        if mode is None:
+            step = lambda: plan.reconstruct_batch(n_eval, I, field, zern, None, status)
+        else:
+            step = lambda m=mode: plan.reconstruct_learned(net, m, n_eval, I, uv_d, field, zern, None, status)
+        for _ in range(args.warmup):
+            step()
+        ms, clk = timed(step, args.steps, device)
+        z = zern.cpu().numpy().astype(np.float64)
+        st = status.cpu().numpy()
+        d = z[:, 3:] - z_true[:, 3:].astype(np.float64)
+        err = np.sqrt((d * d).sum(axis=1))
+        out[name] = {"Mpx_s": n_eval * H * H * args.steps / (ms / 1e3) / 1e6, "ms_per_step": ms / args.steps,
+                     "pupil_rms_median_rad": {"background": float(np.median(err[blank])),
+                                              "sample": float(np.median(err[~blank]))},
+                     "pupil_rms_p90_rad": {"background": float(np.percentile(err[blank], 90)),
+                                           "sample": float(np.percentile(err[~blank], 90))},
+                     "tiles_learned": int(np.count_nonzero(st & apic.APIC_TILE_LEARNED)),
+                     "tiles_warm_kept": int(np.count_nonzero(st & apic.APIC_TILE_WARM))}
+    best = out["warm_and_replace"]
+    line = {
+        "metric": "APIC output Mpx/s with the learned aberration network (warm start + replacement on low-contrast "
+                  "tiles); pupil error vs the true coefficients per class",
+        "value": best["Mpx_s"], "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": best["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (network bf16, FP32 accumulate)", "data": "synthetic",
+        "config": {"workload": f"network trained on {n_train} simulated tiles of {n}x{n} ({int(100 * blank_frac)} % "
+                               f"near-blank, contrast < 2 %), evaluated on {n_eval} fresh tiles of {n}x{n} "
+                               f"(8 + 16 images, {int(blank.sum())} near-blank); field-dependent quadratic Zernike "
+                               f"table plus per-tile defocus jitter",
+                   "train": {"tiles": n_train, "epochs": 8, "batch": 64, "dataset_s": t1 - t0, "train_s": t2 - t1,
+                             "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]},
+                   "modes": out, "l2": "inputs_larger_than_l2"},
+        "roofline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    plan.close()
+
+
+def slide_arm(args):
+    """Whole-slide stream: a contiguous strip of a 76.2 x 25.4 mm slide at 10x / 0.25 NA
+    (0.345 um pixels: the slide is 220,870 x 73,623 low-res pixels, about 20,000 windows of 512),
+    cut into 512-pixel windows with 6 % overlap, 40 % of them background (blob-shaped tissue
+    mask over the window grid), 8 + 24 images; one step = cut, reconstruct (background windows
+    skipped by the contrast test) and paste the whole strip."""
+    import torch
+    from paper_2407_20469_gb300 import apic, build, learn, slide, synth
+    build.build()
+    device = torch.device("cuda", torch.cuda.current_device())
+    n, rows, cols = 512, args.slide_rows, args.slide_cols
+    stride = n - int(round(0.06 * n))
+    Hs, Ws = (rows - 1) * stride + n, (cols - 1) * stride + n
+    ill = illumination_for("8+24")
+    batch = 1024
+    plan = apic.Plan.from_illumination(n, ill, max_tiles=batch, bg_contrast=0.02, flags=apic.APIC_SKIP_BACKGROUND)
+    info = plan.info
+    H = info.out_h
+    n_img = info.n_bf + info.n_df
+    win = apic.slide_windows(Hs, Ws, n, stride)
+    assert len(win) == rows * cols
+    # tissue mask over the window grid: a smooth random field, its lowest 40 % background
+    rng = np.random.default_rng(args.seed)
+    f = np.fft.fftfreq(rows)[:, None] ** 2 + np.fft.fftfreq(cols)[None, :] ** 2
+    fld = np.real(np.fft.ifft2(np.fft.fft2(rng.standard_normal((rows, cols))) * np.exp(-f * 60.0)))
+    blank = (fld <= np.quantile(fld, 0.4)).ravel()
+    table = learn.field_table(args.seed)
+    uv = slide.window_positions(win, Hs, Ws, n)
+    zern = learn.coefficients(table, uv)
+    I_slide = torch.zeros((n_img, Hs, Ws), dtype=torch.float32, device=device)
+    for t0 in range(0, len(win), 152):
+        t1 = min(len(win), t0 + 152)
+        I = learn.simulate(plan, zern, blank, args.seed, start=t0, count=t1 - t0)
+        for k in range(t1 - t0):
+            y0, x0 = int(win[t0 + k, 0]), int(win[t0 + k, 1])
+            I_slide[:, y0:y0 + n, x0:x0 + n] = I[k]
+        del I
+    torch.cuda.synchronize()
+    step = lambda: slide.reconstruct_slide(plan, I_slide, Hs, Ws, stride, batch=batch)
+    for _ in range(args.warmup):
+        res = step()
+    plan.counters(reset=True)
+    ms, clk = timed(step, args.steps, device)
+    cnt = plan.counters(reset=True)
+    out_f, z, st, _ = step()
+    st = st.cpu().numpy()
+    skipped = int(np.count_nonzero(st & apic.APIC_TILE_BACKGROUND))
+    sec = ms / args.steps / 1e3
+    slide_px = 4.0 * Hs * Ws
+    line = {
+        "metric": "whole-slide APIC output Mpx/s (slide area, background windows skipped)",
+        "value": slide_px / sec / 1e6, "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"strip of {rows} x {cols} windows of {n}x{n} (stride {stride}, 6 % overlap; "
+                               f"{Hs} x {Ws} low-res px = {Hs * 0.345e-3:.2f} x {Ws * 0.345e-3:.2f} mm of the "
+                               f"76.2 x 25.4 mm slide, {100.0 * rows * cols / 20000:.0f} % of its ~20,000 windows), "
+                               f"8 + 24 images, {int(blank.sum())} background windows ({100 * blank.mean():.0f} %), "
+                               f"paste of each window's owned part",
+                   "windows": rows * cols, "windows_per_s": rows * cols / sec,
+                   "reconstructed_windows": rows * cols - skipped, "skipped_background": skipped,
+                   "reconstructed_tiles_per_s": (rows * cols - skipped) / sec,
+                   "reconstructed_output_Mpx_s": (rows * cols - skipped) * H * H / sec / 1e6,
+                   "batch": batch, "l2": f"inputs_larger_than_l2 ({n_img * Hs * Ws * 4 / 1e9:.1f} GB slide stack)",
+                   "output_finite": bool(torch.isfinite(out_f).all().item()),
+                   "learned_warm_start": "not used: the network's features take tiles of up to 256 pixels"},
+        "roofline": None, "e2e": None, "gpu_launches": cnt["launches"] // max(1, args.steps), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -869,6 +1021,10 @@ def main():
         rgb_arm(args)
     elif args.workload == "blend":
         blend_arm(args)
+    elif args.workload == "learned":
+        learned_arm(args)
+    elif args.workload == "slide":
+        slide_arm(args)
     else:
         gpu_arm(args)
 

@@ -124,6 +124,8 @@ struct apic_plan {
     float* feat = nullptr;                       // learned path: features, network coefficients
     float* c_net = nullptr;
     unsigned long long* d_counters = nullptr;   // kCounters: [1] CG iterations, [2] solves, [4 + i] per image
+    int* d_work = nullptr;                       // tile counters of the darkfield launches: [0] caller's stream,
+                                                 // [1] the second stream
     long long launches = 0;                      // kernel launches issued
     // stage timing: ring of kTimingSlots calls x kStages x {start, stop}
     bool timing = false;
@@ -451,6 +453,7 @@ apic_status alloc_workspace(apic_plan* p) {
     if ((s = dmalloc(p, (void**)&p->c2, T * sizeof(float))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->d_counters, kCounters * sizeof(unsigned long long))) != APIC_OK) return s;
     APIC_TRY_CUDA(cudaMemset(p->d_counters, 0, kCounters * sizeof(unsigned long long)));
+    if ((s = dmalloc(p, (void**)&p->d_work, 2 * sizeof(int))) != APIC_OK) return s;
     const size_t kk_blocks = (size_t)std::max(p->L.grid_kk, p->grid_kkr);
     if ((s = dmalloc(p, (void**)&p->kk_scratch, kk_blocks * D.h * D.h * sizeof(float2))) != APIC_OK) return s;
     if ((s = dmalloc(p, (void**)&p->beta_scratch, (size_t)p->L.grid_ab * D.nrows * sizeof(float))) != APIC_OK)
@@ -503,10 +506,11 @@ cudaError_t launch_df_on(apic_plan* p, int n_tiles, const float* I, const float*
     const int g = grid > 0 ? std::min(grid, df_wave(p)) : df_wave(p);
     if (p->use_reg && p->dev.mr == 512)
         return launch_darkfield_wide(p->dev, p->df_cluster, g, p->smem_dfr, n_tiles, I, phi, spec, scratch,
-                                     p->df_per_block, p->df_iters, p->df_tol, status, p->d_counters, st);
+                                     p->df_per_block, p->df_iters, p->df_tol, status, p->d_counters,
+                                     p->d_work + (second ? 1 : 0), st);
     if (p->use_reg)
         return launch_darkfield_reg(p->dev, g, p->smem_dfr, n_tiles, I, phi, spec, scratch, p->df_per_block,
-                                    p->df_iters, p->df_tol, status, p->d_counters, st);
+                                    p->df_iters, p->df_tol, status, p->d_counters, p->d_work + (second ? 1 : 0), st);
     Launch L = p->L;
     L.grid_df = g;
     return launch_darkfield(p->dev, L, n_tiles, I, phi, spec, scratch, p->df_per_block, p->df_iters, p->df_tol,

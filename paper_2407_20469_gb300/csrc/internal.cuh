@@ -137,9 +137,12 @@ size_t df_scratch_bytes(const DevPlan& P);
 size_t dfr_smem_bytes(int B, int BN, int band_u, int band_q, int max_N);
 size_t dfr_scratch_bytes(const DevPlan& P);
 int configure_dfr(int B, int BN, size_t smem);
+// work: a device int the launcher zeroes on `st`; blocks take tiles from it one at a time
+// (NULL: tiles by stride)
 cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
                                  const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
-                                 float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
+                                 float tol, int32_t* status, unsigned long long* counters, int* work,
+                                 cudaStream_t st);
 
 // wide darkfield kernel of 512-pixel tiles (kernels_dfw.cu)
 size_t dfw_smem_bytes(int max_N, int band);   // band: max of the U, P and Q row bands
@@ -148,7 +151,8 @@ size_t dfw_scratch_bytes(const DevPlan& P);
 int configure_dfw(size_t smem, int K);
 cudaError_t launch_darkfield_wide(const DevPlan& P, int K, int grid, size_t smem, int n_tiles, const float* I,
                                   const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
-                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st);
+                                  float tol, int32_t* status, unsigned long long* counters, int* work,
+                                  cudaStream_t st);
 
 // Network features (net.cu): feat [n_tiles][64][64][8] from the first 8 images
 // of each stack; `scratch` holds h * 64 complex values per block of `grid`.

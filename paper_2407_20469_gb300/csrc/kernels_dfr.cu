@@ -771,7 +771,7 @@ template <int B, int BN>
 __global__ void __launch_bounds__(kDFThreads, 1)
 k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
                 float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
-                int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
+                int32_t* __restrict__ status, unsigned long long* __restrict__ counters, int* __restrict__ work) {
     constexpr int m = 16 * B, n = 16 * BN;
     constexpr int HWM = hw_area_m(B), HWN = HWSize<BN>::value;
     extern __shared__ float4 smem4[];
@@ -829,7 +829,17 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
     c.PF = c.GQ + (size_t)(P.band_q > P.band_p ? P.band_q : P.band_p) * m;   // column-major p, or F(I) rows
     c.bq = c.PF + (size_t)max(m * m, P.band_q * n);
 
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // tiles taken one at a time from the launch's counter (a block that meets skipped
+    // background tiles goes on to the next, so uneven batches balance), or by stride
+    __shared__ int s_next;
+    auto take = [&](int prev) -> int {
+        if (!work) return prev < 0 ? (int)blockIdx.x : prev + (int)gridDim.x;
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = atomicAdd(work, 1);
+        __syncthreads();
+        return s_next;
+    };
+    for (int tile = take(-1); tile < n_tiles; tile = take(tile)) {
         if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
         const float* ph = phi + (size_t)tile * P.npup;
         float2* sp = spec + (size_t)tile * P.nap;
@@ -876,7 +886,7 @@ k_darkfield_reg(DevPlan P, int n_tiles, const float* __restrict__ I, const float
 }
 
 using DFRKernel = void (*)(DevPlan, int, const float*, const float*, float2*, char*, size_t, int, float, int32_t*,
-                           unsigned long long*);
+                           unsigned long long*, int*);
 
 DFRKernel dfr_kernel(int B, int BN) {
     if (B == 4 && BN == 4) return k_darkfield_reg<4, 4>;
@@ -899,11 +909,15 @@ int configure_dfr(int B, int BN, size_t smem) {
 
 cudaError_t launch_darkfield_reg(const DevPlan& P, int grid, size_t smem, int n_tiles, const float* I,
                                  const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
-                                 float tol, int32_t* status, unsigned long long* counters, cudaStream_t st) {
+                                 float tol, int32_t* status, unsigned long long* counters, int* work, cudaStream_t st) {
     DFRKernel f = dfr_kernel(P.mr / 16, P.h / 16);
     if (!f) return cudaErrorInvalidValue;
+    if (work) {
+        const cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
     f<<<min(grid, n_tiles), kDFThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol,
-                                                  status, counters);
+                                                  status, counters, work);
     return cudaGetLastError();
 }
 

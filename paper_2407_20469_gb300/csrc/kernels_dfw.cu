@@ -612,7 +612,7 @@ template <int K>
 __global__ void __launch_bounds__(kWThreads, 1)
 k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const float* __restrict__ phi,
                  float2* __restrict__ spec, char* __restrict__ scratch, size_t per_block, int iters, float tol,
-                 int32_t* __restrict__ status, unsigned long long* __restrict__ counters) {
+                 int32_t* __restrict__ status, unsigned long long* __restrict__ counters, int* __restrict__ work) {
     constexpr int n = 16 * kWBN;
     extern __shared__ float4 smem4[];
     char* sbase = reinterpret_cast<char*>(smem4);
@@ -647,7 +647,18 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
     c.bq = c.GU + (size_t)P.band_u * P.max_mx;
     tile_sync<K>();
 
-    for (int tile = slot; tile < n_tiles; tile += nslots) {
+    // one block per tile: tiles taken one at a time from the launch's counter (a block that
+    // meets skipped background tiles goes on to the next, so uneven batches balance);
+    // clusters (and launches without a counter): by stride
+    __shared__ int s_next;
+    auto take = [&](int prev) -> int {
+        if (K > 1 || !work) return prev < 0 ? slot : prev + nslots;
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = atomicAdd(work, 1);
+        __syncthreads();
+        return s_next;
+    };
+    for (int tile = take(-1); tile < n_tiles; tile = take(tile)) {
         if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) continue;
         const float* ph = phi + (size_t)tile * P.npup;
         float2* sp = spec + (size_t)tile * P.nap;
@@ -683,7 +694,7 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
 }  // namespace
 
 using DFWKernel = void (*)(DevPlan, int, const float*, const float*, float2*, char*, size_t, int, float, int32_t*,
-                           unsigned long long*);
+                           unsigned long long*, int*);
 
 static DFWKernel dfw_kernel(int K) {
     switch (K) {
@@ -725,14 +736,19 @@ int configure_dfw(size_t smem, int K) {
 // grid: tile slots (clusters); each gets K blocks.
 cudaError_t launch_darkfield_wide(const DevPlan& P, int K, int grid, size_t smem, int n_tiles, const float* I,
                                   const float* phi, float2* spec, void* scratch, size_t per_block, int iters,
-                                  float tol, int32_t* status, unsigned long long* counters, cudaStream_t st) {
+                                  float tol, int32_t* status, unsigned long long* counters, int* work,
+                                  cudaStream_t st) {
     DFWKernel f = dfw_kernel(K);
     if (!f || P.h != 16 * kWBN || P.w != P.h) return cudaErrorInvalidValue;
     const int slots = min(grid, n_tiles);
     if (slots < 1) return cudaErrorInvalidConfiguration;
     if (K == 1) {
+        if (work) {
+            const cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int), st);
+            if (e != cudaSuccess) return e;
+        }
         f<<<slots, kWThreads, smem, st>>>(P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol, status,
-                                          counters);
+                                          counters, work);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -748,7 +764,7 @@ cudaError_t launch_darkfield_wide(const DevPlan& P, int K, int grid, size_t smem
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, f, P, n_tiles, I, phi, spec, (char*)scratch, per_block, iters, tol, status,
-                              counters);
+                              counters, (int*)nullptr);
 }
 
 }  // namespace apic

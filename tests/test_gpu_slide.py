@@ -171,3 +171,37 @@ def test_unaligned_buffers_take_the_per_pixel_rule(plan):
     torch.cuda.synchronize()
     d = (ou - ref).abs().max().item()
     assert d <= 1e-6 * ref.abs().max().item()
+
+
+@pytest.mark.parametrize("n", [64, 512])
+def test_skipped_background_tiles_leave_the_others_bit_exact(n):
+    """Uneven work: with APIC_SKIP_BACKGROUND the near-blank tiles of a mixed batch are
+    skipped (status BACKGROUND, zero outputs) and the darkfield blocks take the remaining
+    tiles from a shared counter; each sample tile's result is bit for bit that of a batch
+    holding the sample tiles alone."""
+    from paper_2407_20469_gb300 import learn
+    ill = synth.illumination() if n == 64 else synth.illumination_8_24()
+    T = 40 if n == 64 else 6
+    blank = np.zeros(T, dtype=bool)
+    blank[1::3] = True
+    blank[-1] = True
+    zern = learn.coefficients(learn.field_table(), np.zeros((T, 2), np.float32))
+    plan = apic.Plan.from_illumination(n, ill, max_tiles=T, bg_contrast=0.02, flags=apic.APIC_SKIP_BACKGROUND)
+    I = learn.simulate(plan, zern, blank, 5)
+    H = plan.info.out_h
+    f_mix = torch.full((T, H, 2 * H), 7.0, dtype=torch.float32, device="cuda")
+    z_mix = torch.zeros((T, 15), dtype=torch.float32, device="cuda")
+    s_mix = torch.full((T,), -1, dtype=torch.int32, device="cuda")
+    plan.reconstruct_batch(T, I, f_mix, z_mix, None, s_mix)
+    keep = np.nonzero(~blank)[0]
+    k = len(keep)
+    idx = torch.as_tensor(keep, device="cuda")
+    f_s = torch.zeros((k, H, 2 * H), dtype=torch.float32, device="cuda")
+    z_s = torch.zeros((k, 15), dtype=torch.float32, device="cuda")
+    s_s = torch.full((k,), -1, dtype=torch.int32, device="cuda")
+    plan.reconstruct_batch(k, I[idx].contiguous(), f_s, z_s, None, s_s)
+    torch.cuda.synchronize()
+    st = s_mix.cpu().numpy()
+    assert np.all((st[blank] & apic.APIC_TILE_BACKGROUND) != 0) and np.all(st[~blank] == 0)
+    assert torch.count_nonzero(f_mix[torch.as_tensor(np.nonzero(blank)[0], device="cuda")]) == 0
+    assert torch.equal(f_mix[idx], f_s) and torch.equal(z_mix[idx], z_s)
