@@ -83,6 +83,7 @@ def parse():
                          "whole-slide stream (512-pixel windows, 40 %% background)")
     ap.add_argument("--slide-rows", type=int, default=32)
     ap.add_argument("--slide-cols", type=int, default=64)
+    ap.add_argument("--slide-overlap", type=float, default=0.0, help="window overlap fraction of the slide line")
     ap.add_argument("--seed", type=int, default=2407)
     ap.add_argument("--df-tol", type=float, default=0.0, help="CGLS tolerance (0: library default)")
     ap.add_argument("--df-iters", type=int, default=0, help="CGLS iteration cap (0: library default)")
@@ -908,7 +909,9 @@ def learned_arm(args):
             step = lambda m=mode: plan.reconstruct_learned(net, m, n_eval, I, uv_d, field, zern, None, status)
         for _ in range(args.warmup):
             step()
+        plan.counters(reset=True)
         ms, clk = timed(step, args.steps, device)
+        cnt = plan.counters(reset=True)
         z = zern.cpu().numpy().astype(np.float64)
         st = status.cpu().numpy()
         d = z[:, 3:] - z_true[:, 3:].astype(np.float64)
@@ -918,6 +921,8 @@ def learned_arm(args):
                                               "sample": float(np.median(err[~blank]))},
                      "pupil_rms_p90_rad": {"background": float(np.percentile(err[blank], 90)),
                                            "sample": float(np.percentile(err[~blank], 90))},
+                     "cg_iterations_per_solve": cnt["cg_iterations"] / max(1, cnt["df_solves"]),
+                     "tiles_notconv": int(np.count_nonzero(st & apic.APIC_TILE_NOTCONV)),
                      "tiles_learned": int(np.count_nonzero(st & apic.APIC_TILE_LEARNED)),
                      "tiles_warm_kept": int(np.count_nonzero(st & apic.APIC_TILE_WARM))}
     best = out["warm_and_replace"]
@@ -944,15 +949,18 @@ def learned_arm(args):
 def slide_arm(args):
     """Whole-slide stream: a contiguous strip of a 76.2 x 25.4 mm slide at 10x / 0.25 NA
     (0.345 um pixels: the slide is 220,870 x 73,623 low-res pixels, about 20,000 windows of 512),
-    cut into 512-pixel windows with 6 % overlap, 40 % of them background (blob-shaped tissue
-    mask over the window grid), 8 + 24 images; one step = cut, reconstruct (background windows
-    skipped by the contrast test) and paste the whole strip."""
+    cut into 512-pixel windows, 40 % of them background (blob-shaped tissue mask over the window
+    grid), 8 + 24 images; one step = cut, reconstruct (background windows skipped by the contrast
+    test) and paste the whole strip. The strip's stacks are simulated window by window (each on
+    its own periodic grid), so windows that overlap would see their neighbours' simulations at
+    their edges; by default the windows therefore tile the strip without overlap
+    (--slide-overlap gives the overlap fraction; overlap blending has its own line)."""
     import torch
     from paper_2407_20469_gb300 import apic, build, learn, slide, synth
     build.build()
     device = torch.device("cuda", torch.cuda.current_device())
     n, rows, cols = 512, args.slide_rows, args.slide_cols
-    stride = n - int(round(0.06 * n))
+    stride = n - int(round(args.slide_overlap * n))
     Hs, Ws = (rows - 1) * stride + n, (cols - 1) * stride + n
     ill = illumination_for("8+24")
     batch = 1024
@@ -983,8 +991,12 @@ def slide_arm(args):
     for _ in range(args.warmup):
         res = step()
     plan.counters(reset=True)
+    plan.timing(True)
+    plan.stage_ms(reset=True)
     ms, clk = timed(step, args.steps, device)
     cnt = plan.counters(reset=True)
+    stage, calls = plan.stage_ms(reset=True)
+    plan.timing(False)
     out_f, z, st, _ = step()
     st = st.cpu().numpy()
     skipped = int(np.count_nonzero(st & apic.APIC_TILE_BACKGROUND))
@@ -995,7 +1007,8 @@ def slide_arm(args):
         "value": slide_px / sec / 1e6, "unit": "Mpx/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"strip of {rows} x {cols} windows of {n}x{n} (stride {stride}, 6 % overlap; "
+        "config": {"workload": f"strip of {rows} x {cols} windows of {n}x{n} (stride {stride}, "
+                               f"{100 * args.slide_overlap:.0f} % overlap; "
                                f"{Hs} x {Ws} low-res px = {Hs * 0.345e-3:.2f} x {Ws * 0.345e-3:.2f} mm of the "
                                f"76.2 x 25.4 mm slide, {100.0 * rows * cols / 20000:.0f} % of its ~20,000 windows), "
                                f"8 + 24 images, {int(blank.sum())} background windows ({100 * blank.mean():.0f} %), "
@@ -1005,6 +1018,9 @@ def slide_arm(args):
                    "reconstructed_tiles_per_s": (rows * cols - skipped) / sec,
                    "reconstructed_output_Mpx_s": (rows * cols - skipped) * H * H / sec / 1e6,
                    "batch": batch, "l2": f"inputs_larger_than_l2 ({n_img * Hs * Ws * 4 / 1e9:.1f} GB slide stack)",
+                   "cg_iterations_per_solve": cnt["cg_iterations"] / max(1, cnt["df_solves"]),
+                   "tiles_notconv": int(np.count_nonzero(st & apic.APIC_TILE_NOTCONV)),
+                   "stage_ms_per_step": {k: v / max(1, args.steps) for k, v in stage.items()},
                    "output_finite": bool(torch.isfinite(out_f).all().item()),
                    "learned_warm_start": "not used: the network's features take tiles of up to 256 pixels"},
         "roofline": None, "e2e": None, "gpu_launches": cnt["launches"] // max(1, args.steps), "clocks": clk,
