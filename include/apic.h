@@ -89,7 +89,8 @@ typedef struct {
     float na;                    /* objective numerical aperture (0.25)                      */
     float wavelength_um;         /* 0.52                                                      */
     float pixel_um;              /* camera pixel in the sample plane (0.345)                  */
-    int upsample;                /* output upsampling factor u (2)                             */
+    int upsample;                /* output upsampling factor u (2; 3 for the paper's set-up
+                                    size): u tile_h must be 2^k or 3 * 2^k, at most 3072      */
     int max_tiles;               /* largest n_tiles of one call; larger calls are chunked     */
     int df_iters;                /* CGLS iterations per darkfield image (<= 0: 40)            */
     float df_tol;                /* CG stop: ||C^H r|| <= df_tol ||C^H b|| (<= 0: 3e-4, which

@@ -844,8 +844,10 @@ apic_status apic_plan_create(const apic_params* pr, apic_plan** out) {
     if (!pr->h_kx || !pr->h_ky) return fail(APIC_EINVAL, "NULL illumination arrays");
     if (!(pr->na > 0 && pr->na < 1.5f) || !(pr->wavelength_um > 0) || !(pr->pixel_um > 0))
         return fail(APIC_EINVAL, "na, wavelength_um, pixel_um must be positive");
-    if (pr->upsample < 1 || pr->upsample > 8 || !pow2(pr->tile_h * pr->upsample) || pr->tile_h * pr->upsample > 1024)
-        return fail(APIC_EINVAL, "upsample must keep the output a power of two <= 1024");
+    // the output transform takes lengths 2^k and 3 * 2^k (upsampling 3: the paper's set-up size)
+    const int out_n = pr->tile_h * pr->upsample;
+    if (pr->upsample < 1 || pr->upsample > 8 || !(pow2(out_n) || (out_n % 3 == 0 && pow2(out_n / 3))) || out_n > 3072)
+        return fail(APIC_EINVAL, "upsample must make the output side 2^k or 3 * 2^k, at most 3072");
     if (pr->max_tiles < 1) return fail(APIC_EINVAL, "max_tiles < 1");
 
     apic_plan* plan = new apic_plan();

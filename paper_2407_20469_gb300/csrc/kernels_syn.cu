@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_sim_object(DevPlan P, int n_tiles,
     extern __shared__ float4 smem4[];
     float2* sm = reinterpret_cast<float2*>(smem4);
     const int N = P.H, lN = ilog2(N);
+    const bool p2 = is_pow2(N);
     float2* tw = sm + 2 * (kChunk / N) * (N + 1);
     load_twiddles(tw, P.tw_N, N);
     const FFTChunk c = make_chunk(sm, N, tw);
@@ -119,13 +120,13 @@ __global__ void __launch_bounds__(kThreads) k_sim_object(DevPlan P, int n_tiles,
         const float2* o = obj + (size_t)tile * N * N;
         float2* O = ohat + (size_t)tile * N * N;
         for (int r0 = 0; r0 < N; r0 += S) {
-            for (int t = threadIdx.x; t < (S << lN); t += blockDim.x) {
-                const int q = t >> lN, x = t & (N - 1);
+            for (int t = threadIdx.x; t < S * N; t += blockDim.x) {
+                const int q = p2 ? t >> lN : t / N, x = t - q * N;
                 c.a[q * ld + x] = o[(size_t)(r0 + q) * N + x];
             }
             const float2* R = fft_chunk<false>(c);
-            for (int t = threadIdx.x; t < (S << lN); t += blockDim.x) {
-                const int q = t >> lN, x = t & (N - 1);
+            for (int t = threadIdx.x; t < S * N; t += blockDim.x) {
+                const int q = p2 ? t >> lN : t / N, x = t - q * N;
                 O[(size_t)(r0 + q) * N + x] = R[q * ld + x];
             }
             __syncthreads();

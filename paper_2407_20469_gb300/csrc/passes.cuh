@@ -21,7 +21,8 @@ __device__ inline FFTChunk make_chunk(float2* base, int N, const float2* tw) {
     FFTChunk c;
     c.N = N;
     c.logN = ilog2(N);
-    c.S = kChunk / N;
+    c.S = kChunk / N;                 // sequences per chunk: the most that fit and divide N
+    while (c.S > 1 && N % c.S) --c.S;
     c.ld = N + 1;
     c.a = base;
     c.b = base + c.S * c.ld;
@@ -39,6 +40,7 @@ template <bool INV, class Val>
 __device__ void rows_from_points(const FFTChunk& c, float2* G, int m, int y0, int y1, const int* rowptr,
                                  const int* px, const int* py, Val val) {
     const int ld = c.ld, lm = c.logN;
+    const bool p2 = is_pow2(m);
     for (int b0 = 0; b0 <= y1 - y0; b0 += c.S) {
         const int nb = min(c.S, y1 - y0 + 1 - b0);
         zero_smem(c.a, nb * ld);
@@ -49,8 +51,8 @@ __device__ void rows_from_points(const FFTChunk& c, float2* G, int m, int y0, in
         FFTChunk cc = c;
         cc.S = nb;
         const float2* R = fft_chunk<INV>(cc);
-        for (int t = threadIdx.x; t < (nb << lm); t += blockDim.x) {
-            const int s = t >> lm, x = t & (m - 1);
+        for (int t = threadIdx.x; t < nb * m; t += blockDim.x) {
+            const int s = p2 ? t >> lm : t / m, x = t - s * m;
             G[(size_t)freq_index(y0 + b0 + s, m) * m + x] = R[s * ld + x];
         }
         __syncthreads();
@@ -63,10 +65,11 @@ template <class Out>
 __device__ void rows_to_points(const FFTChunk& c, const float2* G, int m, int y0, int y1, const int* rowptr,
                                const int* px, const int* py, Out out) {
     const int ld = c.ld, lm = c.logN;
+    const bool p2 = is_pow2(m);
     for (int b0 = 0; b0 <= y1 - y0; b0 += c.S) {
         const int nb = min(c.S, y1 - y0 + 1 - b0);
-        for (int t = threadIdx.x; t < (nb << lm); t += blockDim.x) {
-            const int s = t >> lm, x = t & (m - 1);
+        for (int t = threadIdx.x; t < nb * m; t += blockDim.x) {
+            const int s = p2 ? t >> lm : t / m, x = t - s * m;
             c.a[s * ld + x] = G[(size_t)freq_index(y0 + b0 + s, m) * m + x];
         }
         FFTChunk cc = c;

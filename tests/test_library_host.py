@@ -109,3 +109,26 @@ def test_binding_refuses_buffers_the_callee_cannot_reach():
     plan = apic.Plan.from_illumination(64, synth.illumination(), flags=apic.APIC_HOST_ONLY)
     with pytest.raises(ValueError):
         plan.background(1, torch.zeros(24, 64, 64), torch.zeros(1), torch.zeros(1, dtype=torch.int32))
+
+
+def test_upsampling_3_plans_and_refusals():
+    """The output side may be 2^k or 3 * 2^k (upsampling 3 for the paper's set-up size): the
+    host aperture at 3x equals the checker's synthetic aperture on the 3n grid; other
+    factors that break both forms are refused."""
+    ill = synth.illumination_12_22()
+    plan = apic.Plan.from_illumination(128, ill, upsample=3, flags=apic.APIC_HOST_ONLY)
+    assert (plan.info.out_h, plan.info.out_w) == (384, 384)
+    g = grid.Geometry(128, 128, float(synth.NA), float(synth.WAVELENGTH_UM), float(synth.PIXEL_UM), 3)
+    k = grid.snap_leds(ill.kx, ill.ky, ill.n_bf, g)
+    spec = oapic.Spectrum(g)
+    for kb in k[:ill.n_bf]:
+        spec.put(grid.disc_points(g, kb), 1.0)
+    for j in grid.darkfield_order(k[ill.n_bf:]):
+        s = grid.darkfield_sets(grid.disc_points(g, k[ill.n_bf + j]), spec.known_set(), int(j), k[ill.n_bf + j])
+        if s.used:
+            spec.put(s.U, 1.0)
+    assert plan.info.n_aperture == int(spec.known.sum())
+    for u in (5, 7):
+        with pytest.raises(apic.ApicError) as e:
+            apic.Plan.from_illumination(128, ill, upsample=u, flags=apic.APIC_HOST_ONLY)
+        assert e.value.code == apic.APIC_EINVAL
