@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--tiles", type=int, default=None, help="tiles per step (default: the workload's)")
     ap.add_argument("--tile", type=int, default=None, help="tile side (default: the workload's)")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-host-tiles", type=int, default=0,
+                    help="tiles the end-to-end leg's pinned host buffers hold (0: the whole step if host RAM allows)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-assisted timing")
     ap.add_argument("--per-tile", type=int, default=32,
@@ -583,6 +585,8 @@ def gpu_arm(args):
         except (ValueError, OSError, AttributeError):
             ram = 0
         Th = max(1, min(T, int(HOST_E2E_RAM_FRAC * ram // per_tile_bytes))) if ram else min(T, 512)
+        if args.e2e_host_tiles > 0:
+            Th = min(Th, args.e2e_host_tiles)
         while True:          # a pinned allocation the host refuses: halve the buffers
             try:
                 I_host = torch.empty((Th,) + tuple(I.shape[1:]), dtype=torch.float32, pin_memory=True)

@@ -266,14 +266,16 @@ def test_register_and_legacy_kernels_agree(n):
     assert rel_l2(fields[0][0], res.field) < FIELD_TOL
 
 
-def test_reconstruct_batch_replays_in_a_cuda_graph():
-    """apic_reconstruct_batch only enqueues kernels on the given stream, so it can be
-    captured once and replayed; replays match eager calls on new inputs."""
-    n, count = 64, 3
-    plan = new_plan(n, max_tiles=count)
+@pytest.mark.parametrize("n,count", [(64, 3), (512, 2)])
+def test_reconstruct_batch_replays_in_a_cuda_graph(n, count):
+    """apic_reconstruct_batch only enqueues work on the given stream (kernels, and the
+    darkfield launches' tile-counter resets), so it can be captured once and replayed;
+    replays match eager calls on new inputs (at 512: the wide darkfield kernel)."""
+    ill = synth.illumination() if n == 64 else synth.illumination_8_24()
+    plan = new_plan(n, ill, max_tiles=count)
     H = plan.info.out_h
-    I1, _, _ = make_tiles(n, count, seed=71)
-    I2, _, _ = make_tiles(n, count, seed=72)
+    I1, _, _ = make_tiles(n, count, seed=71, ill=ill, phase_hi=0.5)
+    I2, _, _ = make_tiles(n, count, seed=72, ill=ill, phase_hi=0.5)
     I = dev(I1)
     ref = []
     for Ih in (I1, I2):
