@@ -373,12 +373,12 @@ def fft2_flops(a, b):
 def df_flops(plan, n):
     """Per used darkfield image: (setup flops per solve, flops per CG iteration), dense-grid counts.
 
-    Setup: the image's n x n transform, P * P (two transforms on the P * P grid: the
-    camera grid for 512-pixel tiles, the register grid otherwise), the known field and
-    C^H b on the image's grid (three); per CG iteration C d and C^H r (four transforms
-    on the image's grid)."""
+    Setup: for 512-pixel tiles the known field's inverse and the forward transform of
+    I - |p|^2 on the camera grid (two); otherwise the image's n x n transform and P * P
+    (two transforms on the register grid); then the known field and C^H b on the
+    image's grid (three). Per CG iteration C d and C^H r (four transforms on the
+    image's grid)."""
     m = plan.info.fft_m
-    pp = n if n == 512 else m
     out = []
     for i in range(plan.info.n_df):
         _, meta = plan.df_set(i, 0)
@@ -386,7 +386,8 @@ def df_flops(plan, n):
             continue
         _, mx, my = plan.df_grid(i)
         mx, my = (mx or m), (my or m)
-        out.append((fft2_flops(n, n) + 2 * fft2_flops(pp, pp) + 3 * fft2_flops(mx, my), 4 * fft2_flops(mx, my)))
+        rhs = 2 * fft2_flops(n, n) if n == 512 else fft2_flops(n, n) + 2 * fft2_flops(m, m)
+        out.append((rhs + 3 * fft2_flops(mx, my), 4 * fft2_flops(mx, my)))
     return out
 
 

@@ -6,8 +6,9 @@
 // five passes per iteration over a band-row grid; see there), at the sizes of a
 // 512 x 512 tile (pupil radius ~85 grid points, up to ~2.8 k unknowns and ~36 k
 // equations per image):
-//  * the image transform (b = F(I_j) on Q) and P * P run on the camera grid,
-//    n = 512 = 16 x 32 (exact for the lags of Eq. 13: |P - P| <= 2 R < n / 2);
+//  * the right-hand side b = F(I_j) - P * P on Q is formed on the camera grid,
+//    n = 512 = 16 x 32, as the spectrum of I_j - |p|^2 with p the known field's
+//    inverse transform (exact: the lags of P * P reach 2 R < n / 2);
 //  * each image's CG runs on its own (row, column) grid chosen with the plan,
 //    rows of 288 or 320 points and columns of 192, 256, 288 or 320 points, the
 //    smallest on which both correlations are free of aliasing;
@@ -195,16 +196,6 @@ struct WMidStoreField {     // column-major p s (16 B values per column)
             }
     }
 };
-template <int B>
-struct WMidAbs2 {           // p -> |p|^2
-    static constexpr bool kOut = true;
-    __device__ void operator()(float2 (&o)[Slots<B>::value][16], int, int) const {
-#pragma unroll
-        for (int s = 0; s < Slots<B>::value; ++s)
-#pragma unroll
-            for (int k1 = 0; k1 < 16; ++k1) o[s][k1] = make_float2(cabs2(o[s][k1]), 0.f);
-    }
-};
 template <int B, bool CONJ>
 struct WMidTimesField {     // o *= p s or conj(p s), from the column-major copy
     const float2* PF;
@@ -344,19 +335,37 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
     tile_sync<K>();
 }
 
-// columns of the real image (n = 512; with tr the transposed image; read once, with
-// evict-first loads): forward along y, rows qy0.. (nQ) stored to GX (row length n).
-// Chunks of 32 columns are staged through shared memory for coalesced image reads;
-// half-warps 0..31 transform them. The stage aliases the half-warp areas: each stage
-// is consumed (or written) only between barriers that separate it from the
-// transforms. Ends with __syncthreads.
+// Columns of I - |p|^2 (n = 512; the image read transposed with tr, once, with
+// evict-first loads): Eq. 13's right-hand side F(I) - P * P is the spectrum of the
+// image minus the intensity of the known field, so p's column x is formed from the
+// band rows py0.. (nP) of GP (P's rows transformed along x on the camera grid) by an
+// inverse transform along y and |p|^2 kept in registers; then the chunk's 32 image
+// columns are staged through shared memory (coalesced reads), the difference is
+// formed and transformed forward along y; rows qy0.. (nQ) go to GX (row length n).
+// Half-warps 0..31 take one column of a chunk each. The stages alias the half-warp
+// areas; barriers separate each use from the transforms. Ends with a tile barrier.
 template <int K>
-__device__ __noinline__ void wpass_image_cols(HWw w, const float2* tw, float2* stage, const float* img, float2* GX,
-                                              int qy0, int nQ, bool tr) {
+__device__ __noinline__ void wpass_image_cols_p(HWw w, const float2* tw, float2* stage, const float* img,
+                                                const float2* GP, int py0, int nP, float2* GX, int qy0, int nQ,
+                                                bool tr) {
     constexpr int BN = kWBN, n = 16 * BN, S = Slots<BN>::value;
     const HalfWarp h = w.h();
     float* stage_f = reinterpret_cast<float*>(stage);
     for (int c0 = 32 * (w.gh / kWHW); c0 < n; c0 += 32 * K) {     // this block's chunks of 32 columns
+        const int x = c0 + w.hw;
+        float2 v[BN], o[S][16];
+        float q[S][16];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) {
+            const int bb = band_row_w(w.t + 16 * j, py0, n);
+            v[j] = bb < nP ? ldx<K>(GP + (size_t)bb * n + x) : make_float2(0.f, 0.f);
+        }
+        fft_a<BN, true>(v, o, h, tw);               // p(x, y), y = (t + 16 s) + BN k1
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) q[s][k1] = cabs2(o[s][k1]);
+        __syncthreads();                            // transforms done: the stage may overwrite the areas
         if (tr) {   // column c of the solve frame is image row c
             for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
                 const int c = idx / n, y = idx - c * n;
@@ -369,21 +378,21 @@ __device__ __noinline__ void wpass_image_cols(HWw w, const float2* tw, float2* s
             }
         }
         __syncthreads();
-        float2 v[BN], o[S][16];
-#pragma unroll
-        for (int j = 0; j < BN; ++j) v[j] = make_float2(stage_f[(w.t + 16 * j) * kWStageLd + w.hw], 0.f);
-        __syncthreads();
-        fft_a<BN, false>(v, o, h, tw);
-        __syncthreads();
 #pragma unroll
         for (int s = 0; s < S; ++s)
-            if (w.t + 16 * s < BN) {
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) {
-                    const int bb = sfreqw(w.t + 16 * s + BN * k1, n) - qy0;
-                    if (bb >= 0 && bb < nQ) stage[bb * kWStageLd + w.hw] = o[s][k1];
-                }
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const int y = (w.t + 16 * s < BN ? w.t + 16 * s : 0) + BN * k1;
+                o[s][k1] = make_float2(stage_f[y * kWStageLd + w.hw] - q[s][k1], 0.f);
             }
+        __syncthreads();                            // the stage is consumed
+        fft_b<BN, false>(o, v, h, tw);              // along y: v[k1] at ky = t + 16 k1
+        __syncthreads();
+#pragma unroll
+        for (int k1 = 0; k1 < BN; ++k1) {
+            const int bb = sfreqw(w.t + 16 * k1, n) - qy0;
+            if (bb >= 0 && bb < nQ) stage[bb * kWStageLd + w.hw] = v[k1];
+        }
         __syncthreads();
         for (int idx = threadIdx.x; idx < nQ * 32; idx += blockDim.x) {
             const int b = idx >> 5, c = idx & 31;
@@ -421,41 +430,14 @@ __device__ __noinline__ void wpass_image_rows(HWw w, const float2* tw, const flo
     tile_sync<K>();
 }
 
-// rows of Q holding the column-transformed |p|^2 on the camera grid: forward along
-// x, b = bq - (P * P) / n^2 on Q (kept in bq). Ends with __syncthreads.
-template <int K>
-__device__ __noinline__ void wpass_rows_rhs(HWw w, const float2* tw, const float2* GQ, int nQ, const int* qrp,
-                                            const int* Qx, float2* bq) {
-    constexpr int B = kWBN, m = 16 * B, S = Slots<B>::value;
-    const HalfWarp h = w.h();
-    const float inv_m2 = 1.f / (float)(m * m);
-    for (int b = w.gh; b < nQ; b += w.ghs) {
-        const float2* row = GQ + (size_t)b * m;
-        float2 v[B], o[S][16];
-#pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + w.t + 16 * j);
-        fft_a<B, false>(v, o, h, tw);
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-            if (w.t + 16 * s < B) {
-#pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + 16 * s + B * k1] = o[s][k1];
-            }
-        __syncwarp(w.mask);
-        for (int e = qrp[b] + w.t; e < qrp[b + 1]; e += 16)
-            bq[e] = csub(bq[e], cscale(w.hs[freq_index(Qx[e], m)], inv_m2));
-        __syncwarp(w.mask);
-    }
-    tile_sync<K>();
-}
-
 }  // namespace
 
 // Shared memory of one block (bytes, 16-aligned offsets):
 //   [0, vec)          half-warp areas of the CG grids (17 x 20 values each)
 //   [vec, vec_end)    CG vectors x, d, s, w (max_N each)
 //   [0, setup)        during an image's setup: half-warp areas of the 512-point
-//                     transforms (17 x 32 values each), or the 32-column stage
+//                     transforms (17 x 32 values each), or the 32-column image
+//                     stage, or the output stage of the image columns
 //   [tw, tw_end)      step twiddles of the camera grid and of the image's row and
 //                     column grids
 //   [red, total)      96 doubles of reductions (block partials, then the blocks' totals)
@@ -471,9 +453,9 @@ __host__ __device__ inline DFWSmem dfw_smem_layout(int max_N, int band) {
     L.vec = walign16(std::max((size_t)kWHW * hw_single_size(kWMaxB), (size_t)band * kWStageLd) * sizeof(float2));
     const size_t cg_end = L.vec + walign16((size_t)4 * max_N * sizeof(float2));
     const size_t setup_hw = (size_t)kWHW * hw_single_size(kWBN) * sizeof(float2);
-    const size_t stage_f = (size_t)16 * kWBN * kWStageLd * sizeof(float);
     const size_t stage_c = (size_t)band * kWStageLd * sizeof(float2);
-    const size_t setup = std::max(setup_hw, std::max(stage_f, stage_c));
+    const size_t stage_f = (size_t)16 * kWBN * kWStageLd * sizeof(float);
+    const size_t setup = std::max(setup_hw, std::max(stage_c, stage_f));
     L.tw = walign16(std::max(cg_end, setup));
     L.red = walign16(L.tw + (size_t)2 * 16 * (kWBN + 2 * kWMaxB) * sizeof(float2));
     L.total = walign16(L.red + 96 * sizeof(double));
@@ -504,7 +486,7 @@ struct DFWCtx {
     float2* tw_y;           // step twiddles of the image's column grid (filled per image)
     float2 *GU, *GQ, *PF, *bq;
     float2 *dv, *sv, *wv, *xv;
-    float2* stage;
+    float2* stage;          // stages of the setup column pass (alias the half-warp areas)
     double* red;
 };
 
@@ -513,12 +495,12 @@ __device__ __forceinline__ const float2* wgrid_table(const DevPlan& P, int G) {
     return G == 12 ? P.tw_w12 : G == 16 ? P.tw_w16 : G == 18 ? P.tw_w18 : P.tw_w20;
 }
 
-// Solve of one darkfield image once b = F(I) on Q is in bq, on a grid of 16 BX row
-// points x 16 BY column points; P * P on the camera grid; by the K blocks of the
-// cluster. Returns the CG iterations (negative: did not converge).
+// Solve of one darkfield image (image `img`) on a grid of 16 BX row points x 16 BY
+// column points, by the K blocks of the cluster: b = F(I - |p|^2) on Q on the camera
+// grid, then CGNR. Returns the CG iterations (negative: did not converge).
 template <int BX, int BY, int K>
-__device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, const DevDF& D, float2* sp,
-                                      const float* ph, int iters, float tol) {
+__device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, const DevDF& D, const float* img,
+                                         float2* sp, const float* ph, int iters, float tol) {
     constexpr int n = 16 * kWBN, mx = 16 * BX;
     const HWw& w = c.w;
     const int u_off = D.u_off, p_off = D.p_off, q_off = D.q_off;
@@ -530,12 +512,13 @@ __device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, cons
     make_step_twiddles(c.tw_x, wgrid_table(P, BX), BX);
     make_step_twiddles(c.tw_y, wgrid_table(P, BY), BY);
     __syncthreads();
-    // P * P on the camera grid: band rows of P along x, |p|^2 per column and back
-    // along y on the Q band rows, then rows forward: b -= P * P on Q
+    // b = F(I) - P * P on Q (Eq. 13) as the spectrum of I - |p|^2 on the camera grid
+    // (exact: P * P's lags reach 2 R < n / 2): the known field's band rows along x,
+    // then per column p, the difference and its forward transform, then the rows
     wpass_rows_in<kWBN>(c.ws, c.tw_n, c.GQ, n, nP, prp, P.dP_x + p_off, pval);
     tile_sync<K>();
-    wpass_cols<kWBN, K>(c.ws, c.tw_n, n, c.GQ, n, py0, nP, c.GQ, n, qy0, nQ, WMidAbs2<kWBN>{});
-    wpass_rows_rhs<K>(c.ws, c.tw_n, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
+    wpass_image_cols_p<K>(c.ws, c.tw_n, c.stage, img, c.GQ, py0, nP, c.PF, qy0, nQ, D.tr != 0);
+    wpass_image_rows<K>(c.ws, c.tw_n, c.PF, nQ, qrp, P.dQ_x + q_off, c.bq);
     // band rows of the known field P (Eq. 11) along x on the row grid, then p s on
     // the column grid, column-major in PF (s = 1 / (mx my): the two unnormalised
     // transforms around each product)
@@ -665,20 +648,16 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
         bool notconv = false;
         for (int di = 0; di < P.n_used; ++di) {
             const DevDF& D = P.df[di];
-            const int nQ = D.qy1 - D.qy0 + 1;
             const float* img = I + ((size_t)tile * P.n_img + D.led) * n * n;
-            // b = F(I_j) on Q (F(I) rows staged in PF)
-            wpass_image_cols<K>(c.ws, c.tw_n, c.stage, img, c.PF, D.qy0, nQ, D.tr != 0);
-            wpass_image_rows<K>(c.ws, c.tw_n, c.PF, nQ, P.d_rowptr + D.qrp, P.dQ_x + D.q_off, c.bq);
             int r;
             switch (16 * D.bx + D.by) {
-                case 16 * 18 + 12: r = dfw_solve<18, 12, K>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 18 + 16: r = dfw_solve<18, 16, K>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 18 + 18: r = dfw_solve<18, 18, K>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 20 + 12: r = dfw_solve<20, 12, K>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 20 + 16: r = dfw_solve<20, 16, K>(c, P, D, sp, ph, iters, tol); break;
-                case 16 * 20 + 18: r = dfw_solve<20, 18, K>(c, P, D, sp, ph, iters, tol); break;
-                default: r = dfw_solve<20, 20, K>(c, P, D, sp, ph, iters, tol); break;
+                case 16 * 18 + 12: r = dfw_solve<18, 12, K>(c, P, D, img, sp, ph, iters, tol); break;
+                case 16 * 18 + 16: r = dfw_solve<18, 16, K>(c, P, D, img, sp, ph, iters, tol); break;
+                case 16 * 18 + 18: r = dfw_solve<18, 18, K>(c, P, D, img, sp, ph, iters, tol); break;
+                case 16 * 20 + 12: r = dfw_solve<20, 12, K>(c, P, D, img, sp, ph, iters, tol); break;
+                case 16 * 20 + 16: r = dfw_solve<20, 16, K>(c, P, D, img, sp, ph, iters, tol); break;
+                case 16 * 20 + 18: r = dfw_solve<20, 18, K>(c, P, D, img, sp, ph, iters, tol); break;
+                default: r = dfw_solve<20, 20, K>(c, P, D, img, sp, ph, iters, tol); break;
             }
             if (r < 0) notconv = true;
             if (threadIdx.x == 0 && rank == 0 && counters) {
