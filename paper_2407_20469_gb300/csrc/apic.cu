@@ -569,7 +569,7 @@ struct StageTimer {
 // allocated on the first learned call.
 apic_status learned_buffers(apic_plan* p) {
     if (p->feat) return APIC_OK;
-    if (!p->kkr_ok || p->dev.h > 256) return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (!p->kkr_ok) return fail(APIC_EINVAL, "network features need tiles of 64, 128, 256 or 512 pixels");
     if (p->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
     apic_status s;
     if ((s = dmalloc(p, (void**)&p->feat, (size_t)p->max_tiles * feature_floats() * sizeof(float))) != APIC_OK)
@@ -1243,8 +1243,7 @@ apic_status apic_features(apic_plan* plan, int n_tiles, const float* I, float* f
     apic_status s = check_stage(plan, n_tiles);
     if (s != APIC_OK) return s;
     if (!I || !feat) return fail(APIC_EINVAL, "NULL intensity or features");
-    if (!plan->kkr_ok || plan->dev.h > 256)
-        return fail(APIC_EINVAL, "network features need tiles of 64, 128 or 256 pixels");
+    if (!plan->kkr_ok) return fail(APIC_EINVAL, "network features need tiles of 64, 128, 256 or 512 pixels");
     if (plan->dev.n_bf != 8) return fail(APIC_EINVAL, "the network takes exactly 8 NA-matching images");
     if (n_tiles == 0) return APIC_OK;
     APIC_TRY_LAUNCH(launch_features(plan->dev, plan->grid_kkr, n_tiles, I, feat, plan->kk_scratch,

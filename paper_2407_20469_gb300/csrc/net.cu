@@ -82,7 +82,7 @@ struct Layout {
 template <int BN>
 __global__ void __launch_bounds__(512, 1) k_features(DevPlan P, int n_tiles, const float* __restrict__ I,
                                                      float* __restrict__ feat, float2* __restrict__ scratch) {
-    constexpr int n = 16 * BN, HWS = HWSize<BN>::value, NHW = 32;
+    constexpr int n = 16 * BN, HWS = HWSize<BN>::value, NHW = 32, S = Slots<BN>::value;
     extern __shared__ float4 smem4[];
     float2* hw_area = reinterpret_cast<float2*>(smem4);
     float2* tw = hw_area + NHW * HWS;
@@ -105,35 +105,40 @@ __global__ void __launch_bounds__(512, 1) k_features(DevPlan P, int n_tiles, con
         s = block_sum(s, red);
         const float inv_dc = s > 0 ? (float)(1.0 / s) : 0.f;
         for (int r = hw; r < n; r += NHW) {
-            float2 v[BN], o[16];
+            float2 v[BN], o[S][16];
 #pragma unroll
             for (int j = 0; j < BN; ++j) v[j] = make_float2(img[(size_t)r * n + t + 16 * j], 0.f);
-            fft_alpha<BN, false>(v, o, h, tw);
-            if (t < BN) {
+            fft_a<BN, false>(v, o, h, tw);
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) {
-                    const int kx = t + BN * k1;
-                    const int sx = kx < n / 2 ? kx : kx - n;
-                    if (sx >= -kCrop / 2 && sx < kCrop / 2) G[(size_t)r * kCrop + sx + kCrop / 2] = o[k1];
+            for (int sl = 0; sl < S; ++sl)
+                if (t + 16 * sl < BN) {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) {
+                        const int kx = t + 16 * sl + BN * k1;
+                        const int sx = kx < n / 2 ? kx : kx - n;
+                        if (sx >= -kCrop / 2 && sx < kCrop / 2) G[(size_t)r * kCrop + sx + kCrop / 2] = o[sl][k1];
+                    }
                 }
-            }
         }
         __syncthreads();
         float* f = feat + (size_t)tile * kCrop * kCrop * kIn + i;
         for (int c = hw; c < kCrop; c += NHW) {
-            float2 v[BN], o[16];
+            float2 v[BN], o[S][16];
 #pragma unroll
             for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * kCrop + c];
-            fft_alpha<BN, false>(v, o, h, tw);
-            if (t < BN) {
+            fft_a<BN, false>(v, o, h, tw);
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) {
-                    const int ky = t + BN * k1;
-                    const int sy = ky < n / 2 ? ky : ky - n;
-                    if (sy >= -kCrop / 2 && sy < kCrop / 2)
-                        f[((size_t)(sy + kCrop / 2) * kCrop + c) * kIn] = logf(sqrtf(cabs2(o[k1])) * inv_dc + 1e-4f);
+            for (int sl = 0; sl < S; ++sl)
+                if (t + 16 * sl < BN) {
+#pragma unroll
+                    for (int k1 = 0; k1 < 16; ++k1) {
+                        const int ky = t + 16 * sl + BN * k1;
+                        const int sy = ky < n / 2 ? ky : ky - n;
+                        if (sy >= -kCrop / 2 && sy < kCrop / 2)
+                            f[((size_t)(sy + kCrop / 2) * kCrop + c) * kIn] =
+                                logf(sqrtf(cabs2(o[sl][k1])) * inv_dc + 1e-4f);
+                    }
                 }
-            }
         }
         __syncthreads();
     }
@@ -620,6 +625,10 @@ cudaError_t launch_features(const DevPlan& P, int grid, int n_tiles, const float
         case 16:
             e = raise_smem_limit((const void*)k_features<16>, smem);
             if (e == cudaSuccess) k_features<16><<<grid, 512, smem, st>>>(P, n_tiles, I, feat, scratch);
+            break;
+        case 32:
+            e = raise_smem_limit((const void*)k_features<32>, smem);
+            if (e == cudaSuccess) k_features<32><<<grid, 512, smem, st>>>(P, n_tiles, I, feat, scratch);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -43,7 +43,7 @@ def _stacks(n, count, seed, blank_frac=0.3):
     return plan, I, uv, zern, blank
 
 
-@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("n", [64, 128, 256, 512])
 def test_features_match_definition(lib, n):
     plan, I, uv, zern, blank = _stacks(n, 3, 40 + n)
     feat = torch.empty((3, 64, 64, 8), dtype=torch.float32, device="cuda")
@@ -58,9 +58,9 @@ def test_features_match_definition(lib, n):
 
 
 def test_features_reject_unsupported_plans(lib):
-    ill = synth.illumination_8_24()
-    plan = apic.Plan.from_illumination(512, ill, max_tiles=1)
-    x = torch.zeros((1, 32, 512, 512), device="cuda")
+    """The network takes exactly 8 NA-matching images: a 12 + 22 plan is refused."""
+    plan = apic.Plan.from_illumination(64, synth.illumination_12_22(), max_tiles=1, upsample=3)
+    x = torch.zeros((1, 34, 64, 64), device="cuda")
     f = torch.zeros((1, 64, 64, 8), device="cuda")
     with pytest.raises(apic.ApicError):
         plan.features(1, x, f)
