@@ -15,7 +15,9 @@
 //  * the band grids GU, GQ, the column-major known field p and b on Q live in the
 //    block's global scratch (L2 / HBM): a 512-pixel tile's GU alone (up to 94 rows
 //    of 320 points) exceeds what shared memory can hold beside the transform
-//    areas. Shared memory holds the half-warp transform areas and the CG vectors;
+//    areas. The band grids are stored in 4 x 4 tiles (t4_index), so that the column
+//    passes' loads and stores use whole sectors and few cache lines, like the rows
+//    passes'. Shared memory holds the half-warp transform areas and the CG vectors;
 //    the setup transforms (512-point areas, the column stage) alias both, since no
 //    CG vector is live while an image is being set up.
 // A tile is solved by a cluster of K blocks of 512 threads (persistent over tiles;
@@ -60,6 +62,30 @@ __device__ __forceinline__ int band_row_w(int i, int y0, int m) {
     if (r < 0) r += m;
     return r;
 }
+
+// Band grids in 4 x 4 tiles: element (r, c) of a grid with ncols columns (a multiple
+// of 4; rows allocated in groups of 4) sits in the 128-byte line of tile (r / 4, c / 4),
+// in its 32-byte sector of rows 2 (r / 2) .. +1 and columns 2 (c / 2) .. +1. A warp's two
+// half-warps read or write two adjacent rows over 16 columns (rows passes: rows 2 w' and
+// 2 w' + 1) or two adjacent columns over 16 rows (columns passes): either way 4 or 5
+// lines per instruction and every loaded sector fully used, where a row-major grid
+// gives the columns passes 16 lines and half-used sectors per instruction.
+// t4_index(r, c) = t4_row(r, ncols) + t4_col(c); adding 4 k to c adds 16 k.
+__device__ __forceinline__ int t4_low(int r) { return ((r & 2) << 2) + ((r & 1) << 1); }
+__device__ __forceinline__ int t4_row(int r, int ncols) { return (r & ~3) * ncols + t4_low(r); }
+__device__ __forceinline__ int t4_col(int c) { return ((c & ~3) << 2) + ((c & 2) << 1) + (c & 1); }
+__host__ __device__ inline int t4_rows(int rows) { return (rows + 3) & ~3; }
+
+// Offset of column t + m of a row (lane t; m known after unrolling): the lane's four
+// column offsets c4[q] = t4_col(t + q) and a multiple of 16.
+struct T4Lane {
+    int c0, c1, c2, c3;
+    __device__ explicit T4Lane(int t) : c0(t4_col(t)), c1(t4_col(t + 1)), c2(t4_col(t + 2)), c3(t4_col(t + 3)) {}
+    __device__ __forceinline__ int at(int m) const {
+        const int q = m & 3;
+        return (q == 0 ? c0 : q == 1 ? c1 : q == 2 ? c2 : c3) + 4 * (m & ~3);
+    }
+};
 
 // Half-warp of a cluster: t lane, hw index in the block, gh index in the cluster
 // (rank x 32 + hw), ghs half-warps in the cluster.
@@ -217,12 +243,13 @@ struct WMidTimesField {     // o *= p s or conj(p s), from the column-major copy
 // ---- passes (each a separate function so registers are allocated per pass)
 
 // rows of a band: scatter val(e) at x = px[e], inverse transform along x, store the
-// rows of G (row stride ld).
+// rows of the tiled grid G (ld columns).
 template <int B, class Val>
 __device__ __noinline__ void wpass_rows_in(HWw w, const float2* tw, float2* G, int ld, int nrows, const int* rp,
                                            const int* px, Val val) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
+    const T4Lane L(w.t);
     for (int b = w.gh; b < nrows; b += w.ghs) {
 #pragma unroll
         for (int j = 0; j < B; ++j) w.hs[w.t + 16 * j] = make_float2(0.f, 0.f);
@@ -234,29 +261,30 @@ __device__ __noinline__ void wpass_rows_in(HWw w, const float2* tw, float2* G, i
         for (int j = 0; j < B; ++j) v[j] = w.hs[w.t + 16 * j];
         __syncwarp(w.mask);
         fft_a<B, true>(v, o, h, tw);
-        float2* row = G + (size_t)b * ld;
+        float2* row = G + t4_row(b, ld);
 #pragma unroll
         for (int s = 0; s < S; ++s)
             if (w.t + 16 * s < B) {
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) row[w.t + 16 * s + B * k1] = o[s][k1];
+                for (int k1 = 0; k1 < 16; ++k1) row[L.at(16 * s + B * k1)] = o[s][k1];
             }
     }
 }
 
-// rows of a band of G: forward transform along x; returns the sum of out(e, value)
-// over this lane's points.
+// rows of a band of the tiled grid G (ld columns): forward transform along x; returns
+// the sum of out(e, value) over this lane's points.
 template <int B, int K, class Out>
 __device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const float2* G, int ld, int nrows,
                                              const int* rp, const int* px, Out out) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
     float acc = 0.f;
+    const int c0 = t4_col(w.t);
     for (int b = w.gh; b < nrows; b += w.ghs) {
-        const float2* row = G + (size_t)b * ld;
+        const float2* row = G + t4_row(b, ld) + c0;
         float2 v[B], o[S][16];
 #pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + w.t + 16 * j);
+        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + 64 * j);
         fft_a<B, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -271,11 +299,13 @@ __device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const floa
     return acc;
 }
 
-// columns x < ncols of a grid whose columns have 16 B points: band rows of Gi (row r
-// of the band at grid row (yi0 + r) mod 16 B, ni rows, row stride ldi) are the input,
-// the rest zero; inverse along y, mid, and (Mid::kOut) forward along y with band rows
-// yo0.. (no) stored to Go (row stride ldo). Each half-warp reads and writes its own
-// columns, so Gi and Go may be the same grid. Ends with a tile barrier.
+// columns x < ncols of a grid whose columns have 16 B points: band rows of the tiled
+// grid Gi (row r of the band at grid row (yi0 + r) mod 16 B, ni rows, ldi columns) are
+// the input, the rest zero; inverse along y, mid, and (Mid::kOut) forward along y with
+// band rows yo0.. (no) stored to the tiled grid Go (ldo columns). Each half-warp reads
+// and writes its own columns, so Gi and Go may be the same grid. A lane's band rows
+// are all congruent mod 4 (16 B is), so their in-tile row offset is one per lane. Ends
+// with a tile barrier.
 // (Measured and left out: staging strips of 32 columns through shared memory for
 // 256-byte row accesses, and issuing the next column's loads before the current
 // transform; both slowed the kernel by ~10 %: the first adds block barriers between
@@ -286,39 +316,43 @@ __device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, cons
                                         int ni, float2* Go, int ldo, int yo0, int no, Mid mid) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
+    const int li = t4_low(w.t - yi0), lo = t4_low(w.t - yo0);
     for (int x = w.gh; x < ncols; x += w.ghs) {
         float2 v[B], o[S][16];
+        const float2* gi = Gi + li + t4_col(x);
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             const int bb = band_row_w(w.t + 16 * j, yi0, m);
-            v[j] = bb < ni ? ldx<K>(Gi + (size_t)bb * ldi + x) : make_float2(0.f, 0.f);
+            v[j] = bb < ni ? ldx<K>(gi + (bb & ~3) * ldi) : make_float2(0.f, 0.f);
         }
         fft_a<B, true>(v, o, h, tw);
         mid(o, x, w.t);
         if constexpr (Mid::kOut) {
             fft_b<B, false>(o, v, h, tw);
+            float2* go = Go + lo + t4_col(x);
 #pragma unroll
             for (int k1 = 0; k1 < B; ++k1) {
                 const int bb = band_row_w(w.t + 16 * k1, yo0, m);
-                if (bb < no) Go[(size_t)bb * ldo + x] = v[k1];
+                if (bb < no) go[(bb & ~3) * ldo] = v[k1];
             }
         }
     }
     tile_sync<K>();
 }
 
-// rows of Q in place (row stride 16 B): forward along x, keep the Q lags, inverse
+// rows of Q in place (tiled grid of 16 B columns): forward along x, keep the Q lags, inverse
 // along x. qmask: per band row 16 words; the bit k1 of half (t + 16 s) & 1 of word
 // (t + 16 s) >> 1 says whether x index (t + 16 s) + B k1 is in Q. Ends with __syncthreads.
 template <int B, int K>
 __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G, int nrows, const unsigned* qmask) {
     constexpr int m = 16 * B, S = Slots<B>::value;
     const HalfWarp h = w.h();
+    const int c0 = t4_col(w.t);
     for (int b = w.gh; b < nrows; b += w.ghs) {
-        float2* row = G + (size_t)b * m;
+        float2* row = G + t4_row(b, m) + c0;
         float2 v[B], o[S][16];
 #pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + w.t + 16 * j);
+        for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + 64 * j);
         fft_a<B, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -330,7 +364,7 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
         }
         fft_b<B, true>(o, v, h, tw);
 #pragma unroll
-        for (int k1 = 0; k1 < B; ++k1) row[w.t + 16 * k1] = v[k1];
+        for (int k1 = 0; k1 < B; ++k1) row[64 * k1] = v[k1];
     }
     tile_sync<K>();
 }
@@ -338,7 +372,7 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
 // Columns of I - |p|^2 (n = 512; the image read transposed with tr, once, with
 // evict-first loads): Eq. 13's right-hand side F(I) - P * P is the spectrum of the
 // image minus the intensity of the known field, so p's column x is formed from the
-// band rows py0.. (nP) of GP (P's rows transformed along x on the camera grid) by an
+// band rows py0.. (nP) of the tiled grid GP (P's rows transformed along x on the camera grid) by an
 // inverse transform along y and |p|^2 kept in registers; then the chunk's 32 image
 // columns are staged through shared memory (coalesced reads), the difference is
 // formed and transformed forward along y; rows qy0.. (nQ) go to GX (row length n).
@@ -355,10 +389,11 @@ __device__ __noinline__ void wpass_image_cols_p(HWw w, const float2* tw, float2*
         const int x = c0 + w.hw;
         float2 v[BN], o[S][16];
         float q[S][16];
+        const float2* gp = GP + t4_low(w.t - py0) + t4_col(x);
 #pragma unroll
         for (int j = 0; j < BN; ++j) {
             const int bb = band_row_w(w.t + 16 * j, py0, n);
-            v[j] = bb < nP ? ldx<K>(GP + (size_t)bb * n + x) : make_float2(0.f, 0.f);
+            v[j] = bb < nP ? ldx<K>(gp + (bb & ~3) * n) : make_float2(0.f, 0.f);
         }
         fft_a<BN, true>(v, o, h, tw);               // p(x, y), y = (t + 16 s) + BN k1
 #pragma unroll
@@ -469,9 +504,9 @@ size_t dfw_smem_bytes(int max_N, int band) { return dfw_smem_layout(max_N, band)
 // of the CG grid), b on Q.
 size_t dfw_scratch_bytes(const DevPlan& P) {
     const int n = P.h;
-    size_t s = (size_t)std::max(P.band_q, P.band_p) * n;                                  // GQ
+    size_t s = (size_t)t4_rows(std::max(P.band_q, P.band_p)) * n;                         // GQ (tiled)
     s += std::max((size_t)P.max_mxy, (size_t)P.band_q * n);                               // PF / F(I) rows
-    s += (size_t)P.band_u * P.max_mx;                                                     // GU
+    s += (size_t)t4_rows(P.band_u) * P.max_mx;                                            // GU (tiled)
     s += (size_t)P.max_M;                                                                 // b on Q
     return (s * sizeof(float2) + 255) & ~(size_t)255;
 }
@@ -625,9 +660,9 @@ k_darkfield_wide(DevPlan P, int n_tiles, const float* __restrict__ I, const floa
 
     char* base = scratch + (size_t)slot * per_block;
     c.GQ = reinterpret_cast<float2*>(base);
-    c.PF = c.GQ + (size_t)max(P.band_q, P.band_p) * n;
+    c.PF = c.GQ + (size_t)t4_rows(max(P.band_q, P.band_p)) * n;
     c.GU = c.PF + max((size_t)P.max_mxy, (size_t)P.band_q * n);
-    c.bq = c.GU + (size_t)P.band_u * P.max_mx;
+    c.bq = c.GU + (size_t)t4_rows(P.band_u) * P.max_mx;
     tile_sync<K>();
 
     // one block per tile: tiles taken one at a time from the launch's counter (a block that
