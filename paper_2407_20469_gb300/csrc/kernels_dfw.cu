@@ -212,6 +212,7 @@ struct WMidStoreField {     // column-major p s (16 B values per column)
     float2* PF;
     float scale;
     static constexpr bool kOut = false;
+    static constexpr bool kPre = false;
     __device__ void operator()(float2 (&o)[Slots<B>::value][16], int x, int t) const {
         float2* col = PF + (size_t)x * (16 * B);
 #pragma unroll
@@ -226,6 +227,23 @@ template <int B, bool CONJ>
 struct WMidTimesField {     // o *= p s or conj(p s), from the column-major copy
     const float2* PF;
     static constexpr bool kOut = true;
+    // one slot (B <= 16): the column's 16 values of this lane are loaded before the
+    // forward transform (pre), so that their latency overlaps it
+    static constexpr bool kPre = Slots<B>::value == 1;
+    struct Pre {
+        float2 v[16];
+    };
+    __device__ void load(Pre& p, int x, int t) const {
+        const float2* col = PF + (size_t)x * (16 * B) + t;
+        if (t < B) {
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) p.v[k1] = col[B * k1];
+        }
+    }
+    __device__ void apply(float2 (&o)[Slots<B>::value][16], const Pre& p) const {
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) o[0][k1] = CONJ ? cmulc(o[0][k1], p.v[k1]) : cmul(o[0][k1], p.v[k1]);
+    }
     __device__ void operator()(float2 (&o)[Slots<B>::value][16], int x, int t) const {
         const float2* col = PF + (size_t)x * (16 * B);
 #pragma unroll
@@ -285,6 +303,9 @@ __device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const floa
         float2 v[B], o[S][16];
 #pragma unroll
         for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + 64 * j);
+        // the row's point range and this lane's first point, loaded before the transform
+        const int e0 = rp[b] + w.t, e1 = rp[b + 1];
+        int xn = e0 < e1 ? px[e0] : 0;
         fft_a<B, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -293,7 +314,11 @@ __device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const floa
                 for (int k1 = 0; k1 < 16; ++k1) w.hs[w.t + 16 * s + B * k1] = o[s][k1];
             }
         __syncwarp(w.mask);
-        for (int e = rp[b] + w.t; e < rp[b + 1]; e += 16) acc += out(e, w.hs[freq_index(px[e], m)]);
+        for (int e = e0; e < e1; e += 16) {
+            const int xc = xn;
+            if (e + 16 < e1) xn = px[e + 16];
+            acc += out(e, w.hs[freq_index(xc, m)]);
+        }
         __syncwarp(w.mask);
     }
     return acc;
@@ -325,8 +350,15 @@ __device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, cons
             const int bb = band_row_w(w.t + 16 * j, yi0, m);
             v[j] = bb < ni ? ldx<K>(gi + (bb & ~3) * ldi) : make_float2(0.f, 0.f);
         }
-        fft_a<B, true>(v, o, h, tw);
-        mid(o, x, w.t);
+        if constexpr (Mid::kPre) {
+            typename Mid::Pre pre;
+            mid.load(pre, x, w.t);
+            fft_a<B, true>(v, o, h, tw);
+            mid.apply(o, pre);
+        } else {
+            fft_a<B, true>(v, o, h, tw);
+            mid(o, x, w.t);
+        }
         if constexpr (Mid::kOut) {
             fft_b<B, false>(o, v, h, tw);
             float2* go = Go + lo + t4_col(x);
@@ -353,11 +385,14 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
         float2 v[B], o[S][16];
 #pragma unroll
         for (int j = 0; j < B; ++j) v[j] = ldx<K>(row + 64 * j);
+        unsigned qw[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) qw[s] = qmask[(size_t)b * kWQWords + ((w.t + 16 * s) >> 1)];
         fft_a<B, false>(v, o, h, tw);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const int ls = w.t + 16 * s;
-            const unsigned bits = qmask[(size_t)b * kWQWords + (ls >> 1)] >> (16 * (ls & 1));
+            const unsigned bits = qw[s] >> (16 * (ls & 1));
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1)
                 if (!((bits >> k1) & 1u)) o[s][k1] = make_float2(0.f, 0.f);
