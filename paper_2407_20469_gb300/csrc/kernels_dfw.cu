@@ -37,6 +37,7 @@
 #include "../../include/apic.h"
 #include "internal.cuh"
 #include "regfft.cuh"
+#include "t4grid.cuh"
 
 namespace apic {
 
@@ -62,30 +63,6 @@ __device__ __forceinline__ int band_row_w(int i, int y0, int m) {
     if (r < 0) r += m;
     return r;
 }
-
-// Band grids in 4 x 4 tiles: element (r, c) of a grid with ncols columns (a multiple
-// of 4; rows allocated in groups of 4) sits in the 128-byte line of tile (r / 4, c / 4),
-// in its 32-byte sector of rows 2 (r / 2) .. +1 and columns 2 (c / 2) .. +1. A warp's two
-// half-warps read or write two adjacent rows over 16 columns (rows passes: rows 2 w' and
-// 2 w' + 1) or two adjacent columns over 16 rows (columns passes): either way 4 or 5
-// lines per instruction and every loaded sector fully used, where a row-major grid
-// gives the columns passes 16 lines and half-used sectors per instruction.
-// t4_index(r, c) = t4_row(r, ncols) + t4_col(c); adding 4 k to c adds 16 k.
-__device__ __forceinline__ int t4_low(int r) { return ((r & 2) << 2) + ((r & 1) << 1); }
-__device__ __forceinline__ int t4_row(int r, int ncols) { return (r & ~3) * ncols + t4_low(r); }
-__device__ __forceinline__ int t4_col(int c) { return ((c & ~3) << 2) + ((c & 2) << 1) + (c & 1); }
-__host__ __device__ inline int t4_rows(int rows) { return (rows + 3) & ~3; }
-
-// Offset of column t + m of a row (lane t; m known after unrolling): the lane's four
-// column offsets c4[q] = t4_col(t + q) and a multiple of 16.
-struct T4Lane {
-    int c0, c1, c2, c3;
-    __device__ explicit T4Lane(int t) : c0(t4_col(t)), c1(t4_col(t + 1)), c2(t4_col(t + 2)), c3(t4_col(t + 3)) {}
-    __device__ __forceinline__ int at(int m) const {
-        const int q = m & 3;
-        return (q == 0 ? c0 : q == 1 ? c1 : q == 2 ? c2 : c3) + 4 * (m & ~3);
-    }
-};
 
 // Half-warp of a cluster: t lane, hw index in the block, gh index in the cluster
 // (rank x 32 + hw), ghs half-warps in the cluster.

@@ -3,8 +3,9 @@
 // wide form, two step-B rows per lane).
 //
 // One block per (tile, NA-matching image) problem, persistent over problems;
-// an n x n complex scratch grid per block (L2-resident). Each half-warp
-// transforms one row or column at a time:
+// an n x n complex scratch grid per block (L2-resident; HBM at n = 512), stored in
+// 4 x 4 tiles (t4grid.cuh) so that the column passes move whole sectors. Each
+// half-warp transforms one row or column at a time:
 //   P1 rows: log(max(I, 1e-6 mean I)), forward transform along x
 //   P2 cols: forward along y, half-plane mask of Eq. 5, inverse along y
 //   P3 rows: inverse along x, / n^2, exp (Eq. 6), forward along x; only the
@@ -22,6 +23,7 @@
 #include "../../include/apic.h"
 #include "internal.cuh"
 #include "regfft.cuh"
+#include "t4grid.cuh"
 
 namespace apic {
 
@@ -54,6 +56,8 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
     const int hw = threadIdx.x >> 4, t = threadIdx.x & 15;
     const HalfWarp h{t, (threadIdx.x & 16) ? 0xFFFF0000u : 0x0000FFFFu, hw_area + hw * HWS};
     float2* G = scratch + (size_t)blockIdx.x * n * n;
+    const T4Lane L(t);
+    const int lrow = t4_row(t, n), lcol = t4_col(t);      // this lane's row / column offsets
     const float inv_n2 = 1.0f / (float)(n * n);
     const long long hh = (long long)P.h * P.h, ww = (long long)P.w * P.w;
     const int nprob = n_tiles * P.n_bf;
@@ -82,20 +86,21 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
             for (int j = 0; j < BN; ++j)      // last read of the image: evict first from L2
                 v[j] = make_float2(__logf(fmaxf(__ldcs(row + t + 16 * j), eps)), 0.f);
             fft_a<BN, false>(v, o, h, tw);
-            float2* gr = G + (size_t)r * n;
+            float2* gr = G + t4_row(r, n);
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 if (t + 16 * s < BN) {
 #pragma unroll
-                    for (int k1 = 0; k1 < 16; ++k1) gr[t + 16 * s + BN * k1] = o[s][k1];
+                    for (int k1 = 0; k1 < 16; ++k1) gr[L.at(16 * s + BN * k1)] = o[s][k1];
                 }
         }
         __syncthreads();
         // P2: columns, forward along y, Eq. 5 mask, inverse along y
         for (int x = hw; x < n; x += kKKHW) {
             float2 v[BN], o[S][16];
+            float2* gc = G + lrow + t4_col(x);              // rows t + 16 j of column x
 #pragma unroll
-            for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * n + x];
+            for (int j = 0; j < BN; ++j) v[j] = gc[16 * j * n];
             fft_a<BN, false>(v, o, h, tw);
             const long long kxp = (long long)sfreq_kk(x, n) * kix * hh;
 #pragma unroll
@@ -110,7 +115,7 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
                 }
             fft_b<BN, true>(o, v, h, tw);
 #pragma unroll
-            for (int k1 = 0; k1 < BN; ++k1) G[(size_t)(t + 16 * k1) * n + x] = v[k1];
+            for (int k1 = 0; k1 < BN; ++k1) gc[16 * k1 * n] = v[k1];
         }
         __syncthreads();
         // only the spectrum at K = k_p - k_i (|k_p| within the pupil box) is gathered:
@@ -119,10 +124,10 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
         const int ky0 = -P.pup_ay - kiy, nby = 2 * P.pup_ay + 1;
         // P3: rows, inverse along x, exp, forward along x; the band columns are stored
         for (int r = hw; r < n; r += kKKHW) {
-            float2* gr = G + (size_t)r * n;
+            float2* gr = G + t4_row(r, n) + lcol;           // columns t + 16 j of row r
             float2 v[BN], o[S][16];
 #pragma unroll
-            for (int j = 0; j < BN; ++j) v[j] = gr[t + 16 * j];
+            for (int j = 0; j < BN; ++j) v[j] = gr[64 * j];
             fft_a<BN, true>(v, o, h, tw);
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -140,7 +145,7 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
 #pragma unroll
             for (int k1 = 0; k1 < BN; ++k1) {
                 const int x = t + 16 * k1;
-                if ((unsigned)(sfreq_kk(x, n) - kx0 + n) % (unsigned)n < (unsigned)nbx) gr[x] = v[k1];
+                if ((unsigned)(sfreq_kk(x, n) - kx0 + n) % (unsigned)n < (unsigned)nbx) gr[64 * k1] = v[k1];
             }
         }
         __syncthreads();
@@ -148,8 +153,10 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
         for (int c = hw; c < nbx; c += kKKHW) {
             const int x = freq_index(kx0 + c, n);
             float2 v[BN], o[S][16];
+            const int cx = t4_col(x);
+            const float2* gc = G + lrow + cx;
 #pragma unroll
-            for (int j = 0; j < BN; ++j) v[j] = G[(size_t)(t + 16 * j) * n + x];
+            for (int j = 0; j < BN; ++j) v[j] = gc[16 * j * n];
             fft_a<BN, false>(v, o, h, tw);
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -158,7 +165,7 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
                     for (int k1 = 0; k1 < 16; ++k1) {
                         const int y = t + 16 * s + BN * k1;
                         if ((unsigned)(sfreq_kk(y, n) - ky0 + n) % (unsigned)n < (unsigned)nby)
-                            G[(size_t)y * n + x] = cscale(o[s][k1], inv_n2);
+                            G[t4_row(y, n) + cx] = cscale(o[s][k1], inv_n2);
                     }
                 }
         }
@@ -166,7 +173,7 @@ k_kk_reg(DevPlan P, int n_tiles, const float* __restrict__ I, float2* __restrict
         float2* out = xdisc + ((size_t)tile * P.n_bf + i) * P.npup;
         for (int p = threadIdx.x; p < P.npup; p += blockDim.x) {
             const int Kx = P.pup_x[p] - kix, Ky = P.pup_y[p] - kiy;
-            out[p] = G[(size_t)freq_index(Ky, n) * n + freq_index(Kx, n)];
+            out[p] = G[t4_index(freq_index(Ky, n), freq_index(Kx, n), n)];
         }
         __syncthreads();
     }
