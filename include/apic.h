@@ -245,16 +245,20 @@ apic_status apic_plan_timing(apic_plan* plan, int enable);
 apic_status apic_plan_stage_ms(apic_plan* plan, double* h_ms, int n, int32_t* h_calls, int reset);
 
 /*
- * apic_reconstruct_batch from and to HOST memory, pipelined. A batch that fits
- * one chunk (up to four GPU-wide darkfield waves and max_tiles) has its copies
- * woven into the reconstruction's own order: the partial wave's intensities
- * first, the others in parts whose earlier stages start as each part lands,
- * and every darkfield round's fields copied out as soon as they are
- * synthesized. Larger batches go in chunks (the first one wave, the rest up to
- * four waves or max_tiles): while one chunk is reconstructed the next chunk's
- * intensities are copied in and the previous chunk's results copied out.
- * Three internal streams and two sets of device staging buffers, allocated on
- * first use and kept. For the copies to overlap the host buffers must be
+ * apic_reconstruct_batch from and to HOST memory, pipelined. A batch of up to
+ * max_tiles tiles that has a partial GPU-wide darkfield wave (or fits four
+ * waves) is one chunk with its copies woven into the reconstruction's own
+ * order: the partial wave's intensities first, the others in up to 16 parts
+ * whose earlier stages start as each part lands, and every darkfield round's
+ * fields copied out as soon as they are synthesized (the first 32 rounds; the
+ * rest when the computation ends). Other batches go in chunks (the first one
+ * wave, the rest up to four waves or max_tiles): while one chunk is
+ * reconstructed the next chunk's intensities are copied in and the previous
+ * chunk's results copied out. Three internal streams; device staging buffers
+ * allocated on first use and kept: one set for max_tiles tiles (inputs,
+ * fields, coefficients, status) when that leaves a quarter of the free device
+ * memory (at least 1 GiB), else for one chunk (then every batch is chunked),
+ * and a second set of one chunk once a batch is chunked. For the copies to overlap the host buffers must be
  * pinned (cudaHostAlloc / cudaHostRegister); pageable buffers work but
  * serialise. Returns when all results are in host memory.
  *   h_intensity [n_tiles][n_bf + n_df][h][w] f32, h_field [n_tiles][u h][u w]

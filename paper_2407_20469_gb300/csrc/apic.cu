@@ -102,12 +102,14 @@ struct apic_plan {
     // host-buffer pipeline (apic_reconstruct_host), created on first use
     struct HostIO {
         bool ready = false;
-        int chunk = 0;
+        int chunk = 0;           // tiles per chunk of the chunked order (buffer sets 0 and 1)
+        int one = 0;             // tiles buffer set 0 holds: calls of up to `one` tiles take the one-chunk order
+        int cap[2] = {0, 0};     // tiles each buffer set holds (0: not allocated)
         cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
         cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
         cudaEvent_t in_tail = nullptr, early = nullptr;   // one-chunk order
-        cudaEvent_t part[8] = {};                          // one-chunk order: the full waves' inputs in parts
-        cudaEvent_t rdone[4] = {};                         // one-chunk order: fields of the first group's rounds
+        cudaEvent_t part[16] = {};                         // one-chunk order: the full waves' inputs in parts
+        cudaEvent_t rdone[32] = {};                        // one-chunk order: fields of the first group's rounds
         cudaEvent_t ml_done = nullptr;                     // one-chunk order: fields of the second group's early rounds
         float* d_in[2] = {};
         float* d_field[2] = {};
@@ -121,6 +123,10 @@ struct apic_plan {
     // second stream for the last partial darkfield wave of a batch (see reconstruct)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tail = nullptr, ev_pre = nullptr, ev_mbe = nullptr;
+    // inputs arriving per group of darkfield rounds (host pipeline): the groups' earlier
+    // stages on a stream of their own, one event per group
+    cudaStream_t prep = nullptr;
+    cudaEvent_t ev_prep[16] = {};
     float* feat = nullptr;                       // learned path: features, network coefficients
     float* c_net = nullptr;
     unsigned long long* d_counters = nullptr;   // kCounters: [1] CG iterations, [2] solves, [4 + i] per image
@@ -478,6 +484,8 @@ apic_status alloc_workspace(apic_plan* p) {
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_tail, cudaEventDisableTiming));
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_pre, cudaEventDisableTiming));
     APIC_TRY_CUDA(cudaEventCreateWithFlags(&p->ev_mbe, cudaEventDisableTiming));
+    APIC_TRY_CUDA(cudaStreamCreateWithPriority(&p->prep, cudaStreamNonBlocking, greatest));
+    for (auto& e : p->ev_prep) APIC_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return APIC_OK;
 }
 
@@ -559,9 +567,9 @@ struct StageTimer {
         p->t_next = (p->t_next + 1) % apic_plan::kTimingSlots;
         p->t_used = std::min(p->t_used + 1, apic_plan::kTimingSlots);
     }
-    void mark(int stage, int end) {
+    void mark(int stage, int end, cudaStream_t on = nullptr) {     // on: another stream of the call
         if (slot < 0) return;
-        cudaEventRecord(p->events[((size_t)slot * apic_plan::kStages + stage) * 2 + end], st);
+        cudaEventRecord(p->events[((size_t)slot * apic_plan::kStages + stage) * 2 + end], on ? on : st);
     }
 };
 
@@ -587,16 +595,18 @@ apic_status learned_buffers(apic_plan* p) {
 // = [m0, nt) after round 0; ml_ready (when set; then on the second stream) once
 // those of ML = [ma, ml) are; the fields [ml, m0) are synthesized last. Without
 // ml_ready ML is synthesized after MA's last round. With parts > 0 (split order
-// only) the full waves' tiles arrive in parts: tiles [part_end[g - 1],
-// part_end[g]) are ready at part_ready[g], and each part's earlier stages start
-// as soon as it is in.
+// only) the full waves' tiles arrive in parts of whole darkfield rounds: part g
+// holds rounds [part_rounds[g - 1], part_rounds[g]) of both groups (MA's tiles
+// [k wa, (k + 1) wa) and MB's [ma + k r, ma + (k + 1) r) for each round k), ready
+// at part_ready[g]; each part's earlier stages run on a stream of their own as
+// soon as it is in, and each round starts once its part's earlier stages end.
 struct SplitHooks {
-    static constexpr int kMaxParts = 8;    // = the host pipeline's part events
-    static constexpr int kMaxRounds = 4;   // = the host pipeline's round events
+    static constexpr int kMaxParts = 16;   // = the host pipeline's part events
+    static constexpr int kMaxRounds = 32;  // = the host pipeline's round events
     cudaEvent_t wait_main = nullptr;
     cudaEvent_t early_done = nullptr;
     int parts = 0;
-    int part_end[kMaxParts] = {};
+    int part_rounds[kMaxParts] = {};
     cudaEvent_t part_ready[kMaxParts] = {};
     cudaEvent_t field_ready[kMaxRounds] = {};
     cudaEvent_t ml_ready = nullptr;
@@ -654,6 +664,7 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
         // full waves' earlier stages then never hold an SM the partial wave's darkfield
         // blocks are about to take (a persistent block keeps its SM for milliseconds)
         bool pre_first = true;
+        cudaStream_t ps = st;       // stream of the earlier stages (the caller's, or the parts' own)
         auto pre_df = [&](int a, int k, bool final, int cap) -> apic_status {
             if (k == 0) return APIC_OK;
             const bool mark0 = first && pre_first, mark1 = last && final;
@@ -663,17 +674,17 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             Launch La = L;
             if (cap > 0) La.grid_ab = std::min(L.grid_ab, 2 * cap);
             if (mark0) tm.mark(1, 0);
-            APIC_TRY_LAUNCH(launch_kk_any(plan, cap, k, It + (size_t)a * in_tile, xd, plan->kk_scratch, stt + a, st));
-            if (mark1) tm.mark(1, 1);
+            APIC_TRY_LAUNCH(launch_kk_any(plan, cap, k, It + (size_t)a * in_tile, xd, plan->kk_scratch, stt + a, ps));
+            if (mark1) tm.mark(1, 1, ps);
             if (mark0) tm.mark(2, 0);
             APIC_TRY_LAUNCH(launch_aberration(D, La, k, xd, zt + (size_t)a * APIC_N_ZERNIKE, plan->beta_scratch,
-                                              plan->ab_passes, stt + a, st,
+                                              plan->ab_passes, stt + a, ps,
                                               net ? plan->c_net + (size_t)a * APIC_N_ZERNIKE : nullptr, warm ? 1 : 0));
-            if (mark1) tm.mark(2, 1);
+            if (mark1) tm.mark(2, 1, ps);
             if (mark0) tm.mark(3, 0);
-            APIC_TRY_LAUNCH(launch_phase(D, k, zt + (size_t)a * APIC_N_ZERNIKE, ph, st));
-            APIC_TRY_LAUNCH(launch_stitch(D, k, xd, ph, plan->spec + (size_t)a * D.nap, stt + a, st));
-            if (mark1) tm.mark(3, 1);
+            APIC_TRY_LAUNCH(launch_phase(D, k, zt + (size_t)a * APIC_N_ZERNIKE, ph, ps));
+            APIC_TRY_LAUNCH(launch_stitch(D, k, xd, ph, plan->spec + (size_t)a * D.nap, stt + a, ps));
+            if (mark1) tm.mark(3, 1, ps);
             return APIC_OK;
         };
         // network coefficients of tiles [a, a + k) of the chunk (learned path)
@@ -681,14 +692,14 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             if (!net || k == 0) return APIC_OK;
             float* feat = plan->feat + (size_t)a * feature_floats();
             const int fgrid = cap > 0 ? std::min(cap, plan->grid_kkr) : plan->grid_kkr;
-            APIC_TRY_LAUNCH(launch_features(D, fgrid, k, It + (size_t)a * in_tile, feat, plan->kk_scratch, st));
+            APIC_TRY_LAUNCH(launch_features(D, fgrid, k, It + (size_t)a * in_tile, feat, plan->kk_scratch, ps));
             const int nb = net_max_batch(net);
             for (int b0 = 0; b0 < k; b0 += nb) {
                 const int bn = std::min(nb, k - b0);
                 const long long before = net_launches(net);
                 APIC_TRY_CUDA(net_predict(net, bn, feat + (size_t)b0 * feature_floats(),
                                           uv + (size_t)(t0 + a + b0) * 2,
-                                          plan->c_net + (size_t)(a + b0) * APIC_N_ZERNIKE, st));
+                                          plan->c_net + (size_t)(a + b0) * APIC_N_ZERNIKE, ps));
                 plan->launches += net_launches(net) - before;
             }
             return APIC_OK;
@@ -716,27 +727,55 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)m0 * in_tile, plan->phi + (size_t)m0 * D.npup,
                                          plan->spec + (size_t)m0 * D.nap, stt + m0, true, plan->side, r));
             APIC_TRY_CUDA(cudaEventRecord(plan->ev_tail, plan->side));
-            const int parts = hk && hk->parts > 0 ? hk->parts : 1;
-            for (int g = 0, a = 0; g < parts; ++g) {
-                const int b = hk && hk->parts > 0 ? hk->part_end[g] : m0;
-                if (hk && hk->parts > 0) {
-                    APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->part_ready[g], 0));
-                } else if (hk && hk->wait_main) {
-                    APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
-                }
+            const int wa = W - r, rounds = m0 / W;
+            // earlier stages of tiles [a, b) on stream ps (after the full waves' inputs, or
+            // a part of them, are in)
+            auto full_pre = [&](int a, int b, bool final) -> apic_status {
                 APIC_TRY_LAUNCH(launch_background(D, b - a, It + (size_t)a * in_tile, plan->c2 + a, stt + a, thresh2,
-                                                  st, replace ? 1 : 0));
-                if (last && g == parts - 1) tm.mark(0, 1);
-                if ((s = learned_part(a, b - a, df_sms(plan, W - r))) != APIC_OK) return s;
-                if ((s = pre_df(a, b - a, g == parts - 1, df_sms(plan, W - r))) != APIC_OK) return s;
-                a = b;
+                                                  ps, replace ? 1 : 0));
+                if (last && final) tm.mark(0, 1, ps);
+                apic_status q;
+                if ((q = learned_part(a, b - a, df_sms(plan, W - r))) != APIC_OK) return q;
+                return pre_df(a, b - a, final, df_sms(plan, W - r));
+            };
+            const bool rparts = hk && hk->parts > 0;
+            int round_part[SplitHooks::kMaxRounds] = {};     // part of each round (round parts)
+            if (rparts) {
+                if (hk->parts > SplitHooks::kMaxParts || hk->part_rounds[hk->parts - 1] != rounds)
+                    return fail(APIC_EINTERNAL, "input parts do not cover the darkfield rounds");
+                if (rounds > SplitHooks::kMaxRounds) return fail(APIC_EINTERNAL, "too many darkfield rounds for parts");
+                // the shared KK / aberration scratch: after the partial wave's earlier stages
+                APIC_TRY_CUDA(cudaStreamWaitEvent(plan->prep, plan->ev_fork, 0));
+                ps = plan->prep;
+                for (int g = 0, k0 = 0; g < hk->parts; ++g) {
+                    const int k1 = hk->part_rounds[g];
+                    APIC_TRY_CUDA(cudaStreamWaitEvent(ps, hk->part_ready[g], 0));
+                    const bool fin = g == hk->parts - 1;
+                    if ((s = full_pre(k0 * wa, k1 * wa, false)) != APIC_OK) return s;
+                    if ((s = full_pre(ma + k0 * r, ma + k1 * r, fin)) != APIC_OK) return s;
+                    APIC_TRY_CUDA(cudaEventRecord(plan->ev_prep[g], ps));
+                    for (int k = k0; k < k1; ++k) round_part[k] = g;
+                    k0 = k1;
+                }
+                ps = st;
+            } else {
+                if (hk && hk->wait_main) APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
+                if ((s = full_pre(0, m0, true)) != APIC_OK) return s;
+                APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
+                APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_pre, 0));
             }
-            APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
-            APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_pre, 0));
+            // a round waits for its part's earlier stages (round parts), once per part
+            auto round_ready = [&](cudaStream_t x, int k, int& seen) -> cudaError_t {
+                if (!rparts || round_part[k] == seen) return cudaSuccess;
+                seen = round_part[k];
+                return cudaStreamWaitEvent(x, plan->ev_prep[seen], 0);
+            };
+            int seen_b = -1, seen_a = -1;
             // MB one round (r tiles, one per block) per launch: the rounds before the
             // last are synthesized on the caller's stream with MA, so that only the
             // last round's fields remain once the second stream ends
             for (int a = ma; a < m0; a += r) {
+                APIC_TRY_CUDA(round_ready(plan->side, (a - ma) / r, seen_b));
                 APIC_TRY_LAUNCH(launch_df_on(plan, r, It + (size_t)a * in_tile, plan->phi + (size_t)a * D.npup,
                                              plan->spec + (size_t)a * D.nap, stt + a, true, plan->side, r));
                 if (a + r == ml) {
@@ -754,8 +793,8 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             // MA one round (W - r tiles, one per block) per launch, each round's fields
             // synthesized right after it (T's after the first round, [ma, ml) after the
             // last), so that a host pipeline can copy them out while the rest runs
-            const int wa = W - r;
             for (int a = 0, k = 0; a < ma; a += wa, ++k) {
+                APIC_TRY_CUDA(round_ready(st, k, seen_a));
                 APIC_TRY_LAUNCH(launch_df_on(plan, wa, It + (size_t)a * in_tile, plan->phi + (size_t)a * D.npup,
                                              plan->spec + (size_t)a * D.nap, stt + a, false, st, wa));
                 if (first && k == 0) tm.mark(5, 0);
@@ -928,6 +967,9 @@ apic_status apic_plan_destroy(apic_plan* plan) {
         if (plan->ev_tail) cudaEventDestroy(plan->ev_tail);
         if (plan->ev_pre) cudaEventDestroy(plan->ev_pre);
         if (plan->ev_mbe) cudaEventDestroy(plan->ev_mbe);
+        for (cudaEvent_t e : plan->ev_prep)
+            if (e) cudaEventDestroy(e);
+        if (plan->prep) cudaStreamDestroy(plan->prep);
         auto& io = plan->io;
         for (int b = 0; b < 2; ++b) {
             if (io.in_done[b]) cudaEventDestroy(io.in_done[b]);
@@ -1278,15 +1320,40 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
     const DevPlan& D = plan->dev;
     const size_t in_tile = (size_t)D.n_img * D.h * D.w, out_tile = (size_t)D.H * D.W;
     auto& io = plan->io;
-    // chunk sizes follow the darkfield grid (one tile per block): the first chunk
-    // is one full wave so computation starts after a short copy, the rest go in
-    // chunks of up to four waves; the total number of waves matches one batch.
+    // A call of up to io.one tiles (normally max_tiles: the whole call's inputs and
+    // fields fit on the device beside the plan) takes the one-chunk order: inputs copy
+    // in parts while the earlier stages of the parts already in run, and each darkfield
+    // round's fields copy out once synthesized, so the copies hide behind the
+    // computation. Larger calls (or when device memory is short) go in chunks that
+    // follow the darkfield grid (one tile per block): the first chunk one full wave so
+    // that computation starts after a short copy, the rest up to four waves, double
+    // buffered.
     const int wave = df_wave(plan);
-    const int max_chunk = std::max(1, std::min(plan->max_tiles, 4 * wave));
+    auto buffers = [&](int b, int C) -> apic_status {      // buffer set b for C tiles, once
+        if (io.cap[b] >= C) return APIC_OK;
+        if (io.cap[b] > 0) return fail(APIC_EINTERNAL, "host pipeline buffers already sized");
+        void* q[4] = {};
+        const size_t bytes[4] = {(size_t)C * in_tile * sizeof(float), (size_t)C * out_tile * sizeof(float2),
+                                 (size_t)C * APIC_N_ZERNIKE * sizeof(float), (size_t)C * sizeof(int32_t)};
+        for (int i = 0; i < 4; ++i) {
+            const apic_status r = dmalloc(plan, &q[i], bytes[i]);
+            if (r != APIC_OK) {          // all or nothing: a later call may try again
+                for (int j = 0; j < i; ++j) {
+                    cudaFree(q[j]);
+                    plan->allocs.erase(std::find(plan->allocs.begin(), plan->allocs.end(), q[j]));
+                }
+                return r;
+            }
+        }
+        io.d_in[b] = (float*)q[0];
+        io.d_field[b] = (float*)q[1];
+        io.d_zern[b] = (float*)q[2];
+        io.d_status[b] = (int32_t*)q[3];
+        io.cap[b] = C;
+        return APIC_OK;
+    };
     if (!io.ready) {
         // each object is made once: a set-up that failed part way resumes where it stopped
-        io.chunk = max_chunk;
-        const size_t C = (size_t)io.chunk;
         auto stream = [](cudaStream_t& x) {
             return x ? cudaSuccess : cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
         };
@@ -1305,26 +1372,33 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
             APIC_TRY_CUDA(event(io.in_done[b]));
             APIC_TRY_CUDA(event(io.comp_done[b]));
             APIC_TRY_CUDA(event(io.out_done[b]));
-            if (!io.d_in[b] && (s = dmalloc(plan, (void**)&io.d_in[b], C * in_tile * sizeof(float))) != APIC_OK)
-                return s;
-            if (!io.d_field[b] &&
-                (s = dmalloc(plan, (void**)&io.d_field[b], C * out_tile * sizeof(float2))) != APIC_OK)
-                return s;
-            if (!io.d_zern[b] &&
-                (s = dmalloc(plan, (void**)&io.d_zern[b], C * APIC_N_ZERNIKE * sizeof(float))) != APIC_OK)
-                return s;
-            if (!io.d_status[b] && (s = dmalloc(plan, (void**)&io.d_status[b], C * sizeof(int32_t))) != APIC_OK)
-                return s;
         }
+        io.chunk = std::max(1, std::min(plan->max_tiles, 4 * wave));
+        if (io.cap[0] == 0) {
+            // buffer set 0 for max_tiles tiles where that leaves a quarter of the free
+            // memory (and at least 1 GiB) to others, else for one chunk
+            const size_t per_tile = in_tile * sizeof(float) + out_tile * sizeof(float2) +
+                                    APIC_N_ZERNIKE * sizeof(float) + sizeof(int32_t);
+            size_t fr = 0, tot = 0;
+            APIC_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
+            const size_t need = (size_t)plan->max_tiles * per_tile;
+            const size_t keep = std::max(fr / 4, (size_t)1 << 30);
+            const int C0 = fr > keep && need <= fr - keep ? plan->max_tiles : io.chunk;
+            if ((s = buffers(0, C0)) != APIC_OK) return s;
+        }
+        io.one = io.cap[0];
         io.ready = true;
     }
-    if (n_tiles <= io.chunk) {
+    int r = 0, m0 = n_tiles, ma = n_tiles, ml = n_tiles;
+    split_geometry(plan, n_tiles, r, m0, ma, ml);
+    const bool one_order = r > 0 ? m0 / wave <= SplitHooks::kMaxRounds : n_tiles <= io.chunk;
+    if (n_tiles <= io.one && one_order) {
         // One chunk, copies woven into its order: the partial darkfield wave's
         // inputs go first and its stages start while the other inputs copy; each
         // darkfield round's fields copy out as soon as they are synthesized, so that
-        // only the last round's remain once the computation ends.
-        int r = 0, m0 = n_tiles, ma = n_tiles, ml = n_tiles;
-        split_geometry(plan, n_tiles, r, m0, ma, ml);
+        // only the last round's remain once the computation ends. (A whole number of
+        // waves beyond one chunk has no partial wave to start with, and more rounds
+        // than the round events cannot be followed: chunked order.)
         float* dI = io.d_in[0];
         float* dF = io.d_field[0];
         const size_t fbytes = out_tile * sizeof(float2);
@@ -1334,27 +1408,29 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
             APIC_TRY_CUDA(cudaMemcpyAsync(dI + (size_t)m0 * in_tile, h_I + (size_t)m0 * in_tile,
                                           (size_t)r * in_tile * sizeof(float), cudaMemcpyHostToDevice, io.s_in));
             APIC_TRY_CUDA(cudaEventRecord(io.in_tail, io.s_in));
-            // the full waves' tiles in parts of about a third of a wave, so that each
-            // part's earlier stages overlap the copies of the next and little is left
-            // to prepare once the last part is in
+            // the full waves' tiles in parts of whole darkfield rounds, in the order the
+            // rounds run (each round: W - r tiles of the first group, r of the second), so
+            // that a round starts once its part is in and prepared while later parts copy
             static_assert(sizeof(io.part) / sizeof(io.part[0]) == SplitHooks::kMaxParts, "one event per part");
             static_assert(sizeof(io.rdone) / sizeof(io.rdone[0]) == SplitHooks::kMaxRounds, "one event per round");
-            const int parts = std::min(SplitHooks::kMaxParts, std::max(1, (3 * m0 + wave - 1) / wave));
-            for (int g = 0, a = 0; g < parts; ++g) {
-                const int b = (int)((long long)m0 * (g + 1) / parts);
-                APIC_TRY_CUDA(cudaMemcpyAsync(dI + (size_t)a * in_tile, h_I + (size_t)a * in_tile,
-                                              (size_t)(b - a) * in_tile * sizeof(float), cudaMemcpyHostToDevice,
-                                              io.s_in));
+            static_assert(sizeof(plan->ev_prep) / sizeof(plan->ev_prep[0]) == SplitHooks::kMaxParts, "one per part");
+            const int rounds = m0 / wave, wa = wave - r;
+            const int parts = std::min(SplitHooks::kMaxParts, rounds);
+            auto copy_in = [&](int a, int b) -> cudaError_t {
+                return cudaMemcpyAsync(dI + (size_t)a * in_tile, h_I + (size_t)a * in_tile,
+                                       (size_t)(b - a) * in_tile * sizeof(float), cudaMemcpyHostToDevice, io.s_in);
+            };
+            for (int g = 0, k0 = 0; g < parts; ++g) {
+                const int k1 = (int)((long long)rounds * (g + 1) / parts);
+                APIC_TRY_CUDA(copy_in(k0 * wa, k1 * wa));
+                APIC_TRY_CUDA(copy_in(ma + k0 * r, ma + k1 * r));
                 APIC_TRY_CUDA(cudaEventRecord(io.part[g], io.s_in));
-                hk.part_end[g] = b;
+                hk.part_rounds[g] = k1;
                 hk.part_ready[g] = io.part[g];
-                a = b;
+                k0 = k1;
             }
             hk.parts = parts;
-            for (int k = 0; k < m0 / wave; ++k) {
-                if (k >= SplitHooks::kMaxRounds) return fail(APIC_EINTERNAL, "too many darkfield rounds in a chunk");
-                hk.field_ready[k] = io.rdone[k];
-            }
+            for (int k = 0; k < std::min(m0 / wave, SplitHooks::kMaxRounds); ++k) hk.field_ready[k] = io.rdone[k];
             hk.ml_ready = io.ml_done;
         } else {
             APIC_TRY_CUDA(cudaMemcpyAsync(dI, h_I, (size_t)m0 * in_tile * sizeof(float), cudaMemcpyHostToDevice,
@@ -1373,9 +1449,10 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
         };
         if (r > 0) {
             // in the order the fields become ready: MA's rounds, ML (second stream) before
-            // MA's last round, then the second group's last round
-            const int rounds = m0 / wave, wa = wave - r;
-            for (int k = 0; k < rounds; ++k) {
+            // MA's last round, then the second group's last round (rounds past the
+            // round events: with the rest, once the computation ends)
+            const int rounds = m0 / wave, wa = wave - r, ev_rounds = std::min(rounds, SplitHooks::kMaxRounds);
+            for (int k = 0; k < ev_rounds; ++k) {
                 if (k == rounds - 1 && ml > ma) {
                     APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.ml_done, 0));
                     APIC_TRY_CUDA(fields_out(ma, ml - ma));
@@ -1385,6 +1462,10 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
                 if (k == 0) APIC_TRY_CUDA(fields_out(m0, r));
             }
             APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.comp_done[0], 0));
+            if (ev_rounds < rounds) {
+                APIC_TRY_CUDA(fields_out(ev_rounds * wa, ma - ev_rounds * wa));
+                if (ml > ma) APIC_TRY_CUDA(fields_out(ma, ml - ma));
+            }
             APIC_TRY_CUDA(fields_out(ml, m0 - ml));
         } else {
             APIC_TRY_CUDA(cudaStreamWaitEvent(io.s_out, io.early, 0));
@@ -1400,6 +1481,7 @@ apic_status apic_reconstruct_host(apic_plan* plan, int n_tiles, const float* h_I
         APIC_TRY_CUDA(cudaStreamSynchronize(io.s_comp));
         return host_status_word(h_status, n_tiles);
     }
+    if ((s = buffers(0, io.chunk)) != APIC_OK || (s = buffers(1, io.chunk)) != APIC_OK) return s;
     int k = 0;
     for (int t0 = 0, nt = 0; t0 < n_tiles; t0 += nt, ++k) {
         nt = std::min(k == 0 ? std::min(wave, io.chunk) : io.chunk, n_tiles - t0);

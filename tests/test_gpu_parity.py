@@ -458,10 +458,10 @@ def test_background_statistic_matches_oracle():
 
 def test_reconstruct_host_with_partial_waves_matches_device_path():
     """The host-buffer pipeline over chunks that contain partial darkfield waves
-    (second stream forked from its compute stream) returns the device result bit
-    for bit."""
+    (second stream forked from its compute stream; a batch larger than max_tiles
+    is always chunked) returns the device result bit for bit."""
     n, T = 64, 1000
-    plan = new_plan(n, max_tiles=T)
+    plan = new_plan(n, max_tiles=400)
     from paper_2407_20469_gb300 import learn
     zern = torch.zeros((T, 15), dtype=torch.float32, device="cuda")
     zern[:, 3:] = torch.as_tensor(np.resize(np.linspace(-0.4, 0.4, 12, dtype=np.float32), (T, 12)), device="cuda")
@@ -482,11 +482,13 @@ def test_reconstruct_host_with_partial_waves_matches_device_path():
     assert torch.equal(s_h, s_d.cpu()) and torch.equal(z_h, z_d.cpu()) and torch.equal(f_h, f_d.cpu())
 
 
-def test_reconstruct_host_one_chunk_split_matches_device_path():
-    """One chunk (n_tiles <= the pipeline chunk) with a partial darkfield wave: the
-    inputs copy in two parts and the fields out in two parts around the split
-    order; the result equals the device path bit for bit."""
-    n, T = 64, 500
+@pytest.mark.parametrize("T", [500, 2000])
+def test_reconstruct_host_one_chunk_split_matches_device_path(T):
+    """One chunk (n_tiles <= max_tiles) with a partial darkfield wave: the inputs
+    copy in parts and the fields out per darkfield round around the split order
+    (2000 tiles of 64: more than four rounds); the result equals the device path
+    bit for bit."""
+    n = 64
     plan = new_plan(n, max_tiles=T)
     from paper_2407_20469_gb300 import learn
     zern = torch.zeros((T, 15), dtype=torch.float32, device="cuda")
