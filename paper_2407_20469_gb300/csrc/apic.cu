@@ -192,6 +192,18 @@ apic_status upload(apic_plan* plan) {
     D.ap_y0 = ay0;
     D.ap_y1 = ay1;
     const size_t o_aprp = A.add(rowptr_of(H.ap_y, ay0, ay1));
+    // the aperture list in (x, y) order, by columns ap_x0..ap_x1 (register synthesis)
+    int ax0 = 0, ax1 = -1;
+    if (!H.ap_x.empty()) {
+        ax0 = *std::min_element(H.ap_x.begin(), H.ap_x.end());
+        ax1 = *std::max_element(H.ap_x.begin(), H.ap_x.end());
+    }
+    const std::vector<int> colptr = rowptr_of(H.ap_x, ax0, ax1);
+    std::vector<int> cole(H.ap_x.size()), fillp(colptr.begin(), colptr.end() - 1);
+    for (size_t q = 0; q < H.ap_x.size(); ++q) cole[fillp[H.ap_x[q] - ax0]++] = (int)q;
+    D.ap_x0 = ax0;
+    D.ap_x1 = ax1;
+    const size_t o_apcp = A.add(colptr), o_apce = A.add(cole);
 
     // darkfield tables
     std::vector<DevDF> dfs;
@@ -345,6 +357,8 @@ apic_status upload(apic_plan* plan) {
     D.st_img = (const int*)(b + o_sti);
     D.st_pup = (const int*)(b + o_stq);
     D.ap_rowptr = (const int*)(b + o_aprp);
+    D.ap_colptr = (const int*)(b + o_apcp);
+    D.ap_cole = (const int*)(b + o_apce);
     D.df = (const DevDF*)(b + o_df);
     D.dU_x = (const int*)(b + o_ux);
     D.dU_y = (const int*)(b + o_uy);
@@ -444,6 +458,16 @@ apic_status configure(apic_plan* plan) {
     L.grid_df = sms * std::min(o_df, 2);
     L.grid_syn = sms * std::min(o_syn, o_obj);
     L.grid_sim = sms * o_sim;
+    // register-transform synthesis for output sides 512 and 1024 (the Stockham kernel otherwise)
+    L.grid_synr = 0;
+    L.smem_synr = synr_smem_bytes(D.H);
+    if (!legacy && (D.H == 512 || D.H == 1024)) {
+        const int o_sr = configure_synr(D.H, L.smem_synr);
+        if (o_sr > 0)
+            L.grid_synr = sms * o_sr;
+        else
+            cudaGetLastError();
+    }
     return APIC_OK;
 }
 

@@ -65,6 +65,9 @@ struct DevPlan {
     const int* st_pup;
     int ap_y0, ap_y1;
     const int* ap_rowptr;            // rows ap_y0..ap_y1
+    int ap_x0, ap_x1;
+    const int* ap_colptr;            // columns ap_x0..ap_x1 of the aperture list sorted by (x, y)
+    const int* ap_cole;              // aperture point of each entry of that order
     // darkfield
     const DevDF* df;
     const int* dU_x; const int* dU_y; const int* dU_pup; const int* dU_ap;
@@ -93,6 +96,8 @@ struct DevPlan {
 struct Launch {
     int grid_kk, grid_ab, grid_df, grid_syn, grid_sim;
     size_t smem_kk, smem_df, smem_syn, smem_sim;
+    int grid_synr;                   // register-transform synthesis (output sides 512, 1024), 0: not used
+    size_t smem_synr;
 };
 
 // Kernel launchers (return cudaError_t of the launch).
@@ -126,6 +131,10 @@ cudaError_t launch_darkfield(const DevPlan& P, const Launch& L, int n_tiles, con
                              int32_t* status, unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_synthesize(const DevPlan& P, const Launch& L, int n_tiles, const float2* spec, float2* field,
                               const int32_t* status, cudaStream_t st);
+// Register-transform synthesis for output side H = 32 B (B in 16, 32): dynamic shared memory
+// and blocks per SM (0: unsupported side or failure).
+size_t synr_smem_bytes(int H);
+int configure_synr(int H, size_t smem);
 cudaError_t launch_pupil(const DevPlan& P, int n_tiles, const float* phi, float2* pupil, const int32_t* status,
                          cudaStream_t st);
 cudaError_t launch_sim(const DevPlan& P, const Launch& L, int n_tiles, const float2* obj, const float* phi,

@@ -4,6 +4,7 @@
 
 #include "../../include/apic.h"
 #include "passes.cuh"
+#include "regfft.cuh"
 
 namespace apic {
 
@@ -49,8 +50,145 @@ __global__ void __launch_bounds__(kThreads) k_synthesize(DevPlan P, int n_tiles,
     }
 }
 
+// ---------------------------------------------------------------- synthesis, register transforms
+// The same sum for output sides N = 32 B (B = 16, 32: 512 and 1024), one block of 16 warps
+// per tile (persistent over tiles), each warp transforming one N-point sequence at a time
+// in registers: lane t holds x[t + 32 j] (j < B); step A a DFT_B in registers, the twiddle
+// W_N^(t k2) and a padded shared-memory transpose, step B lanes k2 < B run a DFT_32, so
+// lane k2 ends with X[k2 + B k1] (k1 < 32). Columns first, rows last, so that the final
+// writes are whole rows:
+//   1 columns x of the aperture (ap_x0..ap_x1, in groups of 16, one per warp): the
+//     column's points (list sorted by (x, y)) scattered into the warp's area, inverse
+//     transform along y; the 16 columns staged through shared memory (half the rows at
+//     a time) and stored as 128-byte row segments into the tile's own output rows at
+//     columns 0..ap_x1 - ap_x0 (the output buffer is the scratch);
+//   2 every row: its aperture columns loaded, the rest zero, inverse transform along x,
+//     the row stored whole (evict-first).
+constexpr int kSRWarps = 16;
+constexpr int kSRLd = 33;            // a warp's area: 32 rows of 33 values (the scatter uses N of them)
+
+template <int B>
+__device__ __forceinline__ void warp_fft_inv(float2 (&v)[B], float2 (&o)[32], float2* hs, const float2* tw, int lane) {
+    DFT<B, true>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) hs[k2 * kSRLd + lane] = cmul(v[k2], tw_get(tw, k2 * 32 + lane, true));
+    __syncwarp();
+    const int row = lane < B ? lane : 0;          // lanes k2 >= B transform a copy, discarded
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) o[n1] = hs[row * kSRLd + n1];
+    DFT<32, true>::run(o);
+    __syncwarp();
+}
+
+size_t synr_smem_bytes(int H) {
+    return (size_t)kSRWarps * 32 * kSRLd * sizeof(float2) + (size_t)H * sizeof(float2);
+}
+
+template <int B>
+__global__ void __launch_bounds__(kSRWarps * 32, 1)
+k_synth_reg(DevPlan P, int n_tiles, const float2* __restrict__ spec, float2* __restrict__ field,
+            const int32_t* __restrict__ status) {
+    constexpr int N = 32 * B, HALF = N / 2;
+    extern __shared__ float4 smem4[];
+    float2* areas = reinterpret_cast<float2*>(smem4);
+    float2* tw = areas + kSRWarps * 32 * kSRLd;     // [k2 < B][t < 32] = W_N^(t k2)
+    float2* stage = areas;                          // HALF x 17 values, aliases the warps' areas
+    for (int i = threadIdx.x; i < 32 * B; i += blockDim.x) {
+        const int k2 = i >> 5, t = i & 31;
+        tw[i] = P.tw_N[(t * k2) % N];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* hs = areas + warp * 32 * kSRLd;
+    const int x0 = P.ap_x0, nbx = P.ap_x1 - P.ap_x0 + 1;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        float2* F = field + (size_t)tile * N * N;
+        if (status && (status[tile] & (APIC_TILE_BACKGROUND | APIC_TILE_BADINPUT))) {
+            for (size_t t = threadIdx.x; t < (size_t)N * N; t += blockDim.x) F[t] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const float2* sp = spec + (size_t)tile * P.nap;
+        // 1: aperture columns, 16 at a time
+        for (int c0 = 0; c0 < nbx; c0 += kSRWarps) {
+            const int c = c0 + warp;
+            float2 o[32];
+            if (c < nbx) {
+#pragma unroll
+                for (int j = 0; j < B; ++j) hs[lane + 32 * j] = make_float2(0.f, 0.f);
+                __syncwarp();
+                for (int e = P.ap_colptr[c] + lane; e < P.ap_colptr[c + 1]; e += 32) {
+                    const int p = P.ap_cole[e];
+                    hs[freq_index(P.ap_y[p], N)] = sp[p];
+                }
+                __syncwarp();
+                float2 v[B];
+#pragma unroll
+                for (int j = 0; j < B; ++j) v[j] = hs[lane + 32 * j];
+                __syncwarp();
+                warp_fft_inv<B>(v, o, hs, tw, lane);   // lane k2 < B: rows k2 + B k1
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __syncthreads();                        // areas free (h = 0) / stage consumed (h = 1)
+                if (c < nbx && lane < B) {
+#pragma unroll
+                    for (int k1 = 16 * h; k1 < 16 * h + 16; ++k1) stage[(lane + B * k1 - h * HALF) * 17 + warp] = o[k1];
+                }
+                __syncthreads();
+                const int ncol = min(kSRWarps, nbx - c0);
+                for (int i = threadIdx.x; i < HALF * kSRWarps; i += blockDim.x) {
+                    const int y = i >> 4, q = i & 15;
+                    if (q < ncol) F[(size_t)(h * HALF + y) * N + c0 + q] = stage[y * 17 + q];
+                }
+            }
+            __syncthreads();                            // stage consumed before the areas are reused
+        }
+        // 2: rows (each warp reads its own rows' aperture columns before overwriting them)
+        for (int y = warp; y < N; y += kSRWarps) {
+            float2* row = F + (size_t)y * N;
+            float2 v[B], o[32];
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const int x = lane + 32 * j;
+                const int c = (x < N / 2 ? x : x - N) - x0;
+                v[j] = (unsigned)c < (unsigned)nbx ? row[c] : make_float2(0.f, 0.f);
+            }
+            warp_fft_inv<B>(v, o, hs, tw, lane);
+            if (lane < B) {
+#pragma unroll
+                for (int k1 = 0; k1 < 32; ++k1) __stcs(row + lane + B * k1, o[k1]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int B>
+static int configure_synr_b(size_t smem) {
+    if (raise_smem_limit((const void*)k_synth_reg<B>, smem) != cudaSuccess) return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_synth_reg<B>, kSRWarps * 32, smem) != cudaSuccess)
+        return 0;
+    return occ;
+}
+
+int configure_synr(int H, size_t smem) {
+    if (H == 512) return configure_synr_b<16>(smem);
+    if (H == 1024) return configure_synr_b<32>(smem);
+    return 0;
+}
+
 cudaError_t launch_synthesize(const DevPlan& P, const Launch& L, int n_tiles, const float2* spec, float2* field,
                               const int32_t* status, cudaStream_t st) {
+    if (L.grid_synr > 0 && (P.H == 512 || P.H == 1024)) {
+        const int grid = min(L.grid_synr, n_tiles);
+        if (grid < 1) return cudaSuccess;
+        if (P.H == 512)
+            k_synth_reg<16><<<grid, kSRWarps * 32, L.smem_synr, st>>>(P, n_tiles, spec, field, status);
+        else
+            k_synth_reg<32><<<grid, kSRWarps * 32, L.smem_synr, st>>>(P, n_tiles, spec, field, status);
+        return cudaGetLastError();
+    }
     const int grid = min(L.grid_syn, n_tiles);
     k_synthesize<<<grid, kThreads, L.smem_syn, st>>>(P, n_tiles, spec, field, status);
     return cudaGetLastError();
