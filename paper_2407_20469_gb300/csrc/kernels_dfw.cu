@@ -55,15 +55,6 @@ constexpr int kWQWords = 16;               // Q membership words per band row (t
 
 __device__ __forceinline__ int sfreqw(int i, int n) { return i < n / 2 ? i : i - n; }
 
-// Row of a band starting at signed row y0 that lives at grid index i of an m-point
-// axis; >= the band size when none. Needs |y0| < m.
-__device__ __forceinline__ int band_row_w(int i, int y0, int m) {
-    int r = i - y0;
-    if (r >= m) r -= m;
-    if (r < 0) r += m;
-    return r;
-}
-
 // Half-warp of a cluster: t lane, hw index in the block, gh index in the cluster
 // (rank x 32 + hw), ghs half-warps in the cluster.
 struct HWw {
@@ -185,18 +176,24 @@ struct WOutDot {        // w = C^H C d; returns Re <d, w>
 // ---- per-column operations on a column of 16 B points: slot s of lane t holds
 // o[s][k1] = the value at y = (t + 16 s) + B k1 (valid where t + 16 s < B)
 template <int B>
-struct WMidStoreField {     // column-major p s (16 B values per column)
+struct WMidStoreField {     // column-major p s W^(shift k) (16 B values per column; wt: W_16B^j)
     float2* PF;
     float scale;
+    const float2* wt;
+    int shift;
     static constexpr bool kOut = false;
     static constexpr bool kPre = false;
     __device__ void operator()(float2 (&o)[Slots<B>::value][16], int x, int t) const {
-        float2* col = PF + (size_t)x * (16 * B);
+        constexpr int m = 16 * B;
+        float2* col = PF + (size_t)x * m;
 #pragma unroll
         for (int s = 0; s < Slots<B>::value; ++s)
             if (t + 16 * s < B) {
 #pragma unroll
-                for (int k1 = 0; k1 < 16; ++k1) col[t + 16 * s + B * k1] = cscale(o[s][k1], scale);
+                for (int k1 = 0; k1 < 16; ++k1) {
+                    const int k = t + 16 * s + B * k1;
+                    col[k] = cscale(cmul(o[s][k1], wt[(shift * k) % m]), scale);
+                }
             }
     }
 };
@@ -303,32 +300,34 @@ __device__ __noinline__ float wpass_rows_out(HWw w, const float2* tw, const floa
     return acc;
 }
 
-// columns x < ncols of a grid whose columns have 16 B points: band rows of the tiled
-// grid Gi (row r of the band at grid row (yi0 + r) mod 16 B, ni rows, ldi columns) are
-// the input, the rest zero; inverse along y, mid, and (Mid::kOut) forward along y with
-// band rows yo0.. (no) stored to the tiled grid Go (ldo columns). Each half-warp reads
-// and writes its own columns, so Gi and Go may be the same grid. A lane's band rows
-// are all congruent mod 4 (16 B is), so their in-tile row offset is one per lane. Ends
-// with a tile barrier.
+// columns x < ncols of a grid whose columns have 16 B points: the ni band rows of the
+// tiled grid Gi (ldi columns) are the input at column indices 0..ni - 1, the rest zero;
+// inverse along y, mid, and (Mid::kOut) forward along y, column indices 0..no - 1
+// stored as the band rows of the tiled grid Go (ldo columns). An input band that
+// starts at grid row yi0 and an output band at yo0 are thus transformed as if both
+// started at row 0: by the shift theorem that multiplies the inverse transform by
+// W^(-yi0 k) and the forward one's input by W^(yo0 k), a ramp W^((yo0 - yi0) k) that
+// the stored field (the mid's factor) carries (the column passes of the CG run
+// between the U and the Q band in both directions, with the field and its
+// conjugate). Each half-warp reads and writes its
+// own columns, so Gi and Go may be the same grid. Ends with a tile barrier.
 // (Measured and left out: staging strips of 32 columns through shared memory for
 // 256-byte row accesses, and issuing the next column's loads before the current
 // transform; both slowed the kernel by ~10 %: the first adds block barriers between
 // half-warps that otherwise overlap one another's loads and transforms, the second
 // spills.)
 template <int B, int K, class Mid>
-__device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0,
-                                        int ni, float2* Go, int ldo, int yo0, int no, Mid mid) {
-    constexpr int m = 16 * B, S = Slots<B>::value;
+__device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, const float2* Gi, int ldi, int ni,
+                                        float2* Go, int ldo, int no, Mid mid) {
+    constexpr int S = Slots<B>::value;
     const HalfWarp h = w.h();
-    const int li = t4_low(w.t - yi0), lo = t4_low(w.t - yo0);
+    const int ri = t4_row(w.t, ldi), ro = t4_row(w.t, ldo);      // band row t of the lane
     for (int x = w.gh; x < ncols; x += w.ghs) {
         float2 v[B], o[S][16];
-        const float2* gi = Gi + li + t4_col(x);
+        const float2* gi = Gi + ri + t4_col(x);
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const int bb = band_row_w(w.t + 16 * j, yi0, m);
-            v[j] = bb < ni ? ldx<K>(gi + (bb & ~3) * ldi) : make_float2(0.f, 0.f);
-        }
+        for (int j = 0; j < B; ++j)                                  // band row t + 16 j
+            v[j] = w.t + 16 * j < ni ? ldx<K>(gi + 16 * j * ldi) : make_float2(0.f, 0.f);
         if constexpr (Mid::kPre) {
             typename Mid::Pre pre;
             mid.load(pre, x, w.t);
@@ -340,12 +339,10 @@ __device__ __noinline__ void wpass_cols(HWw w, const float2* tw, int ncols, cons
         }
         if constexpr (Mid::kOut) {
             fft_b<B, false>(o, v, h, tw);
-            float2* go = Go + lo + t4_col(x);
+            float2* go = Go + ro + t4_col(x);
 #pragma unroll
-            for (int k1 = 0; k1 < B; ++k1) {
-                const int bb = band_row_w(w.t + 16 * k1, yo0, m);
-                if (bb < no) go[(bb & ~3) * ldo] = v[k1];
-            }
+            for (int k1 = 0; k1 < B; ++k1)
+                if (w.t + 16 * k1 < no) go[16 * k1 * ldo] = v[k1];
         }
     }
     tile_sync<K>();
@@ -386,7 +383,7 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
 // Columns of I - |p|^2 (n = 512; the image read transposed with tr, once, with
 // evict-first loads): Eq. 13's right-hand side F(I) - P * P is the spectrum of the
 // image minus the intensity of the known field, so p's column x is formed from the
-// band rows py0.. (nP) of the tiled grid GP (P's rows transformed along x on the camera grid) by an
+// nP band rows of the tiled grid GP (P's rows transformed along x on the camera grid) by an
 // inverse transform along y and |p|^2 kept in registers; then the chunk's 32 image
 // columns are staged through shared memory (coalesced reads), the difference is
 // formed and transformed forward along y; rows qy0.. (nQ) go to GX (row length n).
@@ -394,7 +391,7 @@ __device__ __noinline__ void wpass_rows_mask(HWw w, const float2* tw, float2* G,
 // areas; barriers separate each use from the transforms. Ends with a tile barrier.
 template <int K>
 __device__ __noinline__ void wpass_image_cols_p(HWw w, const float2* tw, float2* stage, const float* img,
-                                                const float2* GP, int py0, int nP, float2* GX, int qy0, int nQ,
+                                                const float2* GP, int nP, float2* GX, int qy0, int nQ,
                                                 bool tr) {
     constexpr int BN = kWBN, n = 16 * BN, S = Slots<BN>::value;
     const HalfWarp h = w.h();
@@ -403,12 +400,11 @@ __device__ __noinline__ void wpass_image_cols_p(HWw w, const float2* tw, float2*
         const int x = c0 + w.hw;
         float2 v[BN], o[S][16];
         float q[S][16];
-        const float2* gp = GP + t4_low(w.t - py0) + t4_col(x);
+        // the band as if it started at row 0: that multiplies p by a phase ramp along
+        // y, which |p|^2 does not see
+        const float2* gp = GP + t4_row(w.t, n) + t4_col(x);
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
-            const int bb = band_row_w(w.t + 16 * j, py0, n);
-            v[j] = bb < nP ? ldx<K>(gp + (bb & ~3) * n) : make_float2(0.f, 0.f);
-        }
+        for (int j = 0; j < BN; ++j) v[j] = w.t + 16 * j < nP ? ldx<K>(gp + 16 * j * n) : make_float2(0.f, 0.f);
         fft_a<BN, true>(v, o, h, tw);               // p(x, y), y = (t + 16 s) + BN k1
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -566,7 +562,7 @@ __device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, cons
     // then per column p, the difference and its forward transform, then the rows
     wpass_rows_in<kWBN>(c.ws, c.tw_n, c.GQ, n, nP, prp, P.dP_x + p_off, pval);
     tile_sync<K>();
-    wpass_image_cols_p<K>(c.ws, c.tw_n, c.stage, img, c.GQ, py0, nP, c.PF, qy0, nQ, D.tr != 0);
+    wpass_image_cols_p<K>(c.ws, c.tw_n, c.stage, img, c.GQ, nP, c.PF, qy0, nQ, D.tr != 0);
     wpass_image_rows<K>(c.ws, c.tw_n, c.PF, nQ, qrp, P.dQ_x + q_off, c.bq);
     // band rows of the known field P (Eq. 11) along x on the row grid, then p s on
     // the column grid, column-major in PF (s = 1 / (mx my): the two unnormalised
@@ -574,11 +570,15 @@ __device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, cons
     const float scale = 1.f / ((float)mx * (float)(16 * BY));
     wpass_rows_in<BX>(w, c.tw_x, c.GQ, mx, nP, prp, P.dP_x + p_off, pval);
     tile_sync<K>();
-    wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, WMidStoreField<BY>{c.PF, scale});
+    // the field carries the ramp W^((uy0 - qy0) k) of the U <-> Q column passes and
+    // W^(-py0 k) for its own band's start (see wpass_cols)
+    const int my = 16 * BY, shift = (((uy0 - qy0 - py0) % my) + my) % my;
+    wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, nP, c.GQ, mx, 0,
+                      WMidStoreField<BY>{c.PF, scale, wgrid_table(P, BY), shift});
     // rows of b inverse along x on the row grid; s = d = C^H b
     wpass_rows_in<BX>(w, c.tw_x, c.GQ, mx, nQ, qrp, P.dQ_x + q_off, WValB{c.bq});
     tile_sync<K>();
-    wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
+    wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, nQ, c.GU, mx, nU, WMidTimesField<BY, false>{c.PF});
     const float g0 =
         wpass_rows_out<BX, K>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutStart{c.sv, c.dv, c.xv});
     int par = 0;
@@ -592,9 +592,9 @@ __device__ __forceinline__ int dfw_solve(const DFWCtx& c, const DevPlan& P, cons
     for (; it < iters && !conv; ++it) {
         wpass_rows_in<BX>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WValNextDir{c.sv, c.dv, bf});
         tile_sync<K>();
-        wpass_cols<BY, K>(w, c.tw_y, mx, c.GU, mx, uy0, nU, c.GQ, mx, qy0, nQ, WMidTimesField<BY, true>{c.PF});
+        wpass_cols<BY, K>(w, c.tw_y, mx, c.GU, mx, nU, c.GQ, mx, nQ, WMidTimesField<BY, true>{c.PF});
         wpass_rows_mask<BX, K>(w, c.tw_x, c.GQ, nQ, qmask);
-        wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, qy0, nQ, c.GU, mx, uy0, nU, WMidTimesField<BY, false>{c.PF});
+        wpass_cols<BY, K>(w, c.tw_y, mx, c.GQ, mx, nQ, c.GU, mx, nU, WMidTimesField<BY, false>{c.PF});
         const float dw = wpass_rows_out<BX, K>(w, c.tw_x, c.GU, mx, nU, urp, P.dU_x + u_off, WOutDot{c.wv, c.dv});
         const double delta = tile_sum<K>(dw, c.red, par);
         if (!(delta > 0)) break;

@@ -382,6 +382,49 @@ def test_plans_sharing_kernels_coexist():
     small.close()
 
 
+@pytest.mark.parametrize("n,ill", [(256, None), (512, "8+24")])
+def test_register_synthesis_matches_the_dft(n, ill):
+    """The register-transform synthesis (output sides 512 and 1024: aperture columns,
+    then whole rows) against numpy's inverse DFT of the same aperture values, and
+    against the shared-memory Stockham kernel of the legacy path; a background tile
+    comes out zero."""
+    il = synth.illumination_8_24() if ill else synth.illumination()
+    plans = [new_plan(n, il, max_tiles=3)]
+    if n <= 256:                                    # the legacy path's plan at 256 (Stockham synthesis)
+        plans.append(new_plan(n, il, max_tiles=3, flags=apic.APIC_LEGACY_KERNELS))
+    H = plans[0].info.out_h
+    assert H == 2 * n
+    ap = plans[0].table(apic.APIC_TABLE_APERTURE)
+    rng = np.random.default_rng(n + 1)
+    vals = rng.standard_normal((3, len(ap))) + 1j * rng.standard_normal((3, len(ap)))
+    outs = []
+    for plan in plans:
+        field = torch.full((3, H, 2 * H), 7.0, dtype=torch.float32, device="cuda")
+        plan.synthesize(3, dev(to_interleaved(vals)), field)
+        torch.cuda.synchronize()
+        outs.append(as_complex(field))
+    for t in range(3):
+        F = np.zeros((H, H), np.complex128)
+        F[ap[:, 1] % H, ap[:, 0] % H] = vals[t]
+        ref = grid.synthesize(F)
+        for got in outs:
+            assert np.linalg.norm(got[t] - ref) / np.linalg.norm(ref) < 1e-5
+    # status-skipped tiles: zero output (through the batch path's synthesis)
+    plan = plans[0]
+    I, _, _ = make_tiles(n, 1, seed=9, ill=il) if n <= 256 else (None, None, None)
+    if I is not None:
+        flat = np.zeros_like(I)
+        flat[:] = I.mean()
+        field = torch.full((1, H, 2 * H), 7.0, dtype=torch.float32, device="cuda")
+        z = torch.zeros((1, 15), dtype=torch.float32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        skip = new_plan(n, il, max_tiles=1, flags=apic.APIC_SKIP_BACKGROUND)
+        skip.reconstruct_batch(1, dev(flat), field, z, None, st)
+        torch.cuda.synchronize()
+        assert int(st.item()) & apic.APIC_TILE_BACKGROUND
+        assert float(field.abs().max()) == 0.0
+
+
 @pytest.mark.parametrize("flags", [0, apic.APIC_LEGACY_KERNELS])
 def test_autotune_keeps_the_faster_variants_and_the_results(flags):
     n = 128
