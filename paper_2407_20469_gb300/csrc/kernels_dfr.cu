@@ -54,16 +54,6 @@ constexpr int kStageLd = 33;           // column stage: 32 columns + 1 pad
 
 __device__ __forceinline__ int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
 
-// Row of a band starting at signed row y0 that lives at grid index i of an m-point
-// axis (band row r sits at index (y0 + r) mod m); >= the band size when none.
-// Needs |y0| < m.
-__device__ __forceinline__ int band_row(int i, int y0, int m) {
-    int r = i - y0;
-    if (r >= m) r -= m;
-    if (r < 0) r += m;
-    return r;
-}
-
 // ---- tensor memory as per-thread storage of the known field
 // The darkfield kernel issues no MMA; its 512 TMEM columns x 128 lanes (256 KB per
 // SM) hold each thread's share of the column-major known field p on the paired
@@ -144,22 +134,30 @@ struct OutDot {         // w = C^H C d; returns Re <d, w>
 
 // ---- per-column mid operations (lanes t < B; o[k1] is the value at y = t + B k1)
 template <int B>
-struct MidStoreField {  // store p s (p scaled) column-major (16 B per column)
+struct MidStoreField {  // store p s W^(shift y) (p scaled; wt: W_16B^j) column-major (16 B per column)
     float2* PF;
     float scale;
+    const float2* wt;
+    int shift;
     static constexpr bool kReadsField = false, kTmem = false;
     __device__ void operator()(float2 (&o)[16], int x, int t, const float2 (&)[16]) const {
         float2* col = PF + (size_t)x * (16 * B);
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) col[t + B * k1] = cscale(o[k1], scale);
+        for (int k1 = 0; k1 < 16; ++k1) {
+            const int y = t + B * k1;
+            col[y] = cscale(cmul(o[k1], wt[(shift * y) % (16 * B)]), scale);
+        }
     }
 };
-struct MidAbs2 {        // replace p by |p|^2
+template <int B>
+struct MidAbs2 {        // replace p by |p|^2 W^(shift y) (wt: W_16B^j)
     float2* PF = nullptr;
+    const float2* wt;
+    int shift;
     static constexpr bool kReadsField = false, kTmem = false;
-    __device__ void operator()(float2 (&o)[16], int, int, const float2 (&)[16]) const {
+    __device__ void operator()(float2 (&o)[16], int, int t, const float2 (&)[16]) const {
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) o[k1] = make_float2(cabs2(o[k1]), 0.f);
+        for (int k1 = 0; k1 < 16; ++k1) o[k1] = cscale(wt[(shift * (t + B * k1)) % (16 * B)], cabs2(o[k1]));
     }
 };
 template <int B, bool CONJ>
@@ -173,13 +171,16 @@ struct MidTimesField {  // o *= p s or conj(p s), p s = the stored, scaled field
 };
 // The same two operations with p in the thread's TMEM columns (paired passes; the
 // whole warp calls them, r = the half-warp's column-pair round)
-struct MidStoreFieldT {
+struct MidStoreFieldT {  // p s W^(shift y) (wt: W_16B^j; B of the paired grid)
     uint32_t taddr;
     float scale;
+    const float2* wt;
+    int shift, B;
     static constexpr bool kReadsField = false, kTmem = true;
     __device__ void tm(float2 (&o)[16], int r) const {
+        const int t = threadIdx.x & 15, u = t >= B ? t - B : t, m = 16 * B;   // lane t: point u of its column
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) o[k1] = cscale(o[k1], scale);
+        for (int k1 = 0; k1 < 16; ++k1) o[k1] = cscale(cmul(o[k1], wt[(shift * (u + B * k1)) % m]), scale);
         tmem_st16(taddr + 32 * r, o);
     }
 };
@@ -246,16 +247,19 @@ __device__ __noinline__ float pass_rows_out(HW w, const float2* tw, const float2
     return acc;
 }
 
-// columns x < ncols of a grid whose columns have 16 B points: band rows yi0..
-// (ni of them, row r of the band at grid row (yi0 + r) mod 16 B) of Gi (row stride
-// ldi) are the input, the rest zero; inverse along y, mid, forward along y; band
-// rows yo0.. (no) stored to Go (row stride ldo; no = 0: nothing stored, no forward
-// transform). Each half-warp reads and writes its own columns, so Gi and Go may be
-// the same grid; the known-field values of the column are loaded after the first
-// transform. Ends with __syncthreads.
+// columns x < ncols of a grid whose columns have 16 B points: the ni band rows of Gi
+// (row stride ldi) are the input at column indices 0..ni - 1, the rest zero; inverse
+// along y, mid, forward along y; column indices 0..no - 1 stored as the band rows of
+// Go (row stride ldo; no = 0: nothing stored, no forward transform). A band that
+// starts at grid row y0 is thus transformed as if it started at row 0; by the shift
+// theorem the mid's factor carries the ramp W^((yo0 - yi0) y) (the stored field for
+// the CG's U <-> Q passes in both directions, see df_solve). Each half-warp reads
+// and writes its own columns, so Gi and Go may be the same grid; the known-field
+// values of the column are loaded after the first transform. Ends with
+// __syncthreads.
 template <int B, class Mid>
-__device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
-                                       float2* Go, int ldo, int yo0, int no, Mid mid) {
+__device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int ni,
+                                       float2* Go, int ldo, int no, Mid mid) {
     static_assert(!Mid::kTmem, "TMEM operations need the paired pass");
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
@@ -263,7 +267,7 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const 
         float2 v[B], o[16], pf[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            const int bb = band_row(w.t + 16 * j, yi0, m);
+            const int bb = w.t + 16 * j;
             v[j] = bb < ni ? Gi[(size_t)bb * ldi + x] : make_float2(0.f, 0.f);
         }
         fft_alpha<B, true>(v, o, h, tw);
@@ -280,7 +284,7 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const 
             fft_beta<B, false>(o, v, h, tw);
 #pragma unroll
             for (int k1 = 0; k1 < B; ++k1) {
-                const int bb = band_row(w.t + 16 * k1, yo0, m);
+                const int bb = w.t + 16 * k1;
                 if (bb < no) Go[(size_t)bb * ldo + x] = v[k1];
             }
         }
@@ -293,8 +297,8 @@ __device__ __noinline__ void pass_cols(HW w, const float2* tw, int ncols, const 
 // and each pass makes half as many round trips per half-warp. ncols is even; a grid
 // with an even row stride (16-byte aligned rows) moves each pair as one 16-byte access.
 template <int B, class Mid>
-__device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
-                                        float2* Go, int ldo, int yo0, int no, Mid mid) {
+__device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int ni,
+                                        float2* Go, int ldo, int no, Mid mid) {
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
     const int side = w.t >= B ? 1 : 0;           // lanes t < 2 B: column x + side, point u
@@ -307,7 +311,7 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
         float2 va[B], vb[B], o[16], pf[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            const int bb = band_row(w.t + 16 * j, yi0, m);
+            const int bb = w.t + 16 * j;
             if (bb < ni) {
                 const float2* g = Gi + (size_t)bb * ldi + x;
                 if (vin) {
@@ -339,7 +343,7 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
             fft_beta2<B, false>(o, va, vb, h, tw);
 #pragma unroll
             for (int k1 = 0; k1 < B; ++k1) {
-                const int bb = band_row(w.t + 16 * k1, yo0, m);
+                const int bb = w.t + 16 * k1;
                 if (bb < no) {
                     float2* g = Go + (size_t)bb * ldo + x;
                     if (vout) {
@@ -359,8 +363,8 @@ __device__ __noinline__ void pass_cols2(HW w, const float2* tw, int ncols, const
 // column pair x, x + 1 and transforms the two in turn, so that the pair still moves as
 // one 16-byte access per row on grids with an even row stride. ncols is even.
 template <int B, class Mid>
-__device__ __noinline__ void pass_cols_seq2(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0,
-                                            int ni, float2* Go, int ldo, int yo0, int no, Mid mid) {
+__device__ __noinline__ void pass_cols_seq2(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int ni,
+                                            float2* Go, int ldo, int no, Mid mid) {
     static_assert(!Mid::kTmem, "TMEM operations need the paired pass");
     constexpr int m = 16 * B;
     const HalfWarp h = w.h();
@@ -369,7 +373,7 @@ __device__ __noinline__ void pass_cols_seq2(HW w, const float2* tw, int ncols, c
         float2 va[B], vb[B], o[16], pf[16];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            const int bb = band_row(w.t + 16 * j, yi0, m);
+            const int bb = w.t + 16 * j;
             if (bb < ni) {
                 const float2* g = Gi + (size_t)bb * ldi + x;
                 if (vin) {
@@ -403,7 +407,7 @@ __device__ __noinline__ void pass_cols_seq2(HW w, const float2* tw, int ncols, c
             fft_beta<B, false>(o, vb, h, tw);
 #pragma unroll
             for (int k1 = 0; k1 < B; ++k1) {
-                const int bb = band_row(w.t + 16 * k1, yo0, m);
+                const int bb = w.t + 16 * k1;
                 if (bb < no) {
                     float2* g = Go + (size_t)bb * ldo + x;
                     if (vout) {
@@ -422,14 +426,14 @@ __device__ __noinline__ void pass_cols_seq2(HW w, const float2* tw, int ncols, c
 // column pass on a 16 B grid: paired columns where two fit a half-warp, column pairs
 // in turn up to B = 12, single columns beyond
 template <int B, class Mid>
-__device__ __forceinline__ void cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int yi0, int ni,
-                                     float2* Go, int ldo, int yo0, int no, Mid mid) {
+__device__ __forceinline__ void cols(HW w, const float2* tw, int ncols, const float2* Gi, int ldi, int ni,
+                                     float2* Go, int ldo, int no, Mid mid) {
     if constexpr (2 * B <= 16)
-        pass_cols2<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
+        pass_cols2<B>(w, tw, ncols, Gi, ldi, ni, Go, ldo, no, mid);
     else if constexpr (B <= 12)
-        pass_cols_seq2<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
+        pass_cols_seq2<B>(w, tw, ncols, Gi, ldi, ni, Go, ldo, no, mid);
     else
-        pass_cols<B>(w, tw, ncols, Gi, ldi, yi0, ni, Go, ldo, yo0, no, mid);
+        pass_cols<B>(w, tw, ncols, Gi, ldi, ni, Go, ldo, no, mid);
 }
 
 // rows of Q in place: forward along x, keep the Q lags, inverse along x. Ends with __syncthreads.
@@ -653,12 +657,12 @@ __host__ __device__ constexpr bool uses_tmem(int B) { return kTmemField && (B ==
 // Column pass that multiplies by the scaled field p s or its conjugate: from TMEM on
 // paired grids, else from the column-major copy in global scratch
 template <int BY, bool CONJ>
-__device__ __forceinline__ void cols_times(const DFCtx& c, const float2* tw, int m, const float2* Gi, int ldi, int yi0,
-                                           int ni, float2* Go, int ldo, int yo0, int no) {
+__device__ __forceinline__ void cols_times(const DFCtx& c, const float2* tw, int m, const float2* Gi, int ldi, int ni,
+                                           float2* Go, int ldo, int no) {
     if constexpr (2 * BY <= 16 && kTmemField)
-        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesFieldT<CONJ>{c.tm});
+        cols<BY>(c.w, tw, m, Gi, ldi, ni, Go, ldo, no, MidTimesFieldT<CONJ>{c.tm});
     else
-        cols<BY>(c.w, tw, m, Gi, ldi, yi0, ni, Go, ldo, yo0, no, MidTimesField<BY, CONJ>{c.PF});
+        cols<BY>(c.w, tw, m, Gi, ldi, ni, Go, ldo, no, MidTimesField<BY, CONJ>{c.PF});
 }
 
 // plain twiddle table of a 16 G-point grid of a solve on the 16 B-point register grid
@@ -698,27 +702,35 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     // unnormalised transforms around each product)
     pass_rows_in<BX>(w, twx, c.GQ, mx, nP, prp, P.dP_x + p_off, pval);
     __syncthreads();
+    // (the columns passes transform each band as if it started at row 0, so the field
+    // carries the ramp W^((uy0 - qy0) y) of the U <-> Q passes and W^(-py0 y) for its
+    // own band's start)
     const float scale = 1.f / ((float)mx * (float)my);
+    const int shift = (((uy0 - qy0 - py0) % my) + my) % my;
     if constexpr (2 * BY <= 16 && kTmemField) {
-        cols<BY>(w, twy, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, MidStoreFieldT{c.tm, scale});
+        cols<BY>(w, twy, mx, c.GQ, mx, nP, c.GQ, mx, 0,
+                 MidStoreFieldT{c.tm, scale, grid_table(P, BY, B), shift, BY});
         tmem_wait_st();
     } else {
-        cols<BY>(w, twy, mx, c.GQ, mx, py0, nP, c.GQ, mx, 0, 0, MidStoreField<BY>{c.PF, scale});
+        cols<BY>(w, twy, mx, c.GQ, mx, nP, c.GQ, mx, 0,
+                 MidStoreField<BY>{c.PF, scale, grid_table(P, BY, B), shift});
     }
+    // |p|^2 (blind to the P band's start) times W^(qy0 y): its transform's Q band from row 0
+    const MidAbs2<B> abs2{nullptr, P.tw_r, ((qy0 % m) + m) % m};
     // b -= P * P on Q (16 B grid), then the rows of b inverse along x on the row grid
     if constexpr (BX == B) {
-        cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
+        cols<B>(w, c.tw_m, m, c.GQ, m, nP, c.GQ, m, nQ, abs2);
         pass_rows_rhs<B, true>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
     } else {
         pass_rows_in<B>(w, c.tw_m, c.GQ, m, nP, prp, P.dP_x + p_off, pval);
         __syncthreads();
-        cols<B>(w, c.tw_m, m, c.GQ, m, py0, nP, c.GQ, m, qy0, nQ, MidAbs2{});
+        cols<B>(w, c.tw_m, m, c.GQ, m, nP, c.GQ, m, nQ, abs2);
         pass_rows_rhs<B, false>(w, c.tw_m, c.GQ, nQ, qrp, P.dQ_x + q_off, c.bq);
         pass_rows_in<BX>(w, twx, c.GQ, mx, nQ, qrp, P.dQ_x + q_off, ValB{c.bq});
         __syncthreads();
     }
     // s = d = C^H b
-    cols_times<BY, false>(c, twy, mx, c.GQ, mx, qy0, nQ, c.GU, LDU, uy0, nU);
+    cols_times<BY, false>(c, twy, mx, c.GQ, mx, nQ, c.GU, LDU, nU);
     const float g0 = pass_rows_out<BX>(w, twx, c.GU, LDU, nU, urp, P.dU_x + u_off, OutStart{c.sv, c.dv, c.xv});
     int par = 0;
     const double gamma0 = block_sum2f(g0, c.red, par);
@@ -731,9 +743,9 @@ __device__ __forceinline__ int df_solve(const DFCtx& c, const DevPlan& P, const 
     for (; it < iters && !conv; ++it) {
         pass_rows_in<BX>(w, twx, c.GU, LDU, nU, urp, P.dU_x + u_off, ValNextDir{c.sv, c.dv, bf});
         __syncthreads();
-        cols_times<BY, true>(c, twy, mx, c.GU, LDU, uy0, nU, c.GQ, mx, qy0, nQ);
+        cols_times<BY, true>(c, twy, mx, c.GU, LDU, nU, c.GQ, mx, nQ);
         pass_rows_mask<BX>(w, twx, c.GQ, nQ, qmask);
-        cols_times<BY, false>(c, twy, mx, c.GQ, mx, qy0, nQ, c.GU, LDU, uy0, nU);
+        cols_times<BY, false>(c, twy, mx, c.GQ, mx, nQ, c.GU, LDU, nU);
         const float dw = pass_rows_out<BX>(w, twx, c.GU, LDU, nU, urp, P.dU_x + u_off, OutDot{c.wv, c.dv});
         const double delta = block_sum2f(dw, c.red, par);
         if (!(delta > 0)) break;
