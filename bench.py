@@ -173,7 +173,7 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+        sm, smax, pw, reasons = [], [], [], set()
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
@@ -183,13 +183,18 @@ class ClockSampler:
                 smax.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for name, val in zip(self.NAMES, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sm_mhz_min": min(sm),
+                "power_w_median": statistics.median(pw) if pw else None}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -626,11 +631,14 @@ def gpu_arm(args):
         if world > 1:
             dist.barrier()
         step_ms = []
+        e2e_clocks = ClockSampler(clock_id(device))
+        e2e_clocks.start()
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
             for a, b in chunks:
                 plan.reconstruct_host(b - a, I_host, f_host, z_host, s_host)
             step_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_clk = e2e_clocks.stop()
         ems = sum(step_ms)
         if world > 1:
             t = torch.tensor([ems], dtype=torch.float64, device=device)
@@ -643,7 +651,8 @@ def gpu_arm(args):
                "steps": args.e2e_steps,
                "api": f"apic_reconstruct_host (pinned host buffers of {Th} tiles, {len(chunks)} call(s) per step)",
                "h2d_gbs_measured": h2d_gbs, "d2h_gbs_measured": d2h_gbs,
-               "step_ms": [round(v, 2) for v in step_ms], "step_ms_median": statistics.median(step_ms)}
+               "step_ms": [round(v, 2) for v in step_ms], "step_ms_median": statistics.median(step_ms),
+               "clocks": e2e_clk}
         del I_host, f_host, z_host, s_host
 
     # ---- roofline of the darkfield kernel: dense-grid algorithmic flops of its launches

@@ -754,13 +754,14 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             const int wa = W - r, rounds = m0 / W;
             // earlier stages of tiles [a, b) on stream ps (after the full waves' inputs, or
             // a part of them, are in)
-            auto full_pre = [&](int a, int b, bool final) -> apic_status {
+            // (cap: SMs the persistent KK / aberration kernels may hold, 0 = all)
+            auto full_pre = [&](int a, int b, bool final, int cap) -> apic_status {
                 APIC_TRY_LAUNCH(launch_background(D, b - a, It + (size_t)a * in_tile, plan->c2 + a, stt + a, thresh2,
                                                   ps, replace ? 1 : 0));
                 if (last && final) tm.mark(0, 1, ps);
                 apic_status q;
-                if ((q = learned_part(a, b - a, df_sms(plan, W - r))) != APIC_OK) return q;
-                return pre_df(a, b - a, final, df_sms(plan, W - r));
+                if ((q = learned_part(a, b - a, cap)) != APIC_OK) return q;
+                return pre_df(a, b - a, final, cap);
             };
             const bool rparts = hk && hk->parts > 0;
             int round_part[SplitHooks::kMaxRounds] = {};     // part of each round (round parts)
@@ -774,9 +775,12 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                 for (int g = 0, k0 = 0; g < hk->parts; ++g) {
                     const int k1 = hk->part_rounds[g];
                     APIC_TRY_CUDA(cudaStreamWaitEvent(ps, hk->part_ready[g], 0));
+                    // the first part runs beside the partial wave's solves, so it leaves their
+                    // SMs free; later parts run between darkfield rounds, on every SM that frees
                     const bool fin = g == hk->parts - 1;
-                    if ((s = full_pre(k0 * wa, k1 * wa, false)) != APIC_OK) return s;
-                    if ((s = full_pre(ma + k0 * r, ma + k1 * r, fin)) != APIC_OK) return s;
+                    const int cap = g == 0 ? df_sms(plan, W - r) : 0;
+                    if ((s = full_pre(k0 * wa, k1 * wa, false, cap)) != APIC_OK) return s;
+                    if ((s = full_pre(ma + k0 * r, ma + k1 * r, fin, cap)) != APIC_OK) return s;
                     APIC_TRY_CUDA(cudaEventRecord(plan->ev_prep[g], ps));
                     for (int k = k0; k < k1; ++k) round_part[k] = g;
                     k0 = k1;
@@ -784,7 +788,7 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                 ps = st;
             } else {
                 if (hk && hk->wait_main) APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
-                if ((s = full_pre(0, m0, true)) != APIC_OK) return s;
+                if ((s = full_pre(0, m0, true, df_sms(plan, W - r))) != APIC_OK) return s;
                 APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
                 APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_pre, 0));
             }
