@@ -114,6 +114,8 @@ typedef struct {
     int n_df_used;         /* darkfield images the geometry admits (Sec. 4: <= 42% unknown) */
     int fft_m;             /* grid of the darkfield correlations                            */
     double pupil_rx, pupil_ry;   /* pupil radius in grid steps along x and y              */
+    int df_wave;           /* tiles whose darkfield solves run at once (one per block or
+                              cluster); 0 for a host-only plan                          */
 } apic_plan_info;
 
 /* Human-readable name of a return code. Never NULL. */
@@ -209,10 +211,12 @@ apic_status apic_plan_set_df_grid(apic_plan* plan, int index, int mx, int my);
  * (Eq. 11-13), inverse transform. The global phase of the field is the
  * phase gauge of Eq. 5 (mean phase of the recovered fields set to zero).
  * Batches above max_tiles are processed in chunks. When a chunk is not a
- * whole number of darkfield waves (one tile per block), its last partial
- * wave's darkfield solves run on a second stream the plan owns, forked from
- * and joined back to `stream` (stream capture follows the fork); results are
- * identical to the plain order.
+ * whole number of darkfield waves (one tile per block) and its last partial
+ * wave holds at most half a wave, that wave's darkfield solves run first, on
+ * a second stream the plan owns, forked from and joined back to `stream`
+ * (stream capture follows the fork), while the other tiles' earlier stages
+ * run on the remaining SMs; a larger partial wave simply ends the darkfield
+ * stage. Results are identical in every order.
  */
 apic_status apic_reconstruct_batch(apic_plan* plan, int n_tiles, const float* d_intensity,
                                    float* d_field, float* d_zernike, float* d_pupil,

@@ -55,7 +55,7 @@ class apic_plan_info(C.Structure):
         ("tile_h", C.c_int), ("tile_w", C.c_int), ("out_h", C.c_int), ("out_w", C.c_int),
         ("n_bf", C.c_int), ("n_df", C.c_int), ("n_pupil", C.c_int), ("n_aperture", C.c_int),
         ("n_rows", C.c_int), ("n_df_used", C.c_int), ("fft_m", C.c_int),
-        ("pupil_rx", C.c_double), ("pupil_ry", C.c_double),
+        ("pupil_rx", C.c_double), ("pupil_ry", C.c_double), ("df_wave", C.c_int),
     ]
 
 

@@ -639,9 +639,14 @@ struct SplitHooks {
 // Partial-wave geometry of a chunk of nt tiles: r trailing tiles (0: no split),
 // m0 = nt - r, ma, the full waves' tiles that go to the W - r blocks, and ml, the
 // first tile of the r blocks' last round (= ma when they take a single round).
+// Only a partial wave of at most W / 2 tiles is split off: the full waves' earlier
+// stages run beside its solves on the W - r SMs it leaves, which for a larger one
+// would be too few (a partial wave of r > W / 2 idles fewer than W / 2 SMs for one
+// round at the end of the plain order).
 void split_geometry(const apic_plan* p, int nt, int& r, int& m0, int& ma, int& ml) {
     const int W = df_wave(p);
     r = (p->dev.n_used > 0 && nt > W) ? nt % W : 0;
+    if (2 * r > W) r = 0;
     m0 = nt - r;
     ma = r > 0 ? (W - r) * (m0 / W) : m0;
     ml = r > 0 && m0 - ma > r ? m0 - r : ma;
@@ -1035,6 +1040,7 @@ apic_status apic_plan_query(const apic_plan* plan, apic_plan_info* info) {
     info->fft_m = plan->use_reg ? H.mr : H.m;
     info->pupil_rx = H.Rx;
     info->pupil_ry = H.Ry;
+    info->df_wave = plan->host_only ? 0 : df_wave(plan);
     return APIC_OK;
 }
 

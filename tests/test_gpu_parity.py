@@ -449,11 +449,16 @@ def test_autotune_keeps_the_faster_variants_and_the_results(flags):
     assert rel_l2(b[0], res.field) < FIELD_TOL
 
 
-def test_partial_wave_runs_beside_the_full_waves_bit_exactly():
-    """1000 tiles in one call (the last partial darkfield wave runs on a second
-    stream beside the other tiles' earlier stages) equal ten calls of 100 tiles
-    (no partial wave split), bit for bit."""
-    n, T = 64, 1000
+@pytest.mark.parametrize("frac", [0.25, 0.75])
+def test_partial_wave_runs_beside_the_full_waves_bit_exactly(frac):
+    """Six darkfield waves and a partial one in one call equal calls of half a wave
+    (no partial wave split), bit for bit: a quarter wave runs on a second stream
+    beside the other tiles' earlier stages (split order), three quarters of a wave
+    simply end the darkfield stage (plain order)."""
+    n = 64
+    W = new_plan(n, max_tiles=1).info.df_wave
+    assert W > 0
+    T = 6 * W + int(frac * W)
     plan = new_plan(n, max_tiles=T)
     rng = np.random.default_rng(12)
     zern = torch.as_tensor(np.resize(rng.uniform(-0.5, 0.5, (16, 15)).astype(np.float32), (T, 15)), device="cuda")
@@ -462,6 +467,7 @@ def test_partial_wave_runs_beside_the_full_waves_bit_exactly():
     obj = learn.device_objects(T, 2 * n, 21, "cuda")
     I = torch.empty((T, 24, n, n), dtype=torch.float32, device="cuda")
     plan.simulate(T, obj, zern, 1e4, 21, I)
+    del obj
     H = plan.info.out_h
     f1 = torch.empty((T, H, 2 * H), dtype=torch.float32, device="cuda")
     f2 = torch.empty_like(f1)
@@ -470,8 +476,10 @@ def test_partial_wave_runs_beside_the_full_waves_bit_exactly():
     s1 = torch.empty(T, dtype=torch.int32, device="cuda")
     s2 = torch.empty_like(s1)
     plan.reconstruct_batch(T, I, f1, z1, None, s1)
-    for t0 in range(0, T, 100):
-        plan.reconstruct_batch(100, I[t0:t0 + 100], f2[t0:t0 + 100], z2[t0:t0 + 100], None, s2[t0:t0 + 100])
+    step = max(1, W // 2)
+    for t0 in range(0, T, step):
+        c = min(step, T - t0)
+        plan.reconstruct_batch(c, I[t0:t0 + c], f2[t0:t0 + c], z2[t0:t0 + c], None, s2[t0:t0 + c])
     torch.cuda.synchronize()
     assert torch.equal(s1, s2) and torch.equal(z1, z2) and torch.equal(f1, f2)
     assert torch.isfinite(f1).all()
@@ -525,13 +533,15 @@ def test_reconstruct_host_with_partial_waves_matches_device_path():
     assert torch.equal(s_h, s_d.cpu()) and torch.equal(z_h, z_d.cpu()) and torch.equal(f_h, f_d.cpu())
 
 
-@pytest.mark.parametrize("T", [500, 2000])
-def test_reconstruct_host_one_chunk_split_matches_device_path(T):
-    """One chunk (n_tiles <= max_tiles) with a partial darkfield wave: the inputs
-    copy in parts and the fields out per darkfield round around the split order
-    (2000 tiles of 64: more than four rounds); the result equals the device path
-    bit for bit."""
+@pytest.mark.parametrize("waves", [3, 6])
+def test_reconstruct_host_one_chunk_split_matches_device_path(waves):
+    """One chunk (n_tiles <= max_tiles) with a partial darkfield wave of a quarter
+    wave: the inputs copy in parts of whole darkfield rounds and the fields out per
+    round around the split order (6 waves: more than four rounds); the result
+    equals the device path bit for bit."""
     n = 64
+    W = new_plan(n, max_tiles=1).info.df_wave
+    T = waves * W + W // 4
     plan = new_plan(n, max_tiles=T)
     from paper_2407_20469_gb300 import learn
     zern = torch.zeros((T, 15), dtype=torch.float32, device="cuda")

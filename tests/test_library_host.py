@@ -41,6 +41,7 @@ def _geom(n):
                                    (128, synth.illumination_12_22())])
 def test_host_geometry_matches_oracle(n, ill):
     plan = apic.Plan.from_illumination(n, ill, flags=apic.APIC_HOST_ONLY)
+    assert plan.info.df_wave == 0                  # no device: no darkfield grid
     g = _geom(n)
     k = grid.snap_leds(ill.kx, ill.ky, ill.n_bf, g)
     assert np.array_equal(plan.table(apic.APIC_TABLE_LEDS), k)
