@@ -54,7 +54,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILES = os.path.join(ROOT, "profiles")
 DEFAULT_DF_TOL = 3e-4          # the library's darkfield CG tolerance (apic_params.df_tol <= 0)
 DF_SOURCES = {256: ["kernels_dfr.cu", "regfft.cuh", "common.cuh", "internal.cuh"],
-              512: ["kernels_dfw.cu", "regfft.cuh", "common.cuh", "internal.cuh"]}
+              512: ["kernels_dfw.cu", "regfft.cuh", "t4grid.cuh", "common.cuh", "internal.cuh"]}
 DF_KERNEL = {256: "k_darkfield_reg", 512: "k_darkfield_wide"}
 HOST_E2E_RAM_FRAC = 0.45       # pinned host buffers of the end-to-end leg: at most this share of host RAM
 
