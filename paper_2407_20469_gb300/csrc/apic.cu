@@ -793,7 +793,12 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
                 ps = st;
             } else {
                 if (hk && hk->wait_main) APIC_TRY_CUDA(cudaStreamWaitEvent(st, hk->wait_main, 0));
-                if ((s = full_pre(0, m0, true, df_sms(plan, W - r))) != APIC_OK) return s;
+                // the first quarter capped, so that the partial wave's blocks (forked just
+                // before) keep their SMs; the rest on every SM, so that the SMs the partial
+                // wave frees when it ends do not idle until the full waves are prepared
+                const int a1 = std::max(1, m0 / 4);
+                if ((s = full_pre(0, a1, false, df_sms(plan, W - r))) != APIC_OK) return s;
+                if ((s = full_pre(a1, m0, true, 0)) != APIC_OK) return s;
                 APIC_TRY_CUDA(cudaEventRecord(plan->ev_pre, st));
                 APIC_TRY_CUDA(cudaStreamWaitEvent(plan->side, plan->ev_pre, 0));
             }
