@@ -741,10 +741,11 @@ apic_status reconstruct(apic_plan* plan, apic_net* net, int mode, int n_tiles, c
             // Tiles of the full waves split into MA = [0, ma) on W - r blocks and
             // MB = [ma, m0) on r blocks (one tile per block per round, m0 / W rounds each); T = [m0, nt) is the
             // partial wave. Caller's stream: T's earlier stages, then (fork) the full
-            // waves' background and earlier stages, MA's darkfield rounds, each followed
-            // by its synthesis (T's after the first, ML = [ma, ml) after the last).
-            // Second stream: T's darkfield, then MB's darkfield rounds and the synthesis
-            // of its last round (join).
+            // waves' background and earlier stages (with input parts: per part on a
+            // stream of their own, each round waiting for its part), MA's darkfield
+            // rounds, each followed by its synthesis (T's after the first, ML = [ma, ml)
+            // after the last). Second stream: T's darkfield, then MB's darkfield rounds
+            // and the synthesis of its last round (join).
             if (first) tm.mark(0, 0);
             APIC_TRY_LAUNCH(launch_background(D, r, It + (size_t)m0 * in_tile, plan->c2 + m0, stt + m0, thresh2, st,
                                               replace ? 1 : 0));
