@@ -573,10 +573,10 @@ def gpu_arm(args):
         per_tile = {"value": pt_value, "unit": "Mpx/s", "tiles": k, "ms_per_tile": pt_ms / k,
                     "batched_over_per_tile": None}
 
-    # ---- learned-assisted reconstruction on the same inputs (the network takes tiles of
-    # up to 256 pixels): a network trained here for a few seconds on simulated tiles,
-    # warm-starting the aberration solve (features + network forward + second refinement
-    # inside the timing)
+    # ---- learned-assisted reconstruction on the same inputs, for tiles of up to 256 pixels
+    # (the slide line trains and times its own 512-pixel network): a network trained here
+    # for a few seconds on simulated tiles, warm-starting the aberration solve (features +
+    # network forward + second refinement inside the timing)
     learned = None
     if not args.no_learned and n <= 256:
         learned = learned_timing(args, plan, ill, T, n, H, I, field, zern, status, device)
